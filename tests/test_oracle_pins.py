@@ -1,0 +1,341 @@
+"""Pins for the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed forms,
+brute force from the definition, dense linear algebra, invariants, and the
+Fig. 1 worked example (Section II-A).
+"""
+import os
+from collections import deque
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_06916_b300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+ALPHA = 0.85
+
+
+def _rand_graph(n, m, seed, self_loops=True):
+    rng = np.random.default_rng(seed)
+    s = rng.integers(0, n, m).astype(np.uint32)
+    d = rng.integers(0, n, m).astype(np.uint32)
+    if not self_loops:
+        keep = s != d
+        s, d = s[keep], d[keep]
+    return s, d
+
+
+def _dense_transition(n, s, d, w=None):
+    """Column-stochastic Pt[v, u] = sum over edges u->v of p_uv; d_u = dangling."""
+    w = np.ones(len(s)) if w is None else np.asarray(w, dtype=np.float64)
+    W = np.zeros(n)
+    np.add.at(W, s, w)
+    Pt = np.zeros((n, n))
+    np.add.at(Pt, (d, s), w / W[s])
+    return Pt, (W == 0).astype(np.float64)
+
+
+# ---------------------------------------------------------------- PageRank
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 1000])
+@pytest.mark.parametrize("iters", [1, 5, 20])
+def test_cycle_is_uniform(n, iters):
+    s = np.arange(n, dtype=np.uint32)
+    d = ((np.arange(n) + 1) % n).astype(np.uint32)
+    r = oracle.pagerank(n, s, d, ALPHA, iters)
+    assert np.allclose(r, 1.0 / n, rtol=4e-16 * 8, atol=0)
+
+
+@pytest.mark.parametrize("k", [1, 3, 10, 63])
+@pytest.mark.parametrize("iters", [0, 1, 2, 7, 20, 200])
+def test_in_star_closed_form(k, iters):
+    # k leaves -> centre c = 0; the centre is dangling, leaves have no in-edges.
+    n = k + 1
+    s = np.arange(1, n, dtype=np.uint32)
+    d = np.zeros(k, dtype=np.uint32)
+    r = oracle.pagerank(n, s, d, ALPHA, iters)
+    # r_c^{t+1} = (1-a)/n + a - a(1-1/n) r_c^t  => geometric approach to r*.
+    a = ALPHA
+    rstar = (1 + a * k) / (n + a * k)
+    q = -a * (1 - 1 / n)
+    rc = rstar + q ** iters * (1 / n - rstar)
+    assert r[0] == pytest.approx(rc, rel=1e-13, abs=1e-16)
+    # leaves: (1-a)/n + a r_c^{t-1} / n for t >= 1
+    if iters > 0:
+        rc_prev = rstar + q ** (iters - 1) * (1 / n - rstar)
+        leaf = (1 - a) / n + a * rc_prev / n
+    else:
+        leaf = 1 / n
+    assert np.allclose(r[1:], leaf, rtol=1e-13)
+    if iters >= 200:
+        assert r[0] == pytest.approx(rstar, rel=1e-12)
+        assert np.allclose(r[1:], (1 - rstar) / k, rtol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_dense_power_iteration_and_solve(seed, weighted):
+    n = 5 + 13 * seed  # up to 44 vertices
+    s, d = _rand_graph(n, 3 * n, seed)
+    w = np.random.default_rng(100 + seed).uniform(0.5, 1.5, len(s)) if weighted else None
+    Pt, dang = _dense_transition(n, s, d, w)
+    G = ALPHA * (Pt + np.outer(np.ones(n), dang) / n) + (1 - ALPHA) / n * np.ones((n, n))
+    x = np.full(n, 1.0 / n)
+    for _ in range(20):
+        x = G @ x
+    r = oracle.pagerank(n, s, d, ALPHA, 20, w=w)
+    assert np.abs(r - x).max() < 1e-14
+    # fixed point by Gaussian elimination (textbook): (I - a(Pt + 1 d^T/n)) r = (1-a)/n
+    A = np.eye(n) - ALPHA * (Pt + np.outer(np.ones(n), dang) / n)
+    rstar = np.linalg.solve(A, np.full(n, (1 - ALPHA) / n))
+    r300 = oracle.pagerank(n, s, d, ALPHA, 300, w=w)
+    assert np.abs(r300 - rstar).max() < 1e-13
+
+
+@pytest.mark.parametrize("iters", [1, 3, 20])
+def test_rank_mass_sums_to_one_with_dangling(iters):
+    s, d, _ = inputs.rmat_edges(12, 8 << 12, 7)
+    n = 1 << 12
+    outdeg = np.bincount(s, minlength=n)
+    assert (outdeg == 0).sum() > 100  # plenty of dangling vertices
+    r = oracle.pagerank(n, s, d, ALPHA, iters)
+    assert abs(r.sum() - 1.0) < 1e-12
+    assert (r > 0).all()
+
+
+def test_pagerank_dangling_term_matters():
+    # A plausible mistake (dropping the dangling mass) breaks the sum-to-one pin:
+    # a 2-vertex path 0 -> 1 with 1 dangling.
+    r = oracle.pagerank(2, [0], [1], ALPHA, 1)
+    # r'_0 = (1-a)/2 + a*(0 + 0.5/2); r'_1 = (1-a)/2 + a*(0.5 + 0.5/2)
+    assert r[0] == pytest.approx((1 - ALPHA) / 2 + ALPHA * 0.25, rel=1e-15)
+    assert r[1] == pytest.approx((1 - ALPHA) / 2 + ALPHA * 0.75, rel=1e-15)
+
+
+# ---------------------------------------------------------------- PPR
+
+def test_ppr_uniform_teleport_equals_pagerank():
+    s, d, _ = inputs.rmat_edges(10, 16 << 10, 3)
+    n = 1024
+    t = np.full(n, 1.0 / n)
+    assert np.abs(oracle.personalized_pagerank(n, s, d, t, ALPHA, 30)
+                  - oracle.pagerank(n, s, d, ALPHA, 30)).max() < 1e-15
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ppr_fixed_point_dense(seed):
+    # With dangling mass spread by t the fixed point is x / sum(x),
+    # x = (I - a Pt)^{-1} t (textbook linear solve).
+    n = 30
+    s, d = _rand_graph(n, 60, seed)
+    t = np.zeros(n)
+    t[np.random.default_rng(seed).choice(n, 4, replace=False)] = 0.25
+    Pt, _ = _dense_transition(n, s, d)
+    x = np.linalg.solve(np.eye(n) - ALPHA * Pt, t)
+    r = oracle.personalized_pagerank(n, s, d, t, ALPHA, 400)
+    assert np.abs(r - x / x.sum()).max() < 1e-13
+    # and one step from r0 = t by hand
+    dang = np.bincount(s, minlength=n) == 0
+    r1 = (1 - ALPHA) * t + ALPHA * (Pt @ t + t * t[dang].sum())
+    assert np.abs(oracle.personalized_pagerank(n, s, d, t, ALPHA, 1) - r1).max() < 1e-16
+
+
+# ---------------------------------------------------------------- BFS
+
+def _bellman_ford(n, s, d, root):
+    INF = oracle.INF
+    depth = [INF] * n
+    depth[root] = 0
+    changed = True
+    while changed:  # relax every edge until nothing changes (Algorithm 3)
+        changed = False
+        for u, v in zip(s, d):
+            if depth[u] != INF and depth[v] > depth[u] + 1:
+                depth[v] = depth[u] + 1
+                changed = True
+    return np.array(depth, dtype=np.uint32)
+
+
+def _read_fixture(name):
+    out = {"edge": [], "expect": []}
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            k, *v = line.split()
+            if k in ("edge", "expect"):
+                out[k].append(tuple(int(x) for x in v))
+            else:
+                out[k] = v
+    return out
+
+
+def test_bfs_golden_fixture():
+    fx = _read_fixture("bfs_levels.txt")
+    n = int(fx["n"][0])
+    s = [e[0] for e in fx["edge"]]
+    d = [e[1] for e in fx["edge"]]
+    depth = oracle.bfs(n, s, d, int(fx["root"][0]))
+    want = [oracle.INF if x == "inf" else int(x) for x in fx["depth"]]
+    assert depth.tolist() == want
+    finite = depth[depth != oracle.INF]
+    assert int(finite.max()) == int(fx["maxdepth"][0])  # Algorithm 4 output
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bfs_matches_bellman_ford(seed):
+    n = 3 + 7 * seed
+    s, d = _rand_graph(n, 2 * n, seed)
+    for root in (0, n - 1):
+        assert (oracle.bfs(n, s, d, root) == _bellman_ford(n, s, d, root)).all()
+
+
+# ---------------------------------------------------------------- WCC
+
+def _wcc_dfs(n, s, d):
+    adj = [[] for _ in range(n)]
+    for u, v in zip(s, d):
+        adj[u].append(v)
+        adj[v].append(u)
+    label = [-1] * n
+    for start in range(n):  # increasing ids: each component is first hit at its minimum
+        if label[start] >= 0:
+            continue
+        label[start] = start
+        q = deque([start])
+        while q:
+            u = q.popleft()
+            for v in adj[u]:
+                if label[v] < 0:
+                    label[v] = start
+                    q.append(v)
+    return np.array(label, dtype=np.uint32)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_wcc_matches_dfs(seed):
+    n = 4 + 9 * seed
+    s, d = _rand_graph(n, n, seed)
+    assert (oracle.wcc(n, s, d) == _wcc_dfs(n, s, d)).all()
+
+
+def test_wcc_matches_scipy_components():
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    s, d, _ = inputs.rmat_edges(11, 2 << 11, 5)
+    n = 1 << 11
+    lab = oracle.wcc(n, s, d)
+    A = sp.coo_matrix((np.ones(len(s)), (s, d)), shape=(n, n))
+    k, comp = connected_components(A, directed=True, connection="weak")
+    assert len(np.unique(lab)) == k
+    # same partition, and each label is its component's minimum id
+    for c in range(k):
+        members = np.flatnonzero(comp == c)
+        assert (lab[members] == members.min()).all()
+
+
+# ---------------------------------------------------------------- adjoint
+
+def _dense_M(n, s, d, w):
+    Pt, dang = _dense_transition(n, s, d, w)
+    return ALPHA * (Pt + np.outer(np.ones(n), dang) / n), dang
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_adjoint_teleport_grad_is_unrolled_exact(seed):
+    # L = g . r^K, r^K = M^K r0 + sum_{k<K} M^k (1-a) t  =>  dL/dt = (1-a) sum_{k<K} (M^T)^k g
+    n = 20
+    s, d = _rand_graph(n, 50, seed)
+    w = np.random.default_rng(seed).uniform(0.5, 1.5, len(s))
+    g = np.zeros(n)
+    g[[1, 4, 7]] = 1.0
+    K = 12
+    M, _ = _dense_M(n, s, d, w)
+    acc = np.zeros(n)
+    v = g.copy()
+    for _ in range(K):
+        acc += v
+        v = M.T @ v
+    out = oracle.wpr_adjoint(n, s, d, w, g, ALPHA, fwd_iters=K, adj_terms=K)
+    assert np.abs(out["dt"] - (1 - ALPHA) * acc).max() < 1e-14
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_adjoint_weight_grad_fixed_point_dense(seed):
+    # Exact implicit gradient at the fixed point: lambda = (I - M^T)^{-1} g,
+    # dL/dwhat_uv = a lambda_v r_u, chain rule through what = w / W_u.
+    n = 16
+    s, d = _rand_graph(n, 40, seed)
+    w = np.random.default_rng(seed + 9).uniform(0.5, 1.5, len(s))
+    g = np.zeros(n)
+    g[[0, 3]] = 1.0
+    M, dang = _dense_M(n, s, d, w)
+    A = np.eye(n) - M
+    r = np.linalg.solve(A, np.full(n, (1 - ALPHA) / n))
+    lam = np.linalg.solve(A.T, g)
+    W = np.zeros(n)
+    np.add.at(W, s, w)
+    dwhat = ALPHA * lam[d] * r[s]  # per edge
+    # dL/dw_e = dwhat_e / W_u - sum_{e' from u} dwhat_e' w_e' / W_u^2
+    tmp = np.zeros(n)
+    np.add.at(tmp, s, dwhat * w)
+    dw = dwhat / W[s] - tmp[s] / W[s] ** 2
+    out = oracle.wpr_adjoint(n, s, d, w, g, ALPHA, fwd_iters=400, adj_terms=400)
+    assert np.abs(out["dw"] - dw).max() < 1e-13
+    assert np.abs(out["dt"] - (1 - ALPHA) * lam).max() < 1e-13
+
+
+def test_adjoint_central_differences_and_scale_invariance():
+    n = 1 << 8
+    s, d, w = inputs.rmat_edges(8, 8 << 8, 4, weights=True)
+    w = w.astype(np.float64)
+    T = inputs.targets(n, 16, 44)
+    g = np.zeros(n)
+    g[T] = 1.0
+    K = 200  # a^200 ~ 8e-15: truncation far below the FD error
+    out = oracle.wpr_adjoint(n, s, d, w, g, ALPHA, fwd_iters=K, adj_terms=K)
+    rng = np.random.default_rng(0)
+    for e in rng.choice(len(s), 12, replace=False):
+        h = 1e-6 * w[e]
+        wp, wm = w.copy(), w.copy()
+        wp[e] += h
+        wm[e] -= h
+        Lp = oracle.pagerank(n, s, d, ALPHA, K, w=wp)[T].sum()
+        Lm = oracle.pagerank(n, s, d, ALPHA, K, w=wm)[T].sum()
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - out["dw"][e]) <= 1e-7 * max(abs(fd), 1e-3)
+    # scaling all of u's weights leaves L unchanged => sum_v w_uv dL/dw_uv = 0 per u
+    per_u = np.zeros(n)
+    np.add.at(per_u, s, w * out["dw"])
+    assert np.abs(per_u).max() < 1e-14
+
+
+# ---------------------------------------------------------------- DSSS layout
+
+def test_fig1_subshard_order():
+    fx = _read_fixture("fig1_dsss.txt")
+    n, P = int(fx["n"][0]), int(fx["P"][0])
+    s = np.array([e[0] for e in fx["edge"]])
+    d = np.array([e[1] for e in fx["edge"]])
+    order, off = oracle.dsss_order(n, P, s, d)
+    i, j = 2, 1  # paper's SS_3.2 (1-based)
+    sel = order[off[j * P + i]:off[j * P + i + 1]]
+    assert list(zip(s[sel].tolist(), d[sel].tolist())) == fx["expect"]
+
+
+def test_dsss_order_invariants():
+    n, P = 1000, 7
+    s, d = _rand_graph(n, 5000, 11)
+    order, off = oracle.dsss_order(n, P, s, d)
+    assert sorted(order.tolist()) == list(range(len(s)))  # a permutation
+    L = -(-n // P)
+    for j in range(P):
+        for i in range(P):
+            sel = order[off[j * P + i]:off[j * P + i + 1]]
+            assert (s[sel] // L == i).all() and (d[sel] // L == j).all()
+            key = d[sel].astype(np.int64) * n + s[sel]
+            assert (np.diff(key) >= 0).all()
