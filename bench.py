@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""PageRank GTEPS per iteration of the DSSS sweep on one B300, plus its HBM
+roofline fraction and the FP64 oracle's throughput on the host cores.
+
+Workload (default): R-MAT scale 22, edge factor 16 (67,108,864 uint32 edges,
+a/b/c/d = 0.57/0.19/0.19/0.05, seed 2), P = 16 intervals, PageRank (damping
+0.85, dangling mass spread uniformly) for 20 iterations under SPU. One step =
+one 20-iteration PageRank run over the DSSS already resident in HBM. The edge
+words (268 MB) exceed the 126 MB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--workload rmat22|rmat26|rmat16]
+Under torchrun every rank runs its own replica ("replicas only": the sweep has
+no exchange step on one GPU) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "rmat22": dict(scale=22, ef=16, seed=2, P=16, iters=20),
+    "rmat26": dict(scale=26, ef=22, seed=5, P=64, iters=10),
+    "rmat16": dict(scale=16, ef=16, seed=1, P=4, iters=20),
+}
+METRIC = "PageRank GTEPS/iter & HBM roofline %"
+
+
+def workload_name(w, wl):
+    return (f"R-MAT scale {w['scale']} ef {w['ef']} seed {w['seed']} "
+            f"({w['ef'] << w['scale']} edges), P={w['P']}, PageRank x{w['iters']} SPU")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.6)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier_max(val, world):
+    if world == 1:
+        return val
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([val], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_sample(w, iters_sample, host_edges=None):
+    """FP64 oracle PageRank on the full graph for `iters_sample` iterations."""
+    import oracle
+    from paper_1510_06916_b300 import inputs
+    n = 1 << w["scale"]
+    m = w["ef"] << w["scale"]
+    if host_edges is None:
+        s, d, _ = inputs.rmat_edges(w["scale"], m, w["seed"])
+    else:
+        s, d = host_edges
+    oracle.pagerank(n, s[:1024], d[:1024], 0.85, 1)  # load the library outside the clock
+    t0 = time.perf_counter()
+    oracle.pagerank(n, s, d, 0.85, iters_sample)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return m * iters_sample / dt / 1e9, cores, dt
+
+
+def run_reference(args, w):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1510_06916_b300 import inputs
+    n = 1 << w["scale"]
+    m = w["ef"] << w["scale"]
+    s, d, _ = inputs.rmat_edges(w["scale"], m, w["seed"])
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, 1, (s, d))
+    times = []
+    vals = []
+    for _ in range(args.steps):
+        v, cores, dt = cpu_oracle_sample(w, 1, (s, d))
+        times.append(dt)
+        vals.append(v)
+    total = sum(times)
+    value = m * len(times) / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(w, args.workload), "n": n, "m": m, "P": w["P"],
+                   "iters": w["iters"]},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                         "sample": "1 PageRank iteration (incl. its CSR build) on the full graph per step"},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import numpy as np
+    import torch
+    world, rank, local = dist_setup()
+    from paper_1510_06916_b300 import inputs
+    from paper_1510_06916_b300 import nxgraph as nx
+
+    n = 1 << w["scale"]
+    m = w["ef"] << w["scale"]
+    iters = w["iters"]
+    stream = torch.cuda.current_stream()
+    nx.set_stream(stream)
+    src, dst, _ = inputs.rmat_edges_device(w["scale"], m, w["seed"])
+    torch.cuda.synchronize()
+    g = nx.Graph(src, dst, n, w["P"])
+    del src, dst
+    torch.cuda.empty_cache()
+    info = g.info()
+
+    for _ in range(max(args.warmup, 3)):
+        g.run("pr", iters, "spu")
+    torch.cuda.synchronize()
+
+    clk = ClockSampler(local)
+    clk.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    kern_ms = 0.0
+    launches = 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st = g.run("pr", iters, "spu")
+        kern_ms += st["ms"]
+        launches += st["launches"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = barrier_max(ms, world)
+    ms_per_step = ms_max / args.steps
+    value = m * iters * args.steps * world / (ms_max / 1e3) / 1e9
+
+    # roofline of the sweep kernel: algorithmic bytes per launch / launch time
+    bytes_per_launch = 4 * m + 16 * n
+    t_launch = kern_ms / 1e3 / launches
+    peak, peak_kind = load_peaks()
+    achieved = bytes_per_launch / t_launch / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(args.workload)
+        except Exception:
+            traffic = None
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        hs, hd, _ = inputs.rmat_edges(w["scale"], m, w["seed"])
+        hs_t = torch.from_numpy(hs.view(np.int32)).pin_memory()
+        hd_t = torch.from_numpy(hd.view(np.int32)).pin_memory()
+        out = torch.empty(n, dtype=torch.float32).pin_memory()
+        g2 = nx.Graph(hs_t, hd_t, n, w["P"])  # warm-up of the host path
+        g2.run("pr", iters)
+        g2.values(out)
+        g2.free()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            g2 = nx.Graph(hs_t, hd_t, n, w["P"])
+            g2.run("pr", iters)
+            g2.values(out)
+            g2.free()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        dt = barrier_max(dt, world)
+        e2e = {"value": m * iters * world / dt / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 4 * n,
+               "ms_per_step": dt * 1e3, "includes": "DSSS build from host edges + 20 iterations + values to host"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            v, cores, dt = cpu_oracle_sample(w, 2)
+            cpu = {"value": v, "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                   "sample": f"2 PageRank iterations (incl. CSR build) of the full graph, {dt:.1f} s"}
+        except Exception as e:  # pragma: no cover
+            cpu = {"value": None, "unit": "GTEPS", "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(w, args.workload), "n": n, "m": m, "P": w["P"],
+                       "iters_per_step": iters, "strategy": "SPU",
+                       "l2": "edge words (4 B x m) larger than L2; no flush",
+                       "D": info["D"], "ntiles": info["ntiles"], "build_ms": info["build_ms"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "kernel": "k_sweep<PR> (SPU sweep + fused epilogue)",
+                         "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "launch_ms": t_launch * 1e3},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    g.free()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,231 @@
+/*
+ * nxgraph.h — C ABI of the B300 (sm_103a) DSSS update-sweep library.
+ *
+ * Method: NXgraph (Chi, Dai, Wang, Sun, Li, Yang; arXiv 1510.06916).
+ * Vertices are split into P equal intervals I_0..I_{P-1} of L = ceil(n/P)
+ * vertices; edges into P x P sub-shards SS_ij (source in I_i, destination in
+ * I_j), each sorted by destination and then by source: the Destination-Sorted
+ * Sub-Shard structure (Section II-A, Section III-A "Sharding"). One iteration
+ * updates every destination interval from the previous iteration's values of
+ * every source interval (Algorithm 1, synchronous consistency of Section II-B)
+ * under one of three schedules: Single-Phase Update (Algorithm 5), Double-Phase
+ * Update with per-sub-shard hubs (Algorithm 6) or Mixed-Phase Update
+ * (Algorithm 7, Q resident intervals with Q <= B_M * P / (2 n B_a), Section
+ * III-B3).
+ *
+ * Conventions for every function below:
+ *  - The return value is an nx_status; 0 (NX_OK) is success. No function
+ *    throws, aborts or exits the process. On failure, nx_last_error() returns
+ *    a one-line description (thread-local).
+ *  - "device pointer" means memory on the current CUDA device; "host pointer"
+ *    means ordinary or pinned host memory. Flags or *_is_device arguments say
+ *    which; pointers are never owned by the library unless stated.
+ *  - All GPU work is issued on the stream set by nx_set_stream (default: the
+ *    legacy default stream) and the calls return after that work is complete
+ *    unless stated otherwise.
+ *  - Vertex ids are uint32 in [0, n), n <= 2^30; edge counts m < 2^32.
+ */
+#ifndef NXGRAPH_H
+#define NXGRAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t nx_status;
+#define NX_OK 0
+#define NX_ERR_INVALID_ARG 1      /* bad size, id >= n, missing structure, ... */
+#define NX_ERR_OOM 2              /* device or pinned-host allocation failed   */
+#define NX_ERR_BUDGET_TOO_SMALL 3 /* budget below what the strategy needs      */
+#define NX_ERR_CUDA 4             /* a CUDA call failed (message has the text) */
+#define NX_ERR_TIMEOUT 5          /* a bounded device-side wait ran out        */
+
+/* Vertex programs (Section II-B "Update Scheme"). */
+typedef enum {
+  NX_PR = 0,  /* PageRank: r' = (1-a)/n + a (sum_{u->v} r_u/outdeg_u + Dm/n)      */
+  NX_PPR = 1, /* personalized PageRank: teleport t, r0 = t, dangling mass by t    */
+  NX_WPR = 2, /* weighted PageRank: p_uv = w_uv / W_u (needs NX_WITH_WEIGHTS)     */
+  NX_BFS = 3, /* Algorithms 2-4: depth(root) = 0, min over in-edges of depth+1    */
+  NX_WCC = 4  /* min-label propagation along both edge directions (needs
+                 NX_WITH_TRANSPOSE); label = smallest vertex id in the component */
+} nx_program;
+
+/* Update strategies (Section III-B). */
+typedef enum {
+  NX_SPU = 0,  /* Algorithm 5: all intervals resident (ping-pong), one pass      */
+  NX_DPU = 1,  /* Algorithm 6: ToHub pass writes per-sub-shard hubs, FromHub pass
+                  combines them per destination interval                           */
+  NX_MPU = 2,  /* Algorithm 7: Q intervals resident from the budget; the (P-Q)^2
+                  sub-shards among the others go through hubs                      */
+  NX_AUTO = 3  /* SPU when the budget holds all intervals, else MPU               */
+} nx_strategy;
+
+/* nx_build_dsss flags. */
+#define NX_HOST_PTRS 0u          /* src/dst/w are host pointers                     */
+#define NX_DEV_PTRS 1u           /* src/dst/w are device pointers                   */
+#define NX_WITH_TRANSPOSE 2u     /* also build the source-sorted (transpose) DSSS  */
+#define NX_WITH_WEIGHTS 4u       /* w (float, > 0) is given: weighted PageRank     */
+
+typedef struct nx_graph nx_graph; /* opaque; owns all its device and pinned memory */
+
+typedef struct {
+  float alpha;            /* damping (PageRank family), e.g. 0.85              */
+  uint32_t root;          /* BFS root vertex                                   */
+  const float* teleport;  /* PPR/WPR teleport vector [n], or NULL = uniform 1/n */
+  int32_t teleport_is_device;
+  int32_t use_graph;      /* 1: capture fixed-count iteration loops in a CUDA graph */
+} nx_params;
+
+typedef struct {
+  uint32_t iters_done;    /* sweeps performed                                   */
+  uint32_t Q;             /* resident intervals used (MPU; P for SPU, 0 for DPU) */
+  uint32_t strategy;      /* the strategy that ran (after NX_AUTO)              */
+  uint32_t streamed_cols; /* shards streamed from pinned host per iteration     */
+  float ms;               /* wall time of the iteration loop (CUDA events)      */
+  uint64_t edges_swept;   /* edges read by all sweeps (inactive sources skipped) */
+  uint64_t bytes_model;   /* algorithmic device bytes of the loop (see DESIGN)  */
+  uint64_t h2d_bytes;     /* host->device bytes of the loop (streaming)         */
+  uint64_t d2h_bytes;     /* device->host bytes of the loop                     */
+  uint32_t launches;      /* kernels launched by the loop                       */
+  uint32_t pad_;
+} nx_run_stats;
+
+typedef struct {
+  uint32_t n, P, L;       /* vertices, intervals, interval length ceil(n/P)     */
+  uint32_t ntiles;        /* destination tiles (a tile never crosses an interval) */
+  uint32_t tile_max;      /* max vertices in a tile                             */
+  uint32_t lb;            /* bits of a source offset inside an interval         */
+  uint64_t m;             /* edges                                              */
+  uint64_t D;             /* distinct (sub-shard, destination) pairs = hub size */
+  uint64_t D_t;           /* same for the transpose DSSS (0 if not built)       */
+  uint64_t device_bytes;  /* device memory held by the graph                    */
+  float build_ms;         /* time of nx_build_dsss on the device                */
+  int32_t has_transpose, has_weights;
+} nx_graph_info;
+
+/* Stream for all later calls (a cudaStream_t; NULL = legacy default stream). */
+nx_status nx_set_stream(void* stream);
+
+/* Copies the last error message of this thread into buf (always terminated). */
+void nx_last_error(char* buf, size_t len);
+
+/*
+ * Builds the DSSS of Section II-A / III-A on the device: equal intervals of
+ * L = ceil(n/P) vertices, P*P sub-shards sorted by (destination, source), the
+ * per-sub-shard hub index (Table I, H_ij), out-degrees, and optionally the
+ * transpose (source-sorted) DSSS and per-source normalised weights.
+ *   src, dst : edge endpoints [m] (uint32 ids < n); host or device per flags
+ *   m, n, P  : edges, vertices (1 <= n <= 2^30), intervals (1 <= P <= min(n, 1024))
+ *   w        : edge weights [m] (> 0) when NX_WITH_WEIGHTS, else ignored
+ *   out      : receives the new graph (caller frees with nx_graph_free)
+ * Input arrays are copied; the caller keeps ownership.
+ * Errors: INVALID_ARG (an id >= n, P out of range, m >= 2^32, n > 2^30,
+ * missing w), OOM, CUDA.
+ */
+nx_status nx_build_dsss(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n,
+                        uint32_t P, uint32_t flags, const float* w, nx_graph** out);
+
+nx_status nx_graph_get_info(const nx_graph* g, nx_graph_info* info);
+
+/*
+ * Exports a DSSS in its storage order (Section II-A): edge k of the output is
+ * the k-th stored edge, sub-shard by sub-shard (shard j = destination
+ * interval outer, source interval i inner), each sorted by destination then
+ * source. sub_off[j*P + i] is where SS_ij starts (P*P + 1 entries).
+ *   transpose : 0 = forward DSSS, 1 = the transpose DSSS (its "destination"
+ *               is the original source; the output gives original src/dst)
+ *   src, dst  : host uint32 [m]; sub_off: host uint64 [P*P + 1] (nullable)
+ * Errors: INVALID_ARG (transpose not built), CUDA.
+ */
+nx_status nx_dsss_export(const nx_graph* g, int32_t transpose, uint32_t* src, uint32_t* dst,
+                         uint64_t* sub_off);
+
+/*
+ * Runs `iters` synchronous iterations of `program` (BFS/WCC: at most `iters`,
+ * stopping when no interval is active — Algorithm 1) under `strategy` with a
+ * device-memory budget of mem_budget_bytes for intervals and sub-shards
+ * (0 = unlimited). Values persist in the graph: a later nx_run of the same
+ * program with params->use_graph unchanged continues from them when
+ * `resume` is set in the params-independent sense below.
+ *   params : nullable (alpha 0.85, root 0, uniform teleport)
+ *   stats  : nullable; filled on success
+ * The run starts from the program's Initialize (Algorithm 2 for BFS) unless
+ * nx_set_values was called since the last run of the same program, in which
+ * case it continues from those values.
+ * Errors: INVALID_ARG (program needs a structure the graph lacks, root >= n),
+ * BUDGET_TOO_SMALL (SPU without room for 2 n B_a; MPU/DPU below one interval
+ * pair), OOM, CUDA.
+ */
+nx_status nx_run(nx_graph* g, nx_program program, const nx_params* params, uint32_t iters,
+                 nx_strategy strategy, uint64_t mem_budget_bytes, nx_run_stats* stats);
+
+/*
+ * Copies the current values of the last program run (float ranks for the
+ * PageRank family; uint32 depths / labels for BFS / WCC) into out[count],
+ * count == n. out is device memory if out_is_device, else host memory.
+ */
+nx_status nx_get_values(const nx_graph* g, void* out, uint64_t count, int32_t out_is_device);
+
+/*
+ * Replaces the current values of `program` (same layout as nx_get_values) so
+ * that the next nx_run of that program continues from them (resume; for BFS
+ * and WCC every interval is marked active).
+ */
+nx_status nx_set_values(nx_graph* g, nx_program program, const void* in, uint64_t count,
+                        int32_t in_is_device);
+
+/*
+ * Batched personalized PageRank: B teleport vectors solved together, one
+ * sweep per iteration over the DSSS with B values per vertex.
+ *   teleport : [n][B] row-major float (vertex-major), host or device
+ *   ranks    : output [n][B] float, host or device (same flag)
+ * r0 = t and dangling mass spread by each column's t; alpha from params.
+ * Errors: INVALID_ARG (B not in {1..64} or not a multiple of 4 unless B < 4... see
+ * DESIGN: B in [1, 64]), OOM, CUDA.
+ */
+nx_status nx_run_ppr_batch(nx_graph* g, const float* teleport, uint32_t B, uint32_t iters,
+                           float alpha, float* ranks, int32_t ptrs_are_device,
+                           nx_run_stats* stats);
+
+/*
+ * Adjoint of weighted PageRank (an extension; the paper has no counterpart).
+ * Uses the ranks r of the last NX_WPR run (fwd iterations) and the transpose
+ * DSSS: lambda^0 = grad_r, lambda' = a (W^ lambda + d (1^T lambda)/n) + grad_r
+ * for adj_terms-1 updates, then
+ *   grad_t[v]  = (1-a) lambda_v
+ *   grad_w[e]  = a r_u / W_u (lambda_v - sum_v' w^_uv' lambda_v'),  e = (u, v)
+ * with grad_w in the caller's original edge order.
+ *   grad_r : [n] float; grad_w : [m] float; grad_t : [n] float (nullable)
+ *   all three on the device if ptrs_are_device, else host.
+ * Errors: INVALID_ARG (no weights/transpose, no prior WPR run), OOM, CUDA.
+ */
+nx_status nx_adjoint_wpr(nx_graph* g, const float* grad_r, uint32_t adj_terms, float* grad_w,
+                         float* grad_t, int32_t ptrs_are_device, nx_run_stats* stats);
+
+/*
+ * Runs `program` on `count` independent graphs in one persistent kernel per
+ * call, the whole iteration loop captured in a CUDA graph. Each graph keeps
+ * its own values (read them with nx_get_values). BFS uses root 0.
+ * Errors: INVALID_ARG (WCC on a graph without transpose, ...), TIMEOUT (a
+ * bounded grid barrier gave up; the values are then undefined), OOM, CUDA.
+ */
+nx_status nx_run_multi(nx_graph** graphs, uint32_t count, nx_program program, float alpha,
+                       uint32_t iters, nx_run_stats* stats);
+
+void nx_graph_free(nx_graph* g);
+
+/* Planner model of Section III-B (Table II): bytes read / written per
+ * iteration for strategy s with n vertices, m edges, P intervals, budget B_M,
+ * attribute/id/edge sizes B_a, B_v, B_e and average hub in-degree d.
+ * Q (resident intervals) = min(P, floor(B_M * P / (2 n B_a))) for MPU. */
+nx_status nx_io_model(nx_strategy s, double n, double m, double P, double B_M, double B_a,
+                      double B_v, double B_e, double d, double* Q, double* bytes_read,
+                      double* bytes_write);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NXGRAPH_H */

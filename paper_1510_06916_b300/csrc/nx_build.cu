@@ -1,0 +1,449 @@
+// DSSS builder (Section III-A "Sharding"): edge list -> P x P destination-sorted
+// sub-shards, entirely on the device.
+//
+// Layout produced (per DSSS):
+//   * Vertices: P equal intervals of L = ceil(n/P) (the paper's equal-size
+//     partitioning). Each interval is cut further into destination tiles of at
+//     most tile_max vertices and about E_tile in-edges (a tile never crosses an
+//     interval). Tiles are the unit a thread block owns in a sweep.
+//   * Edges: sorted by (j, i, dst, src) — shard j (destination interval), then
+//     sub-shard SS_ij (source interval i), then destination, then source
+//     (Section III-A: edges sorted by destination, ties by source).
+//     The run of SS_ij that falls in tile t is the "piece" (i, t).
+//   * Each edge is one 32-bit word ((dst - tile_start) << lb) | src_local, with
+//     src_local = src - i*L < 2^lb. This is the paper's "compressed sparse
+//     format": destination and source high bits are implied by the position.
+//   * Hub index (Table I, H_ij): one entry per distinct destination of each
+//     sub-shard, in order, with its destination offset inside its tile.
+#include <algorithm>
+#include <cstdio>
+
+#include "nx_internal.cuh"
+
+namespace nx {
+namespace {
+
+constexpr uint32_t kTileMaxCap = 4096;  // float accumulators: 16 KB of shared memory
+
+__global__ void k_check_ids(const uint32_t* __restrict__ a, uint64_t m, uint32_t n,
+                            uint32_t* __restrict__ bad) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  bool any = false;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+    any |= a[e] >= n;
+  if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
+__global__ void k_histogram(const uint32_t* __restrict__ a, uint64_t m, uint32_t* __restrict__ h) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+    atomicAdd(&h[a[e]], 1u);
+}
+
+__global__ void k_deg_sum(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+                          uint32_t n, uint64_t* __restrict__ out) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    out[v] = (uint64_t)a[v] + (b ? b[v] : 0u);
+}
+
+// A vertex starts a tile at an interval start, every tile_max vertices inside
+// an interval, and where the in-edge prefix crosses a multiple of E_tile.
+__global__ void k_tile_flags(const uint64_t* __restrict__ pre, uint32_t n, uint32_t L,
+                             uint32_t tile_max, uint64_t E, uint32_t* __restrict__ flag) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    uint32_t p = (uint32_t)(v % L);
+    bool s = (p == 0) || (p % tile_max == 0) || (pre[v] / E != pre[v - 1] / E);
+    flag[v] = s ? 1u : 0u;
+  }
+}
+
+__global__ void k_tile_ids(const uint32_t* __restrict__ flag, uint32_t* __restrict__ tid,
+                           uint32_t n, uint32_t* __restrict__ tile_start) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    uint32_t t = tid[v] + flag[v] - 1;  // tid holds the exclusive scan of flags
+    tid[v] = t;
+    if (flag[v]) tile_start[t] = (uint32_t)v;
+  }
+}
+
+struct KeyCodec {
+  uint32_t P, L, lb;
+  __host__ __device__ uint64_t encode(uint32_t s, uint32_t d) const {
+    uint32_t i = s / L, j = d / L;
+    return ((uint64_t)(j * P + i) << (2 * lb)) | ((uint64_t)(d - j * L) << lb) | (s - i * L);
+  }
+  __device__ void decode(uint64_t k, uint32_t* i, uint32_t* j, uint32_t* d, uint32_t* sl) const {
+    uint32_t sub = (uint32_t)(k >> (2 * lb));
+    uint64_t mask = lb ? ((1ull << lb) - 1) : 0ull;
+    *sl = (uint32_t)(k & mask);
+    uint32_t dl = (uint32_t)((k >> lb) & mask);
+    *j = sub / P;
+    *i = sub - *j * P;
+    *d = *j * L + dl;
+  }
+};
+
+__global__ void k_make_keys(const uint32_t* __restrict__ s, const uint32_t* __restrict__ d,
+                            uint64_t m, KeyCodec kc, uint64_t* __restrict__ keys,
+                            uint32_t* __restrict__ idx) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    keys[e] = kc.encode(s[e], d[e]);
+    if (idx) idx[e] = (uint32_t)e;
+  }
+}
+
+struct PieceMap {
+  KeyCodec kc;
+  const uint32_t* tile_of;     // [n]
+  const uint32_t* tile_start;  // [ntiles+1]
+  const uint32_t* col_tb;      // [P+1]
+  __device__ uint64_t piece(uint64_t key, uint32_t* d_out, uint32_t* t_out, uint32_t* sl) const {
+    uint32_t i, j, d;
+    kc.decode(key, &i, &j, &d, sl);
+    uint32_t t = tile_of[d];
+    uint32_t tb = col_tb[j], nt = col_tb[j + 1] - tb;
+    *d_out = d;
+    *t_out = t;
+    return piece_index(kc.P, tb, nt, i, t);
+  }
+};
+
+// Edge words and run-head flags (first edge of each (piece, destination) run).
+__global__ void k_words(const uint64_t* __restrict__ keys, uint64_t m, PieceMap pm,
+                        uint32_t* __restrict__ ew, uint32_t* __restrict__ head) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    uint32_t d, t, sl;
+    uint64_t pc = pm.piece(keys[e], &d, &t, &sl);
+    ew[e] = ((d - pm.tile_start[t]) << pm.kc.lb) | sl;
+    bool h = true;
+    if (e > 0) {
+      uint32_t d0, t0, sl0;
+      uint64_t pc0 = pm.piece(keys[e - 1], &d0, &t0, &sl0);
+      h = (pc0 != pc) || (d0 != d);
+    }
+    head[e] = h ? 1u : 0u;
+  }
+}
+
+// piece_off / hub_off boundaries and hub destination offsets. hidx is the
+// exclusive scan of the head flags (hub entry of each run).
+__global__ void k_bounds(const uint64_t* __restrict__ keys, uint64_t m, PieceMap pm,
+                         const uint32_t* __restrict__ hidx, const uint32_t* __restrict__ ew,
+                         uint64_t* __restrict__ piece_off, uint64_t* __restrict__ hub_off,
+                         uint16_t* __restrict__ hub_dst, uint64_t npieces, uint64_t D) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e <= m; e += stride) {
+    uint32_t d, t, sl;
+    uint64_t pc = e < m ? pm.piece(keys[e], &d, &t, &sl) : npieces;
+    uint64_t prev = 0;
+    bool first = (e == 0);
+    if (!first) {
+      uint32_t d0, t0, sl0;
+      prev = pm.piece(keys[e - 1], &d0, &t0, &sl0) + 1;
+    }
+    uint64_t h = e < m ? (uint64_t)hidx[e] : D;
+    for (uint64_t k = prev; k <= pc && k <= npieces; ++k) {
+      piece_off[k] = e;
+      hub_off[k] = h;
+    }
+    if (e < m) {
+      // hidx is the exclusive scan of the head flags: a head is where it steps
+      bool is_head = (e + 1 < m) ? (hidx[e + 1] != hidx[e]) : ((uint64_t)hidx[e] + 1 == D);
+      if (is_head) hub_dst[hidx[e]] = (uint16_t)(ew[e] >> pm.kc.lb);
+    }
+  }
+}
+
+__global__ void k_wsum(const uint32_t* __restrict__ s, const float* __restrict__ w, uint64_t m,
+                       double* __restrict__ W) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+    atomicAdd(&W[s[e]], (double)w[e]);
+}
+
+__global__ void k_wnorm(const uint32_t* __restrict__ s, const float* __restrict__ w, uint64_t m,
+                        const double* __restrict__ W, float* __restrict__ wn) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+    wn[e] = (float)((double)w[e] / W[s[e]]);
+}
+
+__global__ void k_wsum_f(const double* __restrict__ W, uint32_t n, float* __restrict__ Wf) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    Wf[v] = (float)W[v];
+}
+
+__global__ void k_gather_f(const float* __restrict__ src, const uint32_t* __restrict__ idx,
+                           uint64_t m, float* __restrict__ out) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+    out[e] = src[idx[e]];
+}
+
+unsigned grid_for(uint64_t work, unsigned threads = 256) {
+  uint64_t b = ceil_div(work ? work : 1, threads);
+  uint64_t cap = (uint64_t)num_sms() * 16;
+  return (unsigned)std::min<uint64_t>(b, cap);
+}
+
+// Builds one DSSS from (s, d) over the geometry; wn (nullable) are the
+// normalised weights in input order.
+nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geometry& geo,
+                    const uint32_t* tile_of, const float* wn, Dsss& out) {
+  out.m = m;
+  const uint64_t npieces = (uint64_t)geo.P * geo.ntiles;
+  KeyCodec kc{geo.P, geo.L, geo.lb};
+  const uint32_t key_bits = bits_for((uint64_t)geo.P * geo.P) + 2 * geo.lb;
+  if (key_bits > 64) return invalid("DSSS key does not fit 64 bits (n too large for P)");
+  DevBuf keys, idx;
+  NX_TRY(keys.alloc(std::max<uint64_t>(m, 1) * sizeof(uint64_t)));
+  if (wn) NX_TRY(idx.alloc(std::max<uint64_t>(m, 1) * sizeof(uint32_t)));
+  if (m) {
+    k_make_keys<<<grid_for(m), 256, 0, stream()>>>(s, d, m, kc, keys.as<uint64_t>(),
+                                                   wn ? idx.as<uint32_t>() : nullptr);
+    NX_LAUNCH_CHECK();
+    NX_TRY(radix_sort_u64(keys.as<uint64_t>(), wn ? idx.as<uint32_t>() : nullptr, m, key_bits));
+  }
+  const uint64_t mpad = round_up(m, 8) + 8;
+  NX_TRY(out.ew.alloc(mpad * sizeof(uint32_t)));
+  NX_CUDA(cudaMemsetAsync(out.ew.p, 0, mpad * sizeof(uint32_t), stream()));
+  NX_TRY(out.piece_off.alloc((npieces + 1) * sizeof(uint64_t)));
+  NX_TRY(out.hub_off.alloc((npieces + 1) * sizeof(uint64_t)));
+  PieceMap pm{kc, tile_of, geo.tile_start.as<uint32_t>(), geo.col_tb.as<uint32_t>()};
+  DevBuf head, dtot;
+  NX_TRY(head.alloc(std::max<uint64_t>(m, 1) * sizeof(uint32_t)));
+  NX_TRY(dtot.alloc(sizeof(uint32_t)));
+  if (m) {
+    k_words<<<grid_for(m), 256, 0, stream()>>>(keys.as<uint64_t>(), m, pm, out.ew.as<uint32_t>(),
+                                               head.as<uint32_t>());
+    NX_LAUNCH_CHECK();
+    NX_TRY(exclusive_scan_u32(head.as<uint32_t>(), head.as<uint32_t>(), m, dtot.as<uint32_t>()));
+    uint32_t D32 = 0;
+    NX_CUDA(cudaMemcpyAsync(&D32, dtot.p, sizeof D32, cudaMemcpyDeviceToHost, stream()));
+    NX_CUDA(cudaStreamSynchronize(stream()));
+    out.D = D32;
+  } else {
+    out.D = 0;
+  }
+  NX_TRY(out.hub_dst.alloc(std::max<uint64_t>(out.D, 1) * sizeof(uint16_t)));
+  k_bounds<<<grid_for(m + 1), 256, 0, stream()>>>(
+      keys.as<uint64_t>(), m, pm, head.as<uint32_t>(), out.ew.as<uint32_t>(),
+      out.piece_off.as<uint64_t>(), out.hub_off.as<uint64_t>(), out.hub_dst.as<uint16_t>(),
+      npieces, out.D);
+  NX_LAUNCH_CHECK();
+  if (wn) {
+    NX_TRY(out.wt.alloc(mpad * sizeof(float)));
+    NX_CUDA(cudaMemsetAsync(out.wt.p, 0, mpad * sizeof(float), stream()));
+    if (m) {
+      k_gather_f<<<grid_for(m), 256, 0, stream()>>>(wn, idx.as<uint32_t>(), m, out.wt.as<float>());
+      NX_LAUNCH_CHECK();
+    }
+  }
+  out.h_piece_off.resize(npieces + 1);
+  NX_CUDA(cudaMemcpyAsync(out.h_piece_off.data(), out.piece_off.p, (npieces + 1) * sizeof(uint64_t),
+                          cudaMemcpyDeviceToHost, stream()));
+  NX_CUDA(cudaStreamSynchronize(stream()));
+  out.dev_cols = geo.P;
+  return NX_OK;
+}
+
+nx_status build_geometry(nx_graph* g, const uint32_t* deg_a, const uint32_t* deg_b,
+                         uint64_t m_bal, DevBuf& tile_of) {
+  Geometry& geo = g->geo;
+  const uint32_t n = geo.n;
+  uint64_t E = m_bal / ((uint64_t)num_sms() * 8);
+  E = std::max<uint64_t>(2048, std::min<uint64_t>(E, 65536));
+  DevBuf pre, flag;
+  NX_TRY(pre.alloc((uint64_t)n * sizeof(uint64_t)));
+  NX_TRY(flag.alloc((uint64_t)n * sizeof(uint32_t)));
+  NX_TRY(tile_of.alloc((uint64_t)n * sizeof(uint32_t)));
+  k_deg_sum<<<grid_for(n), 256, 0, stream()>>>(deg_a, deg_b, n, pre.as<uint64_t>());
+  NX_LAUNCH_CHECK();
+  NX_TRY(exclusive_scan_u64(pre.as<uint64_t>(), pre.as<uint64_t>(), n, nullptr));
+  k_tile_flags<<<grid_for(n), 256, 0, stream()>>>(pre.as<uint64_t>(), n, geo.L, geo.tile_max, E,
+                                                  flag.as<uint32_t>());
+  NX_LAUNCH_CHECK();
+  DevBuf tot;
+  NX_TRY(tot.alloc(sizeof(uint32_t)));
+  NX_TRY(exclusive_scan_u32(flag.as<uint32_t>(), tile_of.as<uint32_t>(), n, tot.as<uint32_t>()));
+  uint32_t ntiles = 0;
+  NX_CUDA(cudaMemcpyAsync(&ntiles, tot.p, sizeof ntiles, cudaMemcpyDeviceToHost, stream()));
+  NX_CUDA(cudaStreamSynchronize(stream()));
+  geo.ntiles = ntiles;
+  NX_TRY(geo.tile_start.alloc(((uint64_t)ntiles + 1) * sizeof(uint32_t)));
+  k_tile_ids<<<grid_for(n), 256, 0, stream()>>>(flag.as<uint32_t>(), tile_of.as<uint32_t>(), n,
+                                                geo.tile_start.as<uint32_t>());
+  NX_LAUNCH_CHECK();
+  NX_CUDA(cudaMemcpyAsync(geo.tile_start.as<uint32_t>() + ntiles, &geo.n, sizeof(uint32_t),
+                          cudaMemcpyHostToDevice, stream()));
+  geo.h_tile_start.resize((size_t)ntiles + 1);
+  NX_CUDA(cudaMemcpyAsync(geo.h_tile_start.data(), geo.tile_start.p,
+                          ((uint64_t)ntiles + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                          stream()));
+  NX_CUDA(cudaStreamSynchronize(stream()));
+  // first tile of every column (empty trailing intervals get ntiles)
+  geo.h_col_tb.assign((size_t)geo.P + 1, ntiles);
+  {
+    uint32_t t = 0;
+    for (uint32_t j = 0; j < geo.P; ++j) {
+      uint64_t v0 = (uint64_t)j * geo.L;
+      while (t < ntiles && geo.h_tile_start[t] < v0) ++t;
+      geo.h_col_tb[j] = t;
+    }
+  }
+  NX_TRY(geo.col_tb.alloc(((size_t)geo.P + 1) * sizeof(uint32_t)));
+  NX_CUDA(cudaMemcpyAsync(geo.col_tb.p, geo.h_col_tb.data(), ((size_t)geo.P + 1) * sizeof(uint32_t),
+                          cudaMemcpyHostToDevice, stream()));
+  NX_CUDA(cudaStreamSynchronize(stream()));
+  return NX_OK;
+}
+
+nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t P,
+                     uint32_t flags, const float* w, nx_graph* g) {
+  const bool on_dev = flags & NX_DEV_PTRS;
+  const bool want_t = flags & NX_WITH_TRANSPOSE;
+  const bool want_w = flags & NX_WITH_WEIGHTS;
+  cudaEvent_t e0, e1;
+  NX_CUDA(cudaEventCreate(&e0));
+  NX_CUDA(cudaEventCreate(&e1));
+  NX_CUDA(cudaEventRecord(e0, stream()));
+  // device copies of the inputs
+  DevBuf ds, dd, dw;
+  const uint32_t *s = src, *d = dst;
+  const float* wp = w;
+  if (!on_dev) {
+    NX_TRY(ds.alloc(std::max<uint64_t>(m, 1) * 4));
+    NX_TRY(dd.alloc(std::max<uint64_t>(m, 1) * 4));
+    if (m) {
+      NX_CUDA(cudaMemcpyAsync(ds.p, src, m * 4, cudaMemcpyHostToDevice, stream()));
+      NX_CUDA(cudaMemcpyAsync(dd.p, dst, m * 4, cudaMemcpyHostToDevice, stream()));
+    }
+    s = ds.as<uint32_t>();
+    d = dd.as<uint32_t>();
+    if (want_w) {
+      NX_TRY(dw.alloc(std::max<uint64_t>(m, 1) * 4));
+      if (m) NX_CUDA(cudaMemcpyAsync(dw.p, w, m * 4, cudaMemcpyHostToDevice, stream()));
+      wp = dw.as<float>();
+    }
+  }
+  {  // ids < n
+    DevBuf bad;
+    NX_TRY(bad.alloc(4));
+    NX_CUDA(cudaMemsetAsync(bad.p, 0, 4, stream()));
+    if (m) {
+      k_check_ids<<<grid_for(m), 256, 0, stream()>>>(s, m, n, bad.as<uint32_t>());
+      k_check_ids<<<grid_for(m), 256, 0, stream()>>>(d, m, n, bad.as<uint32_t>());
+      NX_LAUNCH_CHECK();
+    }
+    uint32_t hb = 0;
+    NX_CUDA(cudaMemcpyAsync(&hb, bad.p, 4, cudaMemcpyDeviceToHost, stream()));
+    NX_CUDA(cudaStreamSynchronize(stream()));
+    if (hb) return invalid("nx_build_dsss: an edge endpoint is >= n");
+  }
+  g->m = m;
+  Geometry& geo = g->geo;
+  geo.n = n;
+  geo.P = P;
+  geo.L = (uint32_t)ceil_div(n, P);
+  geo.lb = bits_for(geo.L);
+  geo.tile_max = (uint32_t)std::min<uint64_t>(kTileMaxCap, 1ull << (32 - geo.lb));
+  // degrees
+  DevBuf indeg;
+  NX_TRY(g->outdeg.alloc((uint64_t)n * 4));
+  NX_TRY(indeg.alloc((uint64_t)n * 4));
+  NX_CUDA(cudaMemsetAsync(g->outdeg.p, 0, (uint64_t)n * 4, stream()));
+  NX_CUDA(cudaMemsetAsync(indeg.p, 0, (uint64_t)n * 4, stream()));
+  if (m) {
+    k_histogram<<<grid_for(m), 256, 0, stream()>>>(s, m, g->outdeg.as<uint32_t>());
+    k_histogram<<<grid_for(m), 256, 0, stream()>>>(d, m, indeg.as<uint32_t>());
+    NX_LAUNCH_CHECK();
+  }
+  DevBuf tile_of;
+  NX_TRY(build_geometry(g, indeg.as<uint32_t>(), want_t ? g->outdeg.as<uint32_t>() : nullptr,
+                        want_t ? 2 * m : m, tile_of));
+  indeg.release();
+  // weights: W_u in FP64, normalised weights in input order
+  DevBuf wn;
+  if (want_w) {
+    DevBuf W;
+    NX_TRY(W.alloc((uint64_t)n * 8));
+    NX_CUDA(cudaMemsetAsync(W.p, 0, (uint64_t)n * 8, stream()));
+    NX_TRY(wn.alloc(std::max<uint64_t>(m, 1) * 4));
+    NX_TRY(g->wsum.alloc((uint64_t)n * 4));
+    if (m) {
+      k_wsum<<<grid_for(m), 256, 0, stream()>>>(s, wp, m, W.as<double>());
+      k_wnorm<<<grid_for(m), 256, 0, stream()>>>(s, wp, m, W.as<double>(), wn.as<float>());
+      NX_LAUNCH_CHECK();
+    }
+    k_wsum_f<<<grid_for(n), 256, 0, stream()>>>(W.as<double>(), n, g->wsum.as<float>());
+    NX_LAUNCH_CHECK();
+    NX_CUDA(cudaStreamSynchronize(stream()));
+    g->has_w = true;
+  }
+  NX_TRY(build_one(s, d, m, geo, tile_of.as<uint32_t>(), want_w ? wn.as<float>() : nullptr, g->fwd));
+  if (want_t) {
+    NX_TRY(build_one(d, s, m, geo, tile_of.as<uint32_t>(), want_w ? wn.as<float>() : nullptr,
+                     g->tr));
+    g->has_tr = true;
+  }
+  if (want_w) {  // caller-order endpoints for the edge gradients
+    NX_TRY(g->orig_src.alloc(std::max<uint64_t>(m, 1) * 4));
+    NX_TRY(g->orig_dst.alloc(std::max<uint64_t>(m, 1) * 4));
+    if (m) {
+      NX_CUDA(cudaMemcpyAsync(g->orig_src.p, s, m * 4, cudaMemcpyDeviceToDevice, stream()));
+      NX_CUDA(cudaMemcpyAsync(g->orig_dst.p, d, m * 4, cudaMemcpyDeviceToDevice, stream()));
+    }
+  }
+  NX_CUDA(cudaEventRecord(e1, stream()));
+  NX_CUDA(cudaEventSynchronize(e1));
+  NX_CUDA(cudaEventElapsedTime(&g->build_ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return NX_OK;
+}
+
+}  // namespace
+}  // namespace nx
+
+uint64_t nx_graph::device_bytes() const {
+  const nx::DevBuf* bufs[] = {&geo.tile_start, &geo.col_tb, &fwd.ew, &fwd.wt, &fwd.piece_off,
+                              &fwd.hub_off, &fwd.hub_dst, &tr.ew, &tr.wt, &tr.piece_off,
+                              &tr.hub_off, &tr.hub_dst, &outdeg, &wsum, &orig_src, &orig_dst,
+                              &val[0], &val[1], &aux[0], &aux[1], &act[0], &act[1], &scal,
+                              &tile_part, &split_buf, &tile_ticket, &items, &hubs, &tele,
+                              &lam[0], &lam[1], &ybuf, &stage[0], &stage[1], &vstage[0],
+                              &vstage[1], &accres};
+  uint64_t s = 0;
+  for (auto* b : bufs) s += b->bytes;
+  return s;
+}
+
+extern "C" nx_status nx_build_dsss(const uint32_t* src, const uint32_t* dst, uint64_t m,
+                                   uint32_t n, uint32_t P, uint32_t flags, const float* w,
+                                   nx_graph** out) {
+  if (!out) return nx::invalid("nx_build_dsss: out is NULL");
+  *out = nullptr;
+  if (n == 0 || n > (1u << 30)) return nx::invalid("nx_build_dsss: n must be in [1, 2^30]");
+  if (P == 0 || P > n || P > 1024)
+    return nx::invalid("nx_build_dsss: P must be in [1, min(n, 1024)]");
+  if (m >= (1ull << 32)) return nx::invalid("nx_build_dsss: m must be < 2^32");
+  if (m && (!src || !dst)) return nx::invalid("nx_build_dsss: src/dst is NULL");
+  if ((flags & NX_WITH_WEIGHTS) && m && !w)
+    return nx::invalid("nx_build_dsss: NX_WITH_WEIGHTS needs w");
+  nx_graph* g = new (std::nothrow) nx_graph();
+  if (!g) return nx::invalid("nx_build_dsss: out of host memory");
+  nx_status st = nx::build_impl(src, dst, m, n, P, flags, w, g);
+  if (st != NX_OK) {
+    cudaStreamSynchronize(nx::stream());
+    delete g;
+    return st;
+  }
+  *out = g;
+  return NX_OK;
+}

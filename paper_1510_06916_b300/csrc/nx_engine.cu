@@ -1,0 +1,658 @@
+// Update engine (Section III-B): Initialize, the per-iteration schedules of
+// SPU / DPU / MPU (Algorithms 5-7), activity-driven termination (Algorithm 1),
+// value access, and the I/O model of Table II.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "nx_sweep.cuh"
+
+namespace nx {
+namespace {
+
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------- init kernels
+__global__ void k_init_pr(uint32_t n, const float* __restrict__ tele, const float* __restrict__ rin,
+                          const uint32_t* __restrict__ outdeg, float* __restrict__ r,
+                          float* __restrict__ c, double* __restrict__ part) {
+  __shared__ double red[8];
+  double s = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    float rv = rin ? rin[v] : (tele ? tele[v] : 1.0f / (float)n);
+    r[v] = rv;
+    uint32_t od = outdeg[v];
+    if (c) c[v] = od ? rv / (float)od : 0.0f;
+    if (od == 0) s += (double)rv;
+  }
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, uint32_t k, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (uint32_t q = 0; q < k; ++q) t += part[q];
+    *out = t;
+  }
+}
+
+__global__ void k_init_min(uint32_t n, int bfs, uint32_t root, uint32_t* __restrict__ v) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
+    v[x] = bfs ? (x == root ? 0u : kInf) : (uint32_t)x;
+}
+
+unsigned grid_for(uint64_t work) {
+  uint64_t b = ceil_div(work ? work : 1, 256);
+  return (unsigned)std::min<uint64_t>(b, (uint64_t)num_sms() * 8);
+}
+
+ProgKind kind_of(nx_program p) {
+  switch (p) {
+    case NX_WPR: return PK_WPR;
+    case NX_BFS: return PK_BFS;
+    case NX_WCC: return PK_WCC;
+    default: return PK_PR;
+  }
+}
+bool is_min(nx_program p) { return p == NX_BFS || p == NX_WCC; }
+
+// ---------------------------------------------------------------- plans
+struct PlanOut {
+  std::vector<Item> items;
+  uint32_t slots = 0;
+};
+
+uint64_t piece_len(const nx_graph* g, const Dsss& d, uint32_t i, uint32_t t, uint32_t j) {
+  const auto& tb = g->geo.h_col_tb;
+  uint64_t pc = piece_index(g->geo.P, tb[j], tb[j + 1] - tb[j], i, t);
+  return d.h_piece_off[pc + 1] - d.h_piece_off[pc];
+}
+
+uint32_t col_of_tile(const nx_graph* g, uint32_t t) { return g->geo.h_tile_start[t] / g->geo.L; }
+
+uint64_t target_block_edges(uint64_t total) {
+  uint64_t e = total / ((uint64_t)num_sms() * 8);
+  return std::max<uint64_t>(4096, e);
+}
+
+// Tiles of columns [c0, c1), sweeping sources [i0, i1) over `ds`.
+void plan_tiles(const nx_graph* g, const std::vector<const Dsss*>& ds, uint32_t i0, uint32_t i1,
+                uint32_t c0, uint32_t c1, bool allow_split, uint64_t blk, PlanOut& out) {
+  const auto& tb = g->geo.h_col_tb;
+  std::vector<std::pair<uint64_t, Item>> tmp;
+  for (uint32_t j = c0; j < c1; ++j)
+    for (uint32_t t = tb[j]; t < tb[j + 1]; ++t) {
+      uint64_t cost = 0;
+      for (const Dsss* d : ds)
+        for (uint32_t i = i0; i < i1; ++i) cost += piece_len(g, *d, i, t, j);
+      uint32_t k = 1;
+      if (allow_split && cost > 2 * blk) k = (uint32_t)ceil_div(cost, blk);
+      for (uint32_t q = 0; q < k; ++q) {
+        Item it{};
+        it.tile = t;
+        it.nsplit = k;
+        it.slot = k > 1 ? out.slots : 0;
+        it.sub = q;
+        it.vbeg = cost * q / k;
+        it.vend = (q + 1 == k) ? ~0ull : cost * (q + 1) / k;
+        tmp.push_back({cost / k + 1, it});
+      }
+      if (k > 1) out.slots += k;
+    }
+  std::stable_sort(tmp.begin(), tmp.end(),
+                   [](const auto& a, const auto& b) { return a.first > b.first; });
+  for (auto& p : tmp) out.items.push_back(p.second);
+}
+
+// Single pieces (i, t) of row i for tiles of columns [c0, c1) (ToHub / row pass).
+void plan_row(const nx_graph* g, const Dsss& d, uint32_t i, uint32_t c0, uint32_t c1, uint64_t blk,
+              PlanOut& out) {
+  const auto& tb = g->geo.h_col_tb;
+  std::vector<std::pair<uint64_t, Item>> tmp;
+  for (uint32_t j = c0; j < c1; ++j)
+    for (uint32_t t = tb[j]; t < tb[j + 1]; ++t) {
+      uint64_t cost = piece_len(g, d, i, t, j);
+      if (!cost) continue;
+      uint32_t k = cost > 2 * blk ? (uint32_t)ceil_div(cost, blk) : 1;
+      for (uint32_t q = 0; q < k; ++q) {
+        Item it{};
+        it.tile = t;
+        it.nsplit = k;
+        it.slot = k > 1 ? out.slots : 0;
+        it.sub = q;
+        it.row = i;
+        it.vbeg = cost * q / k;
+        it.vend = (q + 1 == k) ? ~0ull : cost * (q + 1) / k;
+        tmp.push_back({cost / k + 1, it});
+      }
+      if (k > 1) out.slots += k;
+    }
+  std::stable_sort(tmp.begin(), tmp.end(),
+                   [](const auto& a, const auto& b) { return a.first > b.first; });
+  for (auto& p : tmp) out.items.push_back(p.second);
+}
+
+// ---------------------------------------------------------------- buffers
+nx_status ensure(DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return NX_OK;
+  return b.alloc(bytes);
+}
+
+// Scalar slots (doubles): [0..1] dangling mass ping-pong; u32 counters after.
+struct Scal {
+  double* dm;          // [2]
+  uint32_t* ticket;    // [1]
+  uint32_t* act_count; // [1]
+};
+Scal scal_of(nx_graph* g) {
+  Scal s;
+  s.dm = g->scal.as<double>();
+  s.ticket = reinterpret_cast<uint32_t*>(s.dm + 2);
+  s.act_count = s.ticket + 1;
+  return s;
+}
+
+nx_status prepare(nx_graph* g) {
+  const uint64_t n = g->geo.n;
+  for (int k = 0; k < 2; ++k) {
+    NX_TRY(ensure(g->val[k], n * 4));
+    NX_TRY(ensure(g->act[k], ((size_t)g->geo.P + 1) * 4));
+  }
+  if (!g->scal.p) {
+    NX_TRY(g->scal.alloc(64));
+    NX_CUDA(cudaMemsetAsync(g->scal.p, 0, 64, stream()));
+  }
+  if (!g->tile_part.p) NX_TRY(g->tile_part.alloc(((size_t)g->geo.ntiles + 1) * 8));
+  if (!g->tile_ticket.p) {
+    NX_TRY(g->tile_ticket.alloc(((size_t)g->geo.ntiles + 1) * 4));
+    NX_CUDA(cudaMemsetAsync(g->tile_ticket.p, 0, ((size_t)g->geo.ntiles + 1) * 4, stream()));
+  }
+  return NX_OK;
+}
+
+nx_status upload_items(nx_graph* g, const PlanOut& plan) {
+  NX_TRY(ensure(g->items, std::max<size_t>(plan.items.size(), 1) * sizeof(Item)));
+  if (!plan.items.empty())
+    NX_CUDA(cudaMemcpyAsync(g->items.p, plan.items.data(), plan.items.size() * sizeof(Item),
+                            cudaMemcpyHostToDevice, stream()));
+  const uint64_t need = (uint64_t)plan.slots * g->geo.tile_max * 8;  // hi + lo per slot
+  NX_TRY(ensure(g->split_buf, std::max<uint64_t>(need, 4)));
+  return NX_OK;
+}
+
+// ---------------------------------------------------------------- initialize
+nx_status initialize(nx_graph* g, nx_program prog, const nx_params& p, const float* tele,
+                     const void* resume) {
+  const uint32_t n = g->geo.n;
+  Scal sc = scal_of(g);
+  g->cur = 0;
+  if (!is_min(prog)) {
+    const bool need_c = prog != NX_WPR;
+    if (need_c) {
+      NX_TRY(ensure(g->aux[0], (size_t)n * 4));
+      NX_TRY(ensure(g->aux[1], (size_t)n * 4));
+    }
+    const unsigned gb = grid_for(n);
+    DevBuf part;
+    NX_TRY(part.alloc((size_t)gb * 8));
+    const float* r0_tele = (prog == NX_PPR) ? tele : nullptr;  // PPR: r0 = t
+    k_init_pr<<<gb, 256, 0, stream()>>>(n, r0_tele, static_cast<const float*>(resume),
+                                        g->outdeg.as<uint32_t>(), g->val[0].as<float>(),
+                                        need_c ? g->aux[0].as<float>() : nullptr, part.as<double>());
+    NX_LAUNCH_CHECK();
+    k_sum_parts<<<1, 32, 0, stream()>>>(part.as<double>(), gb, sc.dm);
+    NX_LAUNCH_CHECK();
+    NX_CUDA(cudaStreamSynchronize(stream()));
+  } else {
+    const uint32_t P = g->geo.P;
+    std::vector<uint32_t> a0(P + 1, 0);
+    if (resume) {
+      NX_CUDA(cudaMemcpyAsync(g->val[0].p, resume, (size_t)n * 4, cudaMemcpyDeviceToDevice,
+                              stream()));
+      std::fill(a0.begin(), a0.begin() + P, 1u);
+    } else {
+      k_init_min<<<grid_for(n), 256, 0, stream()>>>(n, prog == NX_BFS, p.root,
+                                                     g->val[0].as<uint32_t>());
+      NX_LAUNCH_CHECK();
+      if (prog == NX_BFS) a0[p.root / g->geo.L] = 1u;
+      else std::fill(a0.begin(), a0.begin() + P, 1u);
+    }
+    NX_CUDA(cudaMemcpyAsync(g->act[0].p, a0.data(), (P + 1) * 4, cudaMemcpyHostToDevice, stream()));
+    NX_CUDA(cudaMemsetAsync(g->act[1].p, 0, (P + 1) * 4, stream()));
+    NX_CUDA(cudaStreamSynchronize(stream()));
+  }
+  return NX_OK;
+}
+
+// ---------------------------------------------------------------- common args
+SweepArgs base_args(nx_graph* g, nx_program prog, const nx_params& p, const float* tele) {
+  SweepArgs a;
+  const bool tr = (prog == NX_WCC);
+  a.src[0].ew = g->fwd.ew.as<uint32_t>();
+  a.src[0].wt = g->fwd.wt.as<float>();
+  a.src[0].piece_off = g->fwd.piece_off.as<uint64_t>();
+  a.nsrc = 1;
+  if (tr) {
+    a.src[1].ew = g->tr.ew.as<uint32_t>();
+    a.src[1].wt = g->tr.wt.as<float>();
+    a.src[1].piece_off = g->tr.piece_off.as<uint64_t>();
+    a.nsrc = 2;
+  }
+  a.tile_start = g->geo.tile_start.as<uint32_t>();
+  a.col_tb = g->geo.col_tb.as<uint32_t>();
+  a.P = g->geo.P;
+  a.L = g->geo.L;
+  a.lb = g->geo.lb;
+  a.n = g->geo.n;
+  a.tile_max = g->geo.tile_max;
+  a.outdeg = g->outdeg.as<uint32_t>();
+  a.tele = (prog == NX_PPR || prog == NX_WPR) ? tele : nullptr;
+  a.dang_by_tele = (prog == NX_PPR) ? 1 : 0;
+  a.alpha = p.alpha;
+  a.tile_part = g->tile_part.as<double>();
+  Scal sc = scal_of(g);
+  a.ticket = sc.ticket;
+  a.act_count = sc.act_count;
+  a.split = g->split_buf.p;
+  a.tile_ticket = g->tile_ticket.as<uint32_t>();
+  a.n_epi = g->geo.ntiles;
+  a.src_lo = 0;
+  a.src_hi = g->geo.P;
+  a.hub_off = g->fwd.hub_off.as<uint64_t>();
+  a.hub_dst = g->fwd.hub_dst.as<uint16_t>();
+  return a;
+}
+
+void set_iter_ptrs(nx_graph* g, nx_program prog, SweepArgs& a) {
+  const int c = g->cur, n = 1 - g->cur;
+  Scal sc = scal_of(g);
+  a.gsrc = (prog == NX_WPR || is_min(prog)) ? g->val[c].p : g->aux[c].p;
+  a.vold = g->val[c].p;
+  a.vnew = g->val[n].p;
+  a.cnew = (prog == NX_PR || prog == NX_PPR) ? g->aux[n].as<float>() : nullptr;
+  a.dm_in = sc.dm + c;
+  a.dm_out = sc.dm + n;
+  if (is_min(prog)) {
+    a.act_in = g->act[c].as<uint32_t>();
+    a.act_out = g->act[n].as<uint32_t>();
+  } else {
+    a.act_in = nullptr;
+    a.act_out = nullptr;
+  }
+}
+
+uint64_t bytes_per_sweep(const nx_graph* g, nx_program prog, uint64_t edges) {
+  const uint64_t n = g->geo.n;
+  uint64_t b = 4 * edges;             // edge words
+  if (prog == NX_WPR) b += 4 * edges;  // weights
+  if (is_min(prog)) b += 12 * n;       // gather-read, previous, new
+  else b += 16 * n;                    // gather-read c (r), write r, write c (tele), outdeg
+  return b;
+}
+
+// One SPU iteration: every tile of every column in one launch (Algorithm 5;
+// the order of sub-shards does not matter in SPU, Section III-B1).
+nx_status spu_iteration(nx_graph* g, nx_program prog, SweepArgs& a, uint32_t nitems) {
+  set_iter_ptrs(g, prog, a);
+  a.mode = 0;
+  NX_TRY(launch_sweep(kind_of(prog), a, nitems, stream()));
+  g->cur ^= 1;
+  return NX_OK;
+}
+
+// One DPU iteration (Algorithm 6): ToHub over every piece (row-major items),
+// then FromHub + epilogue per destination tile.
+nx_status dpu_iteration(nx_graph* g, nx_program prog, SweepArgs& a, uint32_t n_tohub,
+                        uint32_t n_fromhub) {
+  set_iter_ptrs(g, prog, a);
+  const Item* all = g->items.as<Item>();
+  SweepArgs th = a;
+  th.mode = 1;
+  th.q_res = 0;
+  th.items = all;
+  th.hubs = g->hubs.p;
+  NX_TRY(launch_sweep(kind_of(prog), th, n_tohub, stream()));
+  SweepArgs fh = a;
+  fh.mode = 0;
+  fh.items = all + n_tohub;
+  fh.src_lo = fh.src_hi = 0;
+  fh.hub_lo = 0;
+  fh.hub_hi = g->geo.P;
+  fh.hubs = g->hubs.p;
+  NX_TRY(launch_sweep(kind_of(prog), fh, n_fromhub, stream()));
+  g->cur ^= 1;
+  return NX_OK;
+}
+
+nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t iters,
+                   nx_strategy strategy, uint64_t budget, nx_run_stats* st) {
+  const uint32_t n = g->geo.n, P = g->geo.P;
+  if (prog == NX_WCC && !g->has_tr)
+    return invalid("nx_run: WCC needs the transpose DSSS (build with NX_WITH_TRANSPOSE)");
+  if (prog == NX_WPR && !g->has_w) return invalid("nx_run: WPR needs NX_WITH_WEIGHTS");
+  if (prog == NX_BFS && p.root >= n) return invalid("nx_run: BFS root >= n");
+  if (prog == NX_WCC && strategy == NX_DPU) {
+    // hubs hold one DSSS; WCC sweeps two (forward + transpose)
+    return invalid("nx_run: DPU/MPU hubs support single-DSSS programs (PR, PPR, WPR, BFS)");
+  }
+  // strategy from the budget (Section III-B3: Q <= B_M P / (2 n B_a))
+  const double Ba = 4.0;
+  uint32_t Q = P;
+  if (budget) Q = (uint32_t)std::min<double>(P, std::floor((double)budget * P / (2.0 * n * Ba)));
+  nx_strategy strat = strategy;
+  if (strat == NX_AUTO) strat = (Q >= P) ? NX_SPU : NX_MPU;
+  if (strat == NX_SPU && Q < P) {
+    set_error("nx_run: SPU needs 2 n B_a bytes of budget for the ping-pong intervals");
+    return NX_ERR_BUDGET_TOO_SMALL;
+  }
+  if (strat == NX_MPU && Q >= P) strat = NX_SPU;  // Q = P: MPU is SPU (Section III-B3)
+  if (strat == NX_MPU) {
+    set_error("nx_run: MPU with Q < P is not available in this build");
+    return NX_ERR_INVALID_ARG;
+  }
+  if (strat == NX_MPU && prog == NX_WCC)
+    return invalid("nx_run: DPU/MPU hubs support single-DSSS programs (PR, PPR, WPR, BFS)");
+
+  NX_TRY(prepare(g));
+  // teleport
+  const float* tele = nullptr;
+  if ((prog == NX_PPR || prog == NX_WPR) && p.teleport) {
+    if (p.teleport_is_device) {
+      tele = p.teleport;
+    } else {
+      NX_TRY(ensure(g->tele, (size_t)n * 4));
+      NX_CUDA(cudaMemcpyAsync(g->tele.p, p.teleport, (size_t)n * 4, cudaMemcpyHostToDevice,
+                              stream()));
+      tele = g->tele.as<float>();
+    }
+  }
+  if (prog == NX_PPR && !tele) {  // uniform teleport: PPR equals PageRank
+    NX_TRY(ensure(g->tele, (size_t)n * 4));
+    std::vector<float> u(n, 1.0f / (float)n);
+    NX_CUDA(cudaMemcpyAsync(g->tele.p, u.data(), (size_t)n * 4, cudaMemcpyHostToDevice, stream()));
+    NX_CUDA(cudaStreamSynchronize(stream()));
+    tele = g->tele.as<float>();
+  }
+  // initialize or resume
+  const bool resume = (g->values_set_for == (int)prog);
+  if (resume) {
+    // the resumed values sit in val[cur]; move them to val[0] through the init path
+    DevBuf tmp;
+    NX_TRY(tmp.alloc((size_t)n * 4));
+    NX_CUDA(cudaMemcpyAsync(tmp.p, g->val[g->cur].p, (size_t)n * 4, cudaMemcpyDeviceToDevice,
+                            stream()));
+    NX_TRY(initialize(g, prog, p, tele, tmp.p));
+  } else {
+    NX_TRY(initialize(g, prog, p, tele, nullptr));
+  }
+  g->values_set_for = -1;
+  g->last_prog = (int)prog;
+
+  // plan
+  std::vector<const Dsss*> ds{&g->fwd};
+  if (prog == NX_WCC) ds.push_back(&g->tr);
+  const uint64_t total = g->m * ds.size();
+  const uint64_t blk = target_block_edges(total);
+  PlanOut plan;
+  uint32_t n_a = 0, n_b = 0;
+  if (strat == NX_SPU) {
+    plan_tiles(g, ds, 0, P, 0, P, true, blk, plan);
+    n_a = (uint32_t)plan.items.size();
+  } else {  // DPU: ToHub items (all rows), then FromHub tiles
+    for (uint32_t i = 0; i < P; ++i) plan_row(g, g->fwd, i, 0, P, blk, plan);
+    n_a = (uint32_t)plan.items.size();
+    plan_tiles(g, ds, 0, 0, 0, P, false, blk, plan);
+    n_b = (uint32_t)plan.items.size() - n_a;
+    NX_TRY(ensure(g->hubs, std::max<uint64_t>(g->fwd.D, 1) * 4));
+  }
+  NX_TRY(upload_items(g, plan));
+  SweepArgs a = base_args(g, prog, p, tele);
+  a.items = g->items.as<Item>();
+  a.split = g->split_buf.p;
+
+  // per-interval edge counts (edges streamed by a sweep of active sources)
+  std::vector<uint64_t> row_edges(P, 0);
+  for (uint32_t j = 0; j < P; ++j) {
+    const auto& tb = g->geo.h_col_tb;
+    const uint32_t nt = tb[j + 1] - tb[j];
+    if (nt == 0) continue;  // empty trailing interval
+    for (uint32_t i = 0; i < P; ++i)
+      for (const Dsss* d : ds) {
+        uint64_t p0 = d->h_piece_off[piece_index(P, tb[j], nt, i, tb[j])];
+        uint64_t p1 = d->h_piece_off[piece_index(P, tb[j], nt, i, tb[j + 1] - 1) + 1];
+        row_edges[i] += p1 - p0;
+      }
+  }
+
+  cudaEvent_t e0, e1;
+  NX_CUDA(cudaEventCreate(&e0));
+  NX_CUDA(cudaEventCreate(&e1));
+  Scal sc = scal_of(g);
+  uint64_t swept = 0, d2h = 0;
+  uint32_t done = 0;
+  std::vector<uint32_t> act_h(P + 1, 1);
+  NX_CUDA(cudaEventRecord(e0, stream()));
+  for (uint32_t it = 0; it < iters; ++it) {
+    if (is_min(prog)) {
+      NX_CUDA(cudaMemcpyAsync(act_h.data(), g->act[g->cur].p, (size_t)P * 4,
+                              cudaMemcpyDeviceToHost, stream()));
+      NX_CUDA(cudaStreamSynchronize(stream()));
+      d2h += (uint64_t)P * 4;
+    }
+    for (uint32_t i = 0; i < P; ++i)
+      if (act_h[i]) swept += row_edges[i];
+    if (strat == NX_SPU) NX_TRY(spu_iteration(g, prog, a, n_a));
+    else NX_TRY(dpu_iteration(g, prog, a, n_a, n_b));
+    ++done;
+    if (is_min(prog)) {
+      uint32_t cnt = 0;
+      NX_CUDA(cudaMemcpyAsync(&cnt, sc.act_count, 4, cudaMemcpyDeviceToHost, stream()));
+      NX_CUDA(cudaStreamSynchronize(stream()));
+      d2h += 4;
+      if (cnt == 0) break;
+    }
+  }
+  NX_CUDA(cudaEventRecord(e1, stream()));
+  NX_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  NX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) {
+    memset(st, 0, sizeof *st);
+    st->iters_done = done;
+    st->Q = strat == NX_SPU ? P : (strat == NX_DPU ? 0 : Q);
+    st->strategy = (uint32_t)strat;
+    st->ms = ms;
+    st->edges_swept = swept;
+    st->bytes_model = 0;
+    // algorithmic bytes: edges streamed plus per-vertex traffic of each sweep
+    st->bytes_model = bytes_per_sweep(g, prog, 0) * done + 4 * swept +
+                      (prog == NX_WPR ? 4 * swept : 0);
+    if (strat == NX_DPU) st->bytes_model += (uint64_t)done * 3 * 4 * g->fwd.D;
+    st->d2h_bytes = d2h;
+    st->launches = done * (strat == NX_DPU ? 2u : 1u);
+  }
+  return NX_OK;
+}
+
+}  // namespace
+}  // namespace nx
+
+// ---------------------------------------------------------------- C ABI
+extern "C" nx_status nx_graph_get_info(const nx_graph* g, nx_graph_info* info) {
+  if (!g || !info) return nx::invalid("nx_graph_get_info: NULL argument");
+  memset(info, 0, sizeof *info);
+  info->n = g->geo.n;
+  info->P = g->geo.P;
+  info->L = g->geo.L;
+  info->ntiles = g->geo.ntiles;
+  info->tile_max = g->geo.tile_max;
+  info->lb = g->geo.lb;
+  info->m = g->m;
+  info->D = g->fwd.D;
+  info->D_t = g->has_tr ? g->tr.D : 0;
+  info->device_bytes = g->device_bytes();
+  info->build_ms = g->build_ms;
+  info->has_transpose = g->has_tr;
+  info->has_weights = g->has_w;
+  return NX_OK;
+}
+
+extern "C" nx_status nx_run(nx_graph* g, nx_program program, const nx_params* params,
+                            uint32_t iters, nx_strategy strategy, uint64_t mem_budget_bytes,
+                            nx_run_stats* stats) {
+  if (!g) return nx::invalid("nx_run: graph is NULL");
+  if ((int)program < 0 || (int)program > 4) return nx::invalid("nx_run: unknown program");
+  if ((int)strategy < 0 || (int)strategy > 3) return nx::invalid("nx_run: unknown strategy");
+  nx_params p{};
+  p.alpha = 0.85f;
+  if (params) p = *params;
+  if (!(p.alpha >= 0.f && p.alpha < 1.f)) return nx::invalid("nx_run: alpha must be in [0, 1)");
+  return nx::run_impl(g, program, p, iters, strategy, mem_budget_bytes, stats);
+}
+
+extern "C" nx_status nx_get_values(const nx_graph* g, void* out, uint64_t count,
+                                   int32_t out_is_device) {
+  if (!g || !out) return nx::invalid("nx_get_values: NULL argument");
+  if (count != g->geo.n) return nx::invalid("nx_get_values: count must equal n");
+  if (g->last_prog < 0 && g->values_set_for < 0) return nx::invalid("nx_get_values: nothing run yet");
+  NX_CUDA(cudaMemcpyAsync(out, g->val[g->cur].p, count * 4,
+                          out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          nx::stream()));
+  NX_CUDA(cudaStreamSynchronize(nx::stream()));
+  return NX_OK;
+}
+
+extern "C" nx_status nx_set_values(nx_graph* g, nx_program program, const void* in, uint64_t count,
+                                   int32_t in_is_device) {
+  if (!g || !in) return nx::invalid("nx_set_values: NULL argument");
+  if (count != g->geo.n) return nx::invalid("nx_set_values: count must equal n");
+  if ((int)program < 0 || (int)program > 4) return nx::invalid("nx_set_values: unknown program");
+  NX_TRY(nx::prepare(g));
+  NX_CUDA(cudaMemcpyAsync(g->val[g->cur].p, in, count * 4,
+                          in_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          nx::stream()));
+  NX_CUDA(cudaStreamSynchronize(nx::stream()));
+  g->values_set_for = (int)program;
+  g->last_prog = (int)program;
+  return NX_OK;
+}
+
+extern "C" void nx_graph_free(nx_graph* g) {
+  if (!g) return;
+  cudaStreamSynchronize(nx::stream());
+  if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  delete g;
+}
+
+extern "C" nx_status nx_io_model(nx_strategy s, double n, double m, double P, double B_M,
+                                 double B_a, double B_v, double B_e, double d, double* Q,
+                                 double* bytes_read, double* bytes_write) {
+  if (n <= 0 || P <= 0 || B_a <= 0 || d <= 0) return nx::invalid("nx_io_model: bad sizes");
+  double q = std::min(P, std::floor(B_M * P / (2.0 * n * B_a)));
+  double rd = 0, wr = 0;
+  switch (s) {
+    case NX_SPU:  // Section III-B1: B_read = m B_e + 2 n B_a - B_M (>= 0), no writes
+      q = P;
+      rd = std::max(0.0, m * B_e + 2.0 * n * B_a - B_M);
+      wr = 0;
+      break;
+    case NX_DPU:  // Section III-B2
+      q = 0;
+      rd = m * (B_e + (B_a + B_v) / d) + n * B_a;
+      wr = m * (B_a + B_v) / d + n * B_a;
+      break;
+    case NX_MPU:
+    case NX_AUTO: {  // Section III-B3 (sub-shards of equal size)
+      if (q < 0) q = 0;
+      // Table II form: the hubbed (P-Q)^2 sub-shards carry (B_a + B_v)/d per edge
+      const double f = (P - q) / P;
+      rd = m * (B_e + f * f * (B_a + B_v) / d) + f * n * B_a;
+      wr = f * f * m * (B_a + B_v) / d + f * n * B_a;
+      break;
+    }
+  }
+  if (Q) *Q = q;
+  if (bytes_read) *bytes_read = rd;
+  if (bytes_write) *bytes_write = wr;
+  return NX_OK;
+}
+
+
+namespace nx {
+namespace {
+// Decodes stored edge words back to endpoints (tile geometry + piece table).
+__global__ void k_export(const uint32_t* __restrict__ ew, const uint64_t* __restrict__ piece_off,
+                         const uint32_t* __restrict__ tile_start, const uint32_t* __restrict__ col_tb,
+                         uint32_t P, uint32_t L, uint32_t lb, uint64_t npieces,
+                         uint32_t* __restrict__ s_out, uint32_t* __restrict__ d_out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t pc = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; pc < npieces; pc += stride) {
+    // invert piece_index: column j from the tile prefix, then (i, t)
+    uint32_t lo = 0, hi = P;  // find j with P*tb[j] <= pc < P*tb[j+1]
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) / 2;
+      if ((uint64_t)P * col_tb[mid] <= pc) lo = mid; else hi = mid;
+    }
+    const uint32_t j = lo, tb = col_tb[j], nt = col_tb[j + 1] - tb;
+    if (nt == 0) continue;
+    const uint64_t r = pc - (uint64_t)P * tb;
+    const uint32_t i = (uint32_t)(r / nt), t = tb + (uint32_t)(r % nt);
+    const uint32_t mask = (1u << lb) - 1u;
+    for (uint64_t e = piece_off[pc]; e < piece_off[pc + 1]; ++e) {
+      const uint32_t w = ew[e];
+      s_out[e] = i * L + (w & mask);
+      d_out[e] = tile_start[t] + (w >> lb);
+    }
+  }
+}
+}  // namespace
+}  // namespace nx
+
+extern "C" nx_status nx_dsss_export(const nx_graph* g, int32_t transpose, uint32_t* src,
+                                    uint32_t* dst, uint64_t* sub_off) {
+  if (!g || !src || !dst) return nx::invalid("nx_dsss_export: NULL argument");
+  if (transpose && !g->has_tr) return nx::invalid("nx_dsss_export: no transpose DSSS");
+  const nx::Dsss& d = transpose ? g->tr : g->fwd;
+  const uint64_t m = g->m, np = (uint64_t)g->geo.P * g->geo.ntiles;
+  nx::DevBuf s, t;
+  NX_TRY(s.alloc(std::max<uint64_t>(m, 1) * 4));
+  NX_TRY(t.alloc(std::max<uint64_t>(m, 1) * 4));
+  nx::k_export<<<nx::grid_for(np), 256, 0, nx::stream()>>>(
+      d.ew.as<uint32_t>(), d.piece_off.as<uint64_t>(), g->geo.tile_start.as<uint32_t>(),
+      g->geo.col_tb.as<uint32_t>(), g->geo.P, g->geo.L, g->geo.lb, np, s.as<uint32_t>(),
+      t.as<uint32_t>());
+  NX_LAUNCH_CHECK();
+  // the transpose stores (original dst, original src): swap back
+  uint32_t* so = transpose ? dst : src;
+  uint32_t* dout = transpose ? src : dst;
+  if (m) {
+    NX_CUDA(cudaMemcpyAsync(so, s.p, m * 4, cudaMemcpyDeviceToHost, nx::stream()));
+    NX_CUDA(cudaMemcpyAsync(dout, t.p, m * 4, cudaMemcpyDeviceToHost, nx::stream()));
+  }
+  NX_CUDA(cudaStreamSynchronize(nx::stream()));
+  if (sub_off) {
+    const uint32_t P = g->geo.P;
+    const auto& tb = g->geo.h_col_tb;
+    for (uint32_t j = 0; j < P; ++j)
+      for (uint32_t i = 0; i < P; ++i) {
+        const uint32_t nt = tb[j + 1] - tb[j];
+        sub_off[(uint64_t)j * P + i] =
+            nt ? d.h_piece_off[nx::piece_index(P, tb[j], nt, i, tb[j])]
+               : d.h_piece_off[(uint64_t)P * tb[j]];
+      }
+    sub_off[(uint64_t)P * P] = m;
+  }
+  return NX_OK;
+}

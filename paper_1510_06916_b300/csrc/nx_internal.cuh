@@ -1,0 +1,160 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/nxgraph.h"
+
+namespace nx {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+const char* get_error();
+
+struct Status {
+  nx_status code = NX_OK;
+  bool ok() const { return code == NX_OK; }
+};
+
+#define NX_TRY(expr)                    \
+  do {                                  \
+    nx_status _s = (expr);              \
+    if (_s != NX_OK) return _s;         \
+  } while (0)
+
+nx_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+#define NX_CUDA(call)                                                  \
+  do {                                                                 \
+    cudaError_t _e = (call);                                           \
+    if (_e != cudaSuccess) return nx::cuda_fail(_e, #call, __FILE__, __LINE__); \
+  } while (0)
+#define NX_LAUNCH_CHECK() NX_CUDA(cudaGetLastError())
+
+nx_status invalid(const std::string& msg);
+
+// ---------------------------------------------------------------- stream
+cudaStream_t stream();
+
+// ---------------------------------------------------------------- device buffers
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release();
+  nx_status alloc(size_t n);  // frees first; n == 0 allocates nothing
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct PinnedBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  PinnedBuf() = default;
+  PinnedBuf(const PinnedBuf&) = delete;
+  PinnedBuf& operator=(const PinnedBuf&) = delete;
+  ~PinnedBuf() { release(); }
+  void release();
+  nx_status alloc(size_t n);
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+inline uint32_t bits_for(uint64_t x) {  // bits to hold values in [0, x)
+  uint32_t b = 0;
+  while (b < 64 && (x - 1) >> b) ++b;
+  return x <= 1 ? 0 : b;
+}
+inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+inline uint64_t round_up(uint64_t a, uint64_t b) { return ceil_div(a, b) * b; }
+
+int num_sms();
+
+// ---------------------------------------------------------------- primitives
+// Exclusive scan of in[0..n) into out[0..n); *total (device, nullable) gets the
+// sum. out may alias in. Scratch is allocated internally.
+nx_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* total);
+nx_status exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* total);
+// LSD radix sort of 64-bit keys over bits [0, key_bits), stable, with an
+// optional uint32 payload. keys/vals are sorted in place (scratch internal).
+nx_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t n, uint32_t key_bits);
+
+// ---------------------------------------------------------------- DSSS
+// One destination-sorted structure over the graph's tile geometry. The
+// transpose DSSS is the same structure built with source and destination
+// swapped (its "destination" is the original source).
+struct Dsss {
+  uint64_t m = 0;
+  DevBuf ew;         // uint32 [round_up(m,8)+8]: ((dst - tile_start) << lb) | src_local
+  DevBuf wt;         // float  [same]: normalised weight of each edge (weighted graphs)
+  DevBuf piece_off;  // uint64 [npieces+1]
+  DevBuf hub_off;    // uint64 [npieces+1]: hub entries before each piece
+  DevBuf hub_dst;    // uint16 [D]: destination offset in its tile of each hub entry
+  uint64_t D = 0;
+  std::vector<uint64_t> h_piece_off;
+  // Pinned host copy of the edge words of streamed shards (MPU / budgets).
+  PinnedBuf h_ew;    // holds words [h_ew_first, m) (rounded to 8)
+  uint64_t h_ew_first = 0;
+  uint32_t dev_cols = 0;  // shards [0, dev_cols) are held on the device
+};
+
+struct Geometry {
+  uint32_t n = 0, P = 0, L = 0, lb = 0, tile_max = 0, ntiles = 0;
+  DevBuf tile_start;  // uint32 [ntiles+1]
+  DevBuf col_tb;      // uint32 [P+1]: first tile of each column
+  std::vector<uint32_t> h_tile_start, h_col_tb;
+};
+
+// Piece (i, t) of tile t in column j: P*tb_j + i*nt_j + (t - tb_j).
+__host__ __device__ inline uint64_t piece_index(uint32_t P, uint32_t tb_j, uint32_t nt_j,
+                                                uint32_t i, uint32_t t) {
+  return (uint64_t)P * tb_j + (uint64_t)i * nt_j + (t - tb_j);
+}
+
+}  // namespace nx
+
+// ---------------------------------------------------------------- the graph
+struct nx_graph {
+  uint64_t m = 0;
+  nx::Geometry geo;
+  nx::Dsss fwd, tr;
+  bool has_tr = false, has_w = false;
+  nx::DevBuf outdeg;   // uint32 [n]
+  nx::DevBuf wsum;     // float [n]  W_u (weighted)
+  nx::DevBuf orig_src, orig_dst;  // uint32 [m] caller order (weighted: edge grads)
+  float build_ms = 0.f;
+  // values
+  int last_prog = -1;
+  int values_set_for = -1;  // program whose values were set by nx_set_values
+  nx::DevBuf val[2];        // ping-pong value arrays [n] (float or uint32)
+  nx::DevBuf aux[2];        // PR: contribution arrays c = r / outdeg
+  int cur = 0;              // index of the current values
+  nx::DevBuf act[2];        // uint32 [P+1] interval activity (+ counter slot)
+  nx::DevBuf scal;          // doubles / counters used by the sweeps
+  nx::DevBuf tile_part;     // double [ntiles] per-tile dangling partials
+  nx::DevBuf split_buf;     // split-tile partial accumulators
+  nx::DevBuf tile_ticket;   // uint32 [ntiles]
+  nx::DevBuf items;         // work items of the current plan
+  nx::DevBuf hubs;          // hub values [D]
+  int plan_key = -1;
+  uint32_t nitems = 0;
+  uint64_t split_floats = 0;
+  nx::DevBuf tele;          // float [n] teleport copy (PPR/WPR)
+  nx::DevBuf lam[2], ybuf;  // adjoint scratch
+  nx::DevBuf stage[2];      // staging for streamed shards
+  nx::DevBuf vstage[2];     // staging for non-resident intervals (MPU)
+  nx::PinnedBuf hval[2];    // pinned host values of non-resident intervals
+  nx::DevBuf accres;        // MPU resident-column accumulators
+  cudaGraphExec_t gexec = nullptr;
+  int gexec_key = -1;
+  uint32_t gexec_iters = 0;
+  uint64_t device_bytes() const;
+};

@@ -1,0 +1,315 @@
+// Error state, buffers, and the device-wide primitives the DSSS builder uses:
+// exclusive scans and a stable LSD radix sort of 64-bit keys. All written for
+// this library (no CUB / Thrust).
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "nx_internal.cuh"
+
+namespace nx {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string t_err;
+void set_error(const std::string& msg) { t_err = msg; }
+const char* get_error() { return t_err.c_str(); }
+
+nx_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e),
+           what, file, line);
+  set_error(buf);
+  if (e == cudaErrorMemoryAllocation) return NX_ERR_OOM;
+  return NX_ERR_CUDA;
+}
+
+nx_status invalid(const std::string& msg) {
+  set_error(msg);
+  return NX_ERR_INVALID_ARG;
+}
+
+// ---------------------------------------------------------------- stream
+static cudaStream_t g_stream = nullptr;
+cudaStream_t stream() { return g_stream; }
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || !sms)
+      sms = 148;
+  }
+  return sms;
+}
+
+// ---------------------------------------------------------------- buffers
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+nx_status DevBuf::alloc(size_t n) {
+  release();
+  if (n == 0) return NX_OK;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    cudaGetLastError();
+    char buf[160];
+    snprintf(buf, sizeof buf, "device allocation of %zu bytes failed: %s", n,
+             cudaGetErrorString(e));
+    set_error(buf);
+    return NX_ERR_OOM;
+  }
+  bytes = n;
+  return NX_OK;
+}
+void PinnedBuf::release() {
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  bytes = 0;
+}
+nx_status PinnedBuf::alloc(size_t n) {
+  release();
+  if (n == 0) return NX_OK;
+  cudaError_t e = cudaMallocHost(&p, n);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    cudaGetLastError();
+    char buf[160];
+    snprintf(buf, sizeof buf, "pinned host allocation of %zu bytes failed: %s", n,
+             cudaGetErrorString(e));
+    set_error(buf);
+    return NX_ERR_OOM;
+  }
+  bytes = n;
+  return NX_OK;
+}
+
+// ---------------------------------------------------------------- scan
+namespace {
+constexpr int SC_THREADS = 256;
+constexpr int SC_ITEMS = 8;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+template <class T>
+__device__ T block_exclusive(T v, T* total) {
+  __shared__ T warp_tot[SC_THREADS / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    T t = lane < SC_THREADS / 32 ? warp_tot[lane] : T(0);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, t, d);
+      if (lane >= d) t += y;
+    }
+    if (lane < SC_THREADS / 32) warp_tot[lane] = t;
+  }
+  __syncthreads();
+  T before = (w > 0 ? warp_tot[w - 1] : T(0)) + x - v;
+  if (total) *total = warp_tot[SC_THREADS / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+template <class T>
+__global__ void scan_reduce(const T* in, uint64_t n, T* part) {
+  uint64_t base = (uint64_t)blockIdx.x * SC_TILE + (uint64_t)threadIdx.x * SC_ITEMS;
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < SC_ITEMS; ++k)
+    if (base + k < n) s += in[base + k];
+  T tot;
+  block_exclusive<T>(s, &tot);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+template <class T>
+__global__ void scan_tiles(const T* in, T* out, uint64_t n, const T* part_scanned, T* total) {
+  uint64_t base = (uint64_t)blockIdx.x * SC_TILE + (uint64_t)threadIdx.x * SC_ITEMS;
+  T v[SC_ITEMS];
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < SC_ITEMS; ++k) {
+    v[k] = base + k < n ? in[base + k] : T(0);
+    s += v[k];
+  }
+  T tot;
+  T run = block_exclusive<T>(s, &tot) + (part_scanned ? part_scanned[blockIdx.x] : T(0));
+#pragma unroll
+  for (int k = 0; k < SC_ITEMS; ++k)
+    if (base + k < n) {
+      out[base + k] = run;
+      run += v[k];
+    }
+  if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+    *total = (part_scanned ? part_scanned[blockIdx.x] : T(0)) + tot;
+}
+
+template <class T>
+nx_status exclusive_scan(const T* in, T* out, uint64_t n, T* total) {
+  if (n == 0) {
+    if (total) NX_CUDA(cudaMemsetAsync(total, 0, sizeof(T), stream()));
+    return NX_OK;
+  }
+  uint64_t nb = ceil_div(n, SC_TILE);
+  if (nb == 1) {
+    scan_tiles<T><<<1, SC_THREADS, 0, stream()>>>(in, out, n, nullptr, total);
+    NX_LAUNCH_CHECK();
+    return NX_OK;
+  }
+  DevBuf part;
+  NX_TRY(part.alloc(nb * sizeof(T)));
+  scan_reduce<T><<<(unsigned)nb, SC_THREADS, 0, stream()>>>(in, n, part.as<T>());
+  NX_LAUNCH_CHECK();
+  NX_TRY(exclusive_scan<T>(part.as<T>(), part.as<T>(), nb, nullptr));
+  scan_tiles<T><<<(unsigned)nb, SC_THREADS, 0, stream()>>>(in, out, n, part.as<T>(), total);
+  NX_LAUNCH_CHECK();
+  return NX_OK;
+}
+}  // namespace
+
+nx_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* total) {
+  return exclusive_scan<uint32_t>(in, out, n, total);
+}
+nx_status exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* total) {
+  return exclusive_scan<uint64_t>(in, out, n, total);
+}
+
+// ---------------------------------------------------------------- radix sort
+namespace {
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ROUNDS = 16;                     // keys per lane
+constexpr int RS_WARP_KEYS = 32 * RS_ROUNDS;      // 512
+constexpr int RS_TILE = RS_WARPS * RS_WARP_KEYS;  // 4096
+
+__global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint64_t* __restrict__ keys, uint64_t n,
+                                                      uint32_t shift, uint32_t* __restrict__ counts,
+                                                      uint32_t nb) {
+  __shared__ uint32_t h[RS_WARPS][256];
+  for (int k = threadIdx.x; k < RS_WARPS * 256; k += RS_THREADS) (&h[0][0])[k] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t base = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)w * RS_WARP_KEYS + lane;
+#pragma unroll 4
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    uint64_t idx = base + (uint64_t)r * 32;
+    if (idx < n) atomicAdd(&h[w][(uint32_t)(keys[idx] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < RS_WARPS; ++q) s += h[q][d];
+    counts[(uint64_t)d * nb + blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) rs_scatter(
+    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, uint64_t n, uint32_t shift, const uint32_t* __restrict__ offs,
+    uint32_t nb) {
+  __shared__ uint32_t wc[RS_WARPS][257];
+  for (int k = threadIdx.x; k < RS_WARPS * 257; k += RS_THREADS) (&wc[0][0])[k] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint64_t base = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)w * RS_WARP_KEYS + lane;
+  uint64_t key[RS_ROUNDS];
+  uint32_t rank[RS_ROUNDS];
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    uint64_t idx = base + (uint64_t)r * 32;
+    bool valid = idx < n;
+    key[r] = valid ? kin[idx] : 0ull;
+    uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = wc[w][d];
+    __syncwarp();
+    if ((peers & lt_mask) == 0) wc[w][d] = before + __popc(peers);
+    __syncwarp();
+    rank[r] = before + __popc(peers & lt_mask);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+    uint32_t s = offs[(uint64_t)d * nb + blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < RS_WARPS; ++q) {
+      uint32_t t = wc[q][d];
+      wc[q][d] = s;
+      s += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    uint64_t idx = base + (uint64_t)r * 32;
+    if (idx < n) {
+      uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+      uint32_t pos = wc[w][d] + rank[r];
+      kout[pos] = key[r];
+      if (vin) vout[pos] = vin[idx];
+    }
+  }
+}
+}  // namespace
+
+nx_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t n, uint32_t key_bits) {
+  if (n <= 1 || key_bits == 0) return NX_OK;
+  if (n >= (1ull << 32)) return invalid("radix_sort_u64: n must be < 2^32");
+  const uint32_t nb = (uint32_t)ceil_div(n, RS_TILE);
+  DevBuf k2, v2, counts;
+  NX_TRY(k2.alloc(n * sizeof(uint64_t)));
+  if (vals) NX_TRY(v2.alloc(n * sizeof(uint32_t)));
+  NX_TRY(counts.alloc((uint64_t)nb * 256 * sizeof(uint32_t)));
+  uint64_t* ka = keys;
+  uint64_t* kb = k2.as<uint64_t>();
+  uint32_t* va = vals;
+  uint32_t* vb = vals ? v2.as<uint32_t>() : nullptr;
+  int passes = 0;
+  for (uint32_t shift = 0; shift < key_bits; shift += 8, ++passes) {
+    rs_hist<<<nb, RS_THREADS, 0, stream()>>>(ka, n, shift, counts.as<uint32_t>(), nb);
+    NX_LAUNCH_CHECK();
+    NX_TRY(exclusive_scan_u32(counts.as<uint32_t>(), counts.as<uint32_t>(), (uint64_t)nb * 256,
+                              nullptr));
+    rs_scatter<<<nb, RS_THREADS, 0, stream()>>>(ka, va, kb, vb, n, shift, counts.as<uint32_t>(),
+                                                nb);
+    NX_LAUNCH_CHECK();
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (passes & 1) {  // result sits in the scratch buffers
+    NX_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream()));
+    if (vals)
+      NX_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream()));
+  }
+  // scratch is freed on return: make sure the stream is done with it
+  NX_CUDA(cudaStreamSynchronize(stream()));
+  return NX_OK;
+}
+
+}  // namespace nx
+
+extern "C" nx_status nx_set_stream(void* s) {
+  nx::g_stream = (cudaStream_t)s;
+  return NX_OK;
+}
+
+extern "C" void nx_last_error(char* buf, size_t len) {
+  if (!buf || !len) return;
+  const char* e = nx::get_error();
+  size_t k = strlen(e);
+  if (k >= len) k = len - 1;
+  memcpy(buf, e, k);
+  buf[k] = 0;
+}

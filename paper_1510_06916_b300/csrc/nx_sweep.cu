@@ -1,0 +1,402 @@
+// The DSSS update sweep (Section III-B, III-D) for sm_103a.
+//
+// A thread block owns one destination tile (a slice of a destination interval
+// I_j) and walks the tile's piece of every sub-shard SS_ij, i = 0..P-1. Each
+// warp takes 256 consecutive edge words per step (two 16-byte loads per lane),
+// gathers the source values, and reduces runs of equal destination first in
+// registers and then across lanes with a segmented shuffle scan. One shared-
+// memory atomic per destination run folds the run into the tile accumulator,
+// so there are no global atomics (Section III-D: a destination belongs to one
+// worker, sorted destinations make the reduction a segmented one). After the
+// last piece the block applies the program's epilogue to its tile
+// (InitializeIteration / Update of Algorithm 1, 5) and writes the new values.
+//
+// Tiles too heavy for one block are split over several blocks; each writes its
+// accumulator to a private slot and the last block to finish (a completion
+// counter) combines the slots in a fixed order, so results do not depend on
+// block scheduling except for the order of shared-memory atomics inside a block.
+#include "nx_sweep.cuh"
+
+namespace nx {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr uint32_t kSent = 0xFFFFFFFFu;  // run key of edges outside the range
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+
+// Tile accumulator in shared memory: hi[T] plus, for sums, lo[T] holding the
+// exact rounding error of every atomic add into hi (TwoSum, Knuth TAOCP vol. 2
+// 4.2.2), so long runs into one destination stay compensated.
+template <class V>
+struct Acc {
+  V* hi;
+  float* lo;
+};
+
+struct PrSum {  // PageRank family: compensated sum of float contributions
+  using V = float;
+  static constexpr bool compensated = true;
+  __device__ static V identity() { return 0.f; }
+  __device__ static V op(V a, V b) { return a + b; }
+  __device__ static void emit(Acc<V> acc, uint32_t k, V v) {
+    const float old = atomicAdd(acc.hi + k, v);
+    const float s = old + v;
+    const float bb = s - old;
+    const float err = (old - (s - bb)) + (v - bb);
+    if (err != 0.f) atomicAdd(acc.lo + k, err);
+  }
+  __device__ static V read(Acc<V> acc, uint32_t k) { return acc.hi[k] + acc.lo[k]; }
+  __device__ static void emit_global(V* p, V v) { *p += v; }
+};
+struct MinU {  // BFS / WCC: min of uint32
+  using V = uint32_t;
+  static constexpr bool compensated = false;
+  __device__ static V identity() { return kInf; }
+  __device__ static V op(V a, V b) { return a < b ? a : b; }
+  __device__ static void emit(Acc<V> acc, uint32_t k, V v) {
+    if (v != kInf) atomicMin(acc.hi + k, v);
+  }
+  __device__ static V read(Acc<V> acc, uint32_t k) { return acc.hi[k]; }
+  __device__ static void emit_global(V* p, V v) {
+    if (v < *p) *p = v;
+  }
+};
+
+template <int K>
+struct Prog;
+template <>
+struct Prog<PK_PR> : PrSum {  // gathers c[u] = r[u] / outdeg[u]
+  static constexpr bool weighted = false;
+  __device__ static float gather(const void* g, uint32_t u, float) {
+    return __ldg(static_cast<const float*>(g) + u);
+  }
+};
+template <>
+struct Prog<PK_WPR> : PrSum {  // gathers w^_uv r[u]
+  static constexpr bool weighted = true;
+  __device__ static float gather(const void* g, uint32_t u, float w) {
+    return w * __ldg(static_cast<const float*>(g) + u);
+  }
+};
+template <>
+struct Prog<PK_BFS> : MinU {  // depth[u] + 1 (infinity stays infinity)
+  static constexpr bool weighted = false;
+  __device__ static uint32_t gather(const void* g, uint32_t u, float) {
+    uint32_t d = __ldg(static_cast<const uint32_t*>(g) + u);
+    return d == kInf ? kInf : d + 1;
+  }
+};
+template <>
+struct Prog<PK_WCC> : MinU {  // label[u]
+  static constexpr bool weighted = false;
+  __device__ static uint32_t gather(const void* g, uint32_t u, float) {
+    return __ldg(static_cast<const uint32_t*>(g) + u);
+  }
+};
+
+__device__ __forceinline__ uint4 ld_stream(const uint32_t* p) {
+  return __ldcs(reinterpret_cast<const uint4*>(p));
+}
+__device__ __forceinline__ float4 ld_stream_f(const float* p) {
+  return __ldcs(reinterpret_cast<const float4*>(p));
+}
+
+// Folds edges [a, b) of one piece into the tile accumulator. Edge e is read at
+// ew[e - ew_lo]; its source value at g[sbase + src_local].
+template <class PG>
+__device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
+                                            const float* __restrict__ wt, uint64_t ew_lo,
+                                            uint64_t a, uint64_t b, const void* __restrict__ g,
+                                            uint32_t sbase, uint32_t lb,
+                                            Acc<typename PG::V> acc) {
+  using V = typename PG::V;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t smask = (1u << lb) - 1u;
+  const uint64_t a8 = a & ~7ull;
+  for (uint64_t base = a8 + (uint64_t)warp * 256; base < b; base += (uint64_t)kWarps * 256) {
+    const uint64_t p = base + (uint64_t)lane * 8;
+    uint32_t wv[8];
+    float wf[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      wv[k] = 0;
+      wf[k] = 0.f;
+    }
+    if (p < b) {
+      uint4 q0 = ld_stream(ew + (p - ew_lo)), q1 = ld_stream(ew + (p - ew_lo) + 4);
+      wv[0] = q0.x; wv[1] = q0.y; wv[2] = q0.z; wv[3] = q0.w;
+      wv[4] = q1.x; wv[5] = q1.y; wv[6] = q1.z; wv[7] = q1.w;
+      if (PG::weighted) {
+        float4 f0 = ld_stream_f(wt + (p - ew_lo)), f1 = ld_stream_f(wt + (p - ew_lo) + 4);
+        wf[0] = f0.x; wf[1] = f0.y; wf[2] = f0.z; wf[3] = f0.w;
+        wf[4] = f1.x; wf[5] = f1.y; wf[6] = f1.z; wf[7] = f1.w;
+      }
+    }
+    uint32_t key[8];
+    V val[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const bool valid = (p + k >= a) && (p + k < b);
+      key[k] = valid ? (wv[k] >> lb) : kSent;
+      val[k] = valid ? PG::gather(g, sbase + (wv[k] & smask), wf[k]) : PG::identity();
+    }
+    // runs of equal destination inside the lane: first (head), middle, last (tail)
+    uint32_t hk = key[0], ck = key[0];
+    V hs = val[0], cs = val[0];
+    bool single = true;
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+      if (key[k] == ck) {
+        cs = PG::op(cs, val[k]);
+      } else {
+        if (single) {
+          hk = ck;
+          hs = cs;
+          single = false;
+        } else if (ck != kSent) {
+          PG::emit(acc, ck, cs);
+        }
+        ck = key[k];
+        cs = val[k];
+      }
+    }
+    const uint32_t first_key = single ? ck : hk;
+    uint32_t prev_tail = __shfl_up_sync(0xffffffffu, ck, 1);
+    if (lane == 0) prev_tail = kSent;
+    uint32_t next_first = __shfl_down_sync(0xffffffffu, first_key, 1);
+    if (lane == 31) next_first = kSent;
+    // segmented inclusive scan of the tail runs across lanes
+    const bool starts = (lane == 0) || !single || (ck != prev_tail);
+    const uint32_t smask_b = __ballot_sync(0xffffffffu, starts);
+    const uint32_t le = smask_b & (0xffffffffu >> (31 - lane));
+    const int seg0 = 31 - __clz(le);
+    V x = cs;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      V y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane - d >= seg0) x = PG::op(y, x);
+    }
+    const V prev_x = __shfl_up_sync(0xffffffffu, x, 1);
+    if (!single && hk != kSent) PG::emit(acc, hk, (lane > 0 && hk == prev_tail) ? PG::op(prev_x, hs) : hs);
+    if (ck != kSent && next_first != ck) PG::emit(acc, ck, x);
+  }
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kWarps; ++q) t += red[q];
+  return t;  // valid in thread 0
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
+  using PG = Prog<K>;
+  using V = typename PG::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Acc<V> acc;
+  acc.hi = reinterpret_cast<V*>(smem_raw);
+  acc.lo = PG::compensated ? reinterpret_cast<float*>(smem_raw) + a.tile_max : nullptr;
+  __shared__ double red[kWarps];
+  __shared__ int s_flag;
+
+  const Item it = a.items[blockIdx.x];
+  const uint32_t t = it.tile;
+  const uint32_t ts = a.tile_start[t], te = a.tile_start[t + 1];
+  const uint32_t T = te - ts;
+  const uint32_t j = ts / a.L;
+  const uint32_t tb = a.col_tb[j], nt = a.col_tb[j + 1] - tb;
+
+  if (a.mode == 3) {  // epilogue from the stored accumulators of resident columns
+    const V* ar = static_cast<const V*>(a.accres);
+    for (uint32_t k = threadIdx.x; k < T; k += kThreads) acc.hi[k] = ar[ts + k];
+  } else {
+    for (uint32_t k = threadIdx.x; k < T; k += kThreads) acc.hi[k] = PG::identity();
+  }
+  if (PG::compensated)
+    for (uint32_t k = threadIdx.x; k < T; k += kThreads) acc.lo[k] = 0.f;
+  __syncthreads();
+
+  if (a.mode != 3) {
+    // edges: pieces (i, t) for i in [src_lo, src_hi) of every DSSS of the sweep
+    uint64_t vo = 0;
+    const uint32_t i_lo = a.mode == 1 ? it.row : a.src_lo;
+    const uint32_t i_hi = a.mode == 1 ? it.row + 1 : a.src_hi;
+    for (int s = 0; s < a.nsrc && vo < it.vend; ++s) {
+      const uint64_t* po = a.src[s].piece_off;
+      for (uint32_t i = i_lo; i < i_hi && vo < it.vend; ++i) {
+        const uint64_t pc = piece_index(a.P, tb, nt, i, t);
+        const uint64_t p0 = po[pc], len = po[pc + 1] - p0;
+        const uint64_t lo = vo > it.vbeg ? vo : it.vbeg;
+        const uint64_t hi = (vo + len) < it.vend ? (vo + len) : it.vend;
+        if (lo < hi && (!a.act_in || a.act_in[i])) {
+          const bool staged = (i == a.stage_i);
+          const void* g = staged ? a.gstage : a.gsrc;
+          const uint32_t sb = staged ? 0u : i * a.L;
+          sweep_range<PG>(a.src[s].ew, a.src[s].wt, a.ew_lo[s], p0 + (lo - vo), p0 + (hi - vo), g,
+                          sb, a.lb, acc);
+        }
+        vo += len;
+      }
+    }
+    // FromHub (Algorithm 6, 7): fold hub entries of pieces (i, t), i in [hub_lo, hub_hi)
+    if (a.mode == 0 && it.sub == 0 && a.hub_lo < a.hub_hi) {
+      const V* hv = static_cast<const V*>(a.hubs);
+      for (uint32_t i = a.hub_lo; i < a.hub_hi; ++i) {
+        if (a.act_in && !a.act_in[i]) continue;
+        const uint64_t pc = piece_index(a.P, tb, nt, i, t);
+        const uint64_t h0 = a.hub_off[pc], h1 = a.hub_off[pc + 1];
+        for (uint64_t k = h0 + threadIdx.x; k < h1; k += kThreads) PG::emit(acc, a.hub_dst[k], hv[k]);
+      }
+    }
+    __syncthreads();
+
+    if (it.nsplit > 1) {  // combine the blocks of a split tile in slot order
+      // slot q holds hi[tile_max] (+ lo[tile_max] for sums)
+      const uint64_t slot_len = (uint64_t)a.tile_max * (PG::compensated ? 2 : 1);
+      V* sp = static_cast<V*>(a.split);
+      V* mine = sp + (uint64_t)(it.slot + it.sub) * slot_len;
+      for (uint32_t k = threadIdx.x; k < T; k += kThreads) {
+        mine[k] = acc.hi[k];
+        if (PG::compensated) reinterpret_cast<float*>(mine)[a.tile_max + k] = acc.lo[k];
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_flag = (atomicAdd(&a.tile_ticket[t], 1u) == it.nsplit - 1);
+      __syncthreads();
+      if (!s_flag) return;
+      __threadfence();
+      if (threadIdx.x == 0) a.tile_ticket[t] = 0;
+      for (uint32_t k = threadIdx.x; k < T; k += kThreads) {
+        if constexpr (PG::compensated) {
+          double v = 0.0;  // fixed slot order, double precision
+          for (uint32_t q = 0; q < it.nsplit; ++q) {
+            const float* sq = reinterpret_cast<const float*>(sp + (uint64_t)(it.slot + q) * slot_len);
+            v += (double)__ldcg(sq + k) + (double)__ldcg(sq + a.tile_max + k);
+          }
+          const float hi = (float)v;
+          acc.hi[k] = hi;
+          acc.lo[k] = (float)(v - (double)hi);
+        } else {
+          V v = PG::identity();
+          for (uint32_t q = 0; q < it.nsplit; ++q)
+            v = PG::op(v, __ldcg(sp + (uint64_t)(it.slot + q) * slot_len + k));
+          acc.hi[k] = v;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  if (a.mode == 1) {  // row pass of one source interval (Algorithm 6 ToHub / 7 lines 9-14)
+    const uint32_t i = it.row;
+    const uint64_t pc = piece_index(a.P, tb, nt, i, t);
+    const uint64_t h0 = a.hub_off[pc], h1 = a.hub_off[pc + 1];
+    if (j < a.q_res) {  // destination resident: update it in place
+      V* ar = static_cast<V*>(a.accres);
+      for (uint64_t k = h0 + threadIdx.x; k < h1; k += kThreads) {
+        const uint32_t o = a.hub_dst[k];
+        PG::emit_global(ar + ts + o, PG::read(acc, o));
+      }
+    } else {  // destination on the host side: write the hub
+      V* hv = static_cast<V*>(a.hubs);
+      for (uint64_t k = h0 + threadIdx.x; k < h1; k += kThreads) hv[k] = PG::read(acc, a.hub_dst[k]);
+    }
+    return;
+  }
+  if (a.mode == 2) {
+    V* ar = static_cast<V*>(a.accres);
+    for (uint32_t k = threadIdx.x; k < T; k += kThreads) ar[ts + k] = PG::read(acc, k);
+    return;
+  }
+
+  // ---- epilogue (modes 0 and 3)
+  if constexpr (K == PK_PR || K == PK_WPR) {
+    const float alpha = a.alpha;
+    const float inv_n = 1.0f / (float)a.n;
+    const float dm = (float)(*a.dm_in);
+    float* rn = static_cast<float*>(a.vnew);
+    double part = 0.0;
+    for (uint32_t k = threadIdx.x; k < T; k += kThreads) {
+      const uint32_t v = ts + k;
+      const float tv = a.tele ? a.tele[v] : inv_n;
+      const float spread = a.dang_by_tele ? tv : inv_n;
+      const float r = (1.0f - alpha) * tv + alpha * (PG::read(acc, k) + dm * spread);
+      rn[v - a.out_base] = r;
+      const uint32_t od = a.outdeg[v];
+      if (a.cnew) a.cnew[v - a.out_base] = od ? r / (float)od : 0.0f;
+      if (od == 0) part += (double)r;
+    }
+    const double tot = block_sum_d(part, red);
+    if (threadIdx.x == 0) a.tile_part[t] = tot;
+  } else {
+    const uint32_t* vo = static_cast<const uint32_t*>(a.vold);
+    uint32_t* vn = static_cast<uint32_t*>(a.vnew);
+    bool changed = false;
+    for (uint32_t k = threadIdx.x; k < T; k += kThreads) {
+      const uint32_t v = ts + k - a.out_base;
+      const uint32_t o = vo[v];
+      const uint32_t ak = acc.hi[k];
+      const uint32_t nv = ak < o ? ak : o;
+      vn[v] = nv;
+      changed |= nv < o;
+    }
+    if (__syncthreads_or(changed) && threadIdx.x == 0) a.act_out[j] = 1u;
+  }
+
+  // ---- iteration completion: the last epilogue of the iteration folds the
+  // per-tile dangling mass (fixed order) / counts active intervals.
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_flag = (atomicAdd(a.ticket, 1u) == a.n_epi - 1);
+  __syncthreads();
+  if (!s_flag) return;
+  __threadfence();
+  if constexpr (K == PK_PR || K == PK_WPR) {
+    const uint32_t ntiles = a.col_tb[a.P];
+    double s = 0.0;
+    for (uint32_t q = threadIdx.x; q < ntiles; q += kThreads) s += __ldcg(a.tile_part + q);
+    const double tot = block_sum_d(s, red);
+    if (threadIdx.x == 0) *a.dm_out = tot;
+  } else {
+    uint32_t c = 0;
+    for (uint32_t q = threadIdx.x; q < a.P; q += kThreads) c += __ldcg(a.act_out + q) ? 1u : 0u;
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
+    __shared__ uint32_t cnt[kWarps];
+    if ((threadIdx.x & 31) == 0) cnt[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t tot = 0;
+      for (int q = 0; q < kWarps; ++q) tot += cnt[q];
+      *a.act_count = tot;
+    }
+    // the flags read this iteration become the next iteration's output flags
+    if (a.act_in)
+      for (uint32_t q = threadIdx.x; q < a.P; q += kThreads) const_cast<uint32_t*>(a.act_in)[q] = 0u;
+  }
+  if (threadIdx.x == 0) *a.ticket = 0u;
+}
+
+}  // namespace
+
+nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaStream_t s) {
+  if (nitems == 0) return NX_OK;
+  const bool sums = (kind == PK_PR || kind == PK_WPR);
+  const size_t smem = (size_t)a.tile_max * (sums ? 8 : 4);
+  switch (kind) {
+    case PK_PR: k_sweep<PK_PR><<<nitems, kThreads, smem, s>>>(a); break;
+    case PK_WPR: k_sweep<PK_WPR><<<nitems, kThreads, smem, s>>>(a); break;
+    case PK_BFS: k_sweep<PK_BFS><<<nitems, kThreads, smem, s>>>(a); break;
+    case PK_WCC: k_sweep<PK_WCC><<<nitems, kThreads, smem, s>>>(a); break;
+  }
+  NX_LAUNCH_CHECK();
+  return NX_OK;
+}
+
+}  // namespace nx

@@ -1,0 +1,81 @@
+// Sweep kernels' host-visible interface: work items and launch arguments.
+#pragma once
+#include "nx_internal.cuh"
+
+namespace nx {
+
+// One thread block's work: a destination tile, or a contiguous part of the
+// tile's "virtual edge sequence" (its pieces (i, t) for i = 0..P-1, over each
+// DSSS in the sweep, concatenated) when the tile is too heavy for one block.
+struct Item {
+  uint32_t tile;
+  uint32_t nsplit;  // blocks sharing this tile (1: not split)
+  uint32_t slot;    // first split slot of the tile (split tiles only)
+  uint32_t sub;     // this block's index among them
+  uint64_t vbeg, vend;
+  uint32_t row;     // mode 1: the source interval i of the piece
+  uint32_t pad;
+};
+
+struct SweepSrc {
+  const uint32_t* ew = nullptr;        // edge words; index e addresses edge e of the DSSS
+  const float* wt = nullptr;           // normalised weights (weighted PageRank), same indexing
+  const uint64_t* piece_off = nullptr; // [npieces+1]
+};
+
+enum ProgKind : int { PK_PR = 0, PK_WPR = 1, PK_BFS = 2, PK_WCC = 3 };
+
+struct SweepArgs {
+  SweepSrc src[2];
+  int nsrc = 1;
+  uint32_t src_lo = 0, src_hi = 0;  // source intervals swept: [src_lo, src_hi)
+  const Item* items = nullptr;
+  const uint32_t* tile_start = nullptr;
+  const uint32_t* col_tb = nullptr;
+  uint32_t P = 0, L = 0, lb = 0, n = 0, tile_max = 0;
+  // interval activity (min programs); nullptr = every source interval active
+  const uint32_t* act_in = nullptr;
+  uint32_t* act_out = nullptr;
+  uint32_t* act_count = nullptr;
+  // values
+  const void* gsrc = nullptr;  // gathered per source: c (PR), r (WPR), depth/label
+  const void* vold = nullptr;  // previous values (min programs)
+  void* vnew = nullptr;        // new values
+  float* cnew = nullptr;       // PR: next contributions r / outdeg (nullable)
+  const uint32_t* outdeg = nullptr;
+  const float* tele = nullptr;  // teleport vector or nullptr (uniform 1/n)
+  int dang_by_tele = 0;
+  float alpha = 0.85f;
+  const double* dm_in = nullptr;  // dangling mass of the previous values
+  double* dm_out = nullptr;       // dangling mass of the new values
+  double* tile_part = nullptr;    // [ntiles]
+  uint32_t* ticket = nullptr;     // completion counter of the iteration
+  uint32_t n_epi = 0;             // tile epilogues in the whole iteration
+  void* split = nullptr;          // split-tile partial accumulators
+  uint32_t* tile_ticket = nullptr;
+  // Modes. 0: sweep [src_lo, src_hi) (+ FromHub over [hub_lo, hub_hi)) then
+  // the epilogue; 1: row pass over single pieces of source interval src_lo —
+  // columns < q_res accumulate into accres, the others write their hub
+  // (ToHub); 2: sweep then store the raw accumulator into accres; 3: epilogue
+  // from accres (no edges).
+  int mode = 0;
+  uint32_t q_res = 0;
+  const uint64_t* hub_off = nullptr;  // of src[0]
+  const uint16_t* hub_dst = nullptr;
+  void* hubs = nullptr;               // hub values [D]
+  uint32_t hub_lo = 0, hub_hi = 0;
+  void* accres = nullptr;             // accumulators of resident columns [n_res]
+  // staged (non-resident) intervals: the source interval stage_i is read from
+  // gstage[0..L); epilogue values of a staged column go to vnew/cnew at
+  // v - out_base and previous values come from vold at v - out_base.
+  const void* gstage = nullptr;
+  uint32_t stage_i = 0xFFFFFFFFu;
+  uint32_t out_base = 0;
+  // debug/robustness: number of items and edge words addressable by ew[]
+  uint64_t ew_lo[2] = {0, 0};         // first edge index held by src[s].ew
+};
+
+// Launches one sweep over `nitems` items (kind selects the program).
+nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaStream_t s);
+
+}  // namespace nx

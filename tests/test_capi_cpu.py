@@ -1,0 +1,74 @@
+"""Host-side checks that need no GPU: the C-ABI library loads and exports every
+symbol include/nxgraph.h declares, its error path works without a device, and
+the planner's byte model follows Section III-B / Table II."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1510_06916_b300 import nxgraph as nx
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                   "nxgraph.h")
+
+
+def declared_functions():
+    text = open(HDR).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nx_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_expected_api():
+    names = declared_functions()
+    for must in ("nx_build_dsss", "nx_run", "nx_get_values"):
+        assert must in names
+    assert set(names) == set(nx.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = nx.lib()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_bad_arguments_rejected_before_any_device_work():
+    # n == 0 / P == 0 / P > n are refused by argument checks alone
+    with pytest.raises(nx.NxError) as e:
+        nx.Graph(np.zeros(1, np.uint32), np.zeros(1, np.uint32), 0, 1)
+    assert e.value.code == nx.NX_ERR_INVALID_ARG
+    with pytest.raises(nx.NxError) as e:
+        nx.Graph(np.zeros(1, np.uint32), np.zeros(1, np.uint32), 4, 0)
+    assert e.value.code == nx.NX_ERR_INVALID_ARG
+    with pytest.raises(nx.NxError) as e:
+        nx.Graph(np.zeros(1, np.uint32), np.zeros(1, np.uint32), 4, 5)
+    assert e.value.code == nx.NX_ERR_INVALID_ARG
+
+
+def test_io_model_spu_dpu():
+    n, m, Ba, Bv, Be, d = 7.2e8, 6.63e9, 8.0, 4.0, 4.0, 15.0
+    BM = 2 * n * Ba + 0.25 * m * Be  # SPU regime, part of the edges cached
+    q, rd, wr = nx.io_model("spu", n, m, 16, BM, Ba, Bv, Be, d)
+    assert q == 16 and wr == 0
+    assert rd == pytest.approx(m * Be + 2 * n * Ba - BM)  # Section III-B1
+    q, rd, wr = nx.io_model("spu", n, m, 16, 2 * n * Ba + m * Be + 1, Ba, Bv, Be, d)
+    assert rd == 0  # everything resident: no reads
+    q, rd, wr = nx.io_model("dpu", n, m, 16, 1e9, Ba, Bv, Be, d)
+    assert q == 0
+    assert rd == pytest.approx(m * (Be + (Ba + Bv) / d) + n * Ba)  # Section III-B2
+    assert wr == pytest.approx(m * (Ba + Bv) / d + n * Ba)
+
+
+@pytest.mark.parametrize("frac", [0.0, 0.25, 0.5, 0.999])
+def test_io_model_mpu_interpolates(frac):
+    n, m, Ba, Bv, Be, d, P = 1e6, 2e7, 4.0, 4.0, 4.0, 12.0, 64
+    BM = frac * 2 * n * Ba
+    q, rd, wr = nx.io_model("mpu", n, m, P, BM, Ba, Bv, Be, d)
+    assert q == np.floor(BM * P / (2 * n * Ba))  # Section III-B3 bound on Q
+    f = (P - q) / P
+    assert rd == pytest.approx(m * (Be + f * f * (Ba + Bv) / d) + f * n * Ba)  # Table II
+    assert wr == pytest.approx(f * f * m * (Ba + Bv) / d + f * n * Ba)
+    # Q = 0 reduces to DPU (Section III-B3)
+    q0, rd0, wr0 = nx.io_model("mpu", n, m, P, 0.0, Ba, Bv, Be, d)
+    qd, rdd, wrd = nx.io_model("dpu", n, m, P, 0.0, Ba, Bv, Be, d)
+    assert q0 == 0 and rd0 == pytest.approx(rdd) and wr0 == pytest.approx(wrd)

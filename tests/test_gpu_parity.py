@@ -1,0 +1,252 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a B300).
+
+Tolerances (PageRank family, FP32 on the GPU vs FP64 oracle): L1 over the
+vector <= 1e-6 and max per-vertex relative error <= 1e-4 over vertices with a
+non-zero reference. BFS depths and WCC labels: bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_06916_b300 import inputs
+from paper_1510_06916_b300 import nxgraph as nx
+
+pytestmark = pytest.mark.gpu
+
+L1_TOL = 1e-6
+REL_TOL = 1e-4
+
+
+def pr_err(gpu, ref):
+    gpu = gpu.astype(np.float64)
+    l1 = float(np.abs(gpu - ref).sum())
+    nz = ref != 0
+    rel = float((np.abs(gpu - ref)[nz] / np.abs(ref[nz])).max()) if nz.any() else 0.0
+    return l1, rel
+
+
+def assert_pr_close(gpu, ref, what=""):
+    l1, rel = pr_err(gpu, ref)
+    print(f"{what}: L1={l1:.3e} max_rel={rel:.3e}")
+    assert l1 <= L1_TOL, (what, l1, rel)
+    assert rel <= REL_TOL, (what, l1, rel)
+
+
+def rmat(scale, ef, seed, weights=False):
+    return inputs.rmat_edges(scale, ef << scale, seed, weights=weights)
+
+
+# ------------------------------------------------------------------ builder
+
+@pytest.mark.parametrize("P", [1, 2, 4, 7, 16])
+def test_dsss_layout_matches_oracle(P):
+    n = 1 << 12
+    s, d, _ = rmat(12, 16, 9)
+    g = nx.Graph(s, d, n, P, transpose=True)
+    order, off = oracle.dsss_order(n, P, s, d)
+    gs, gd, goff = g.export()
+    assert (goff == off).all()
+    assert (gs == s[order]).all() and (gd == d[order]).all()
+    # transpose DSSS = the DSSS of the reversed graph
+    order_t, off_t = oracle.dsss_order(n, P, d, s)
+    ts, td, toff = g.export(transpose=True)
+    assert (toff == off_t).all()
+    assert (ts == s[order_t]).all() and (td == d[order_t]).all()
+    info = g.info()
+    heads = np.ones(len(s), bool)
+    ks = (d[order].astype(np.int64) // info["L"]) * P + s[order] // info["L"]
+    heads[1:] = (ks[1:] != ks[:-1]) | (d[order][1:] != d[order][:-1])
+    assert info["D"] == heads.sum()  # distinct (sub-shard, destination) pairs
+
+
+def test_fig1_example_on_device():
+    # Section II-A, Fig. 1: SS_3.2 = e5.2, e4.3, e5.3 with intervals of 2 vertices
+    s = np.array([5, 1, 4, 6, 5, 3, 2, 7], np.uint32)
+    d = np.array([3, 2, 3, 0, 2, 5, 2, 4], np.uint32)
+    g = nx.Graph(s, d, 8, 4)
+    gs, gd, off = g.export()
+    sel = slice(int(off[1 * 4 + 2]), int(off[1 * 4 + 3]))
+    assert list(zip(gs[sel].tolist(), gd[sel].tolist())) == [(5, 2), (4, 3), (5, 3)]
+
+
+def test_ragged_and_empty_intervals():
+    # n = 9, P = 4: L = 3, the last interval is empty
+    rng = np.random.default_rng(1)
+    s = rng.integers(0, 9, 40).astype(np.uint32)
+    d = rng.integers(0, 9, 40).astype(np.uint32)
+    g = nx.Graph(s, d, 9, 4, transpose=True)
+    order, off = oracle.dsss_order(9, 4, s, d)
+    gs, gd, goff = g.export()
+    assert (goff == off).all() and (gs == s[order]).all() and (gd == d[order]).all()
+    g.run("pr", 20)
+    assert_pr_close(g.values(), oracle.pagerank(9, s, d, 0.85, 20), "ragged PR")
+    g.run("bfs", 100, root=3)
+    assert (g.values(dtype=np.uint32) == oracle.bfs(9, s, d, 3)).all()
+    g.run("wcc", 100)
+    assert (g.values(dtype=np.uint32) == oracle.wcc(9, s, d)).all()
+
+
+def test_invalid_inputs():
+    s = np.array([0, 5], np.uint32)
+    d = np.array([1, 2], np.uint32)
+    with pytest.raises(nx.NxError) as e:
+        nx.Graph(s, d, 5, 2)  # id 5 >= n
+    assert e.value.code == nx.NX_ERR_INVALID_ARG
+    g = nx.Graph(np.array([0, 1], np.uint32), np.array([1, 2], np.uint32), 3, 1)
+    with pytest.raises(nx.NxError):
+        g.run("wcc", 5)  # no transpose
+    with pytest.raises(nx.NxError):
+        g.run("wpr", 5)  # no weights
+    with pytest.raises(nx.NxError):
+        g.run("bfs", 5, root=3)
+    with pytest.raises(nx.NxError) as e:
+        g.run("pr", 5, strategy="spu", budget=8)  # below 2 n B_a
+    assert e.value.code == nx.NX_ERR_BUDGET_TOO_SMALL
+
+
+# ------------------------------------------------------------------ programs
+
+def test_pagerank_rmat16_p4():
+    # R-MAT scale 16, edge factor 16, seed 1, P = 4, 20 iterations, SPU
+    n = 1 << 16
+    s, d, _ = rmat(16, 16, 1)
+    g = nx.Graph(s, d, n, 4, transpose=True)
+    st = g.run("pr", 20, "spu")
+    assert st["iters_done"] == 20
+    r = g.values()
+    assert abs(r.astype(np.float64).sum() - 1.0) < 1e-5
+    assert_pr_close(r, oracle.pagerank(n, s, d, 0.85, 20), "rmat16 PR")
+
+
+def test_bfs_wcc_rmat16_bitexact():
+    n = 1 << 16
+    s, d, _ = rmat(16, 16, 1)
+    g = nx.Graph(s, d, n, 4, transpose=True)
+    g.run("bfs", 1000, root=0)
+    assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 0)).all()
+    g.run("wcc", 1000)
+    assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+
+
+@pytest.mark.parametrize("P", [1, 3, 16, 64])
+def test_programs_across_P(P):
+    n = 5000  # not a power of two: ragged last interval and tiles
+    s, d, _ = inputs.rmat_edges(13, 60000, 17)
+    keep = (s < n) & (d < n)
+    s, d = s[keep], d[keep]
+    g = nx.Graph(s, d, n, P, transpose=True)
+    g.run("pr", 20)
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"P={P} PR")
+    g.run("bfs", 1000, root=1)
+    assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 1)).all()
+    g.run("wcc", 1000)
+    assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+
+
+def test_heavy_hub_split_tiles():
+    # in-star with 300k leaves: one destination far heavier than a block's share
+    k = 300_000
+    n = k + 1
+    s = np.arange(1, n, dtype=np.uint32)
+    d = np.zeros(k, dtype=np.uint32)
+    s = np.concatenate([s, np.array([0, 5], np.uint32)])  # a little extra structure
+    d = np.concatenate([d, np.array([7, 0], np.uint32)])
+    g = nx.Graph(s, d, n, 4, transpose=True)
+    g.run("pr", 20)
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), "hub PR")
+    g.run("bfs", 100, root=5)
+    assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 5)).all()
+    g.run("wcc", 100)
+    assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+
+
+def test_tiny_and_empty_graphs():
+    g = nx.Graph(np.zeros(0, np.uint32), np.zeros(0, np.uint32), 5, 2, transpose=True)
+    g.run("pr", 3)
+    assert np.allclose(g.values(), 0.2, rtol=1e-6)
+    g.run("bfs", 10, root=2)
+    assert (g.values(dtype=np.uint32) == np.array([nx.INF, nx.INF, 0, nx.INF, nx.INF])).all()
+    g.run("wcc", 10)
+    assert (g.values(dtype=np.uint32) == np.arange(5)).all()
+    g1 = nx.Graph(np.zeros(3, np.uint32), np.zeros(3, np.uint32), 1, 1, transpose=True)
+    g1.run("pr", 5)
+    assert g1.values()[0] == pytest.approx(1.0, rel=1e-6)
+
+
+def test_cycle_uniform_on_device():
+    n = 100_003
+    s = np.arange(n, dtype=np.uint32)
+    d = ((np.arange(n) + 1) % n).astype(np.uint32)
+    g = nx.Graph(s, d, n, 8)
+    g.run("pr", 20)
+    assert np.allclose(g.values(), 1.0 / n, rtol=1e-5)
+
+
+def test_ppr_single_vector():
+    n = 1 << 14
+    s, d, _ = rmat(14, 16, 3)
+    t = inputs.ppr_teleports(n, 1, 33)[:, 0].copy()
+    g = nx.Graph(s, d, n, 8)
+    g.run("ppr", 30, teleport=t)
+    assert_pr_close(g.values(), oracle.personalized_pagerank(n, s, d, t, 0.85, 30), "PPR")
+
+
+def test_weighted_pagerank_forward():
+    n = 1 << 13
+    s, d, w = rmat(13, 16, 4, weights=True)
+    g = nx.Graph(s, d, n, 8, transpose=True, weights=w)
+    g.run("wpr", 50)
+    ref = oracle.pagerank(n, s, d, 0.85, 50, w=w.astype(np.float64))
+    assert_pr_close(g.values(), ref, "WPR")
+
+
+# ------------------------------------------------------------------ strategies
+
+@pytest.mark.parametrize("P", [1, 4, 9])
+def test_dpu_equals_spu(P):
+    n = 1 << 14
+    s, d, _ = rmat(14, 16, 5)
+    g = nx.Graph(s, d, n, P)
+    g.run("bfs", 1000, "spu", root=0)
+    b_spu = g.values(dtype=np.uint32)
+    st = g.run("bfs", 1000, "dpu", root=0)
+    assert st["strategy"] == nx.DPU
+    assert (g.values(dtype=np.uint32) == b_spu).all()
+    assert (b_spu == oracle.bfs(n, s, d, 0)).all()
+    g.run("pr", 20, "dpu")
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"DPU P={P}")
+
+
+def test_resume_from_values():
+    n = 1 << 14
+    s, d, _ = rmat(14, 16, 6)
+    g = nx.Graph(s, d, n, 4, transpose=True)
+    g.run("pr", 10)
+    mid = g.values()
+    g.set_values("pr", mid)
+    g.run("pr", 10)
+    ref = oracle.pagerank(n, s, d, 0.85, 20)
+    assert_pr_close(g.values(), ref, "PR 10+10")
+    g.run("bfs", 2, root=0)
+    part = g.values(dtype=np.uint32)
+    g.set_values("bfs", part)
+    g.run("bfs", 1000)
+    assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 0)).all()
+
+
+# ------------------------------------------------------------------ full size
+
+def test_full_size_rmat22_p16():
+    # R-MAT scale 22, edge factor 16 (67,108,864 edges), seed 2, P = 16: the
+    # benchmark's launch configuration, checked on the whole vector.
+    n = 1 << 22
+    s, d, _ = rmat(22, 16, 2)
+    g = nx.Graph(s, d, n, 16, transpose=True)
+    st = g.run("pr", 20, "spu")
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), "rmat22 PR")
+    g.run("bfs", 1000, root=0)
+    assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 0)).all()
+    g.run("wcc", 1000)
+    assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+    st = g.run("pr", 20, "dpu")
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), "rmat22 PR DPU")
