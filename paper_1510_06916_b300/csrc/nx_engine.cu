@@ -37,12 +37,18 @@ __global__ void k_init_pr(uint32_t n, const float* __restrict__ tele, const floa
   }
 }
 
+// One block of 256 threads; a fixed summation order (deterministic).
 __global__ void k_sum_parts(const double* __restrict__ part, uint32_t k, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double t = 0.0;
-    for (uint32_t q = 0; q < k; ++q) t += part[q];
-    *out = t;
+  __shared__ double red[256];
+  double t = 0.0;
+  for (uint32_t q = threadIdx.x; q < k; q += blockDim.x) t += part[q];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d) red[threadIdx.x] += red[threadIdx.x + d];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *out = red[0];
 }
 
 __global__ void k_init_min(uint32_t n, int bfs, uint32_t root, uint32_t* __restrict__ v) {
@@ -203,16 +209,15 @@ nx_status initialize(nx_graph* g, nx_program prog, const nx_params& p, const flo
       NX_TRY(ensure(g->aux[1], (size_t)n * 4));
     }
     const unsigned gb = grid_for(n);
-    DevBuf part;
-    NX_TRY(part.alloc((size_t)gb * 8));
+    NX_TRY(ensure(g->init_part, (size_t)gb * 8));
+    DevBuf& part = g->init_part;
     const float* r0_tele = (prog == NX_PPR) ? tele : nullptr;  // PPR: r0 = t
     k_init_pr<<<gb, 256, 0, stream()>>>(n, r0_tele, static_cast<const float*>(resume),
                                         g->outdeg.as<uint32_t>(), g->val[0].as<float>(),
                                         need_c ? g->aux[0].as<float>() : nullptr, part.as<double>());
     NX_LAUNCH_CHECK();
-    k_sum_parts<<<1, 32, 0, stream()>>>(part.as<double>(), gb, sc.dm);
+    k_sum_parts<<<1, 256, 0, stream()>>>(part.as<double>(), gb, sc.dm);
     NX_LAUNCH_CHECK();
-    NX_CUDA(cudaStreamSynchronize(stream()));
   } else {
     const uint32_t P = g->geo.P;
     std::vector<uint32_t> a0(P + 1, 0);
@@ -398,24 +403,31 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   g->values_set_for = -1;
   g->last_prog = (int)prog;
 
-  // plan
+  // plan (cached per strategy and DSSS set; the graph never changes)
   std::vector<const Dsss*> ds{&g->fwd};
   if (prog == NX_WCC) ds.push_back(&g->tr);
-  const uint64_t total = g->m * ds.size();
-  const uint64_t blk = target_block_edges(total);
-  PlanOut plan;
-  uint32_t n_a = 0, n_b = 0;
-  if (strat == NX_SPU) {
-    plan_tiles(g, ds, 0, P, 0, P, true, blk, plan);
-    n_a = (uint32_t)plan.items.size();
-  } else {  // DPU: ToHub items (all rows), then FromHub tiles
-    for (uint32_t i = 0; i < P; ++i) plan_row(g, g->fwd, i, 0, P, blk, plan);
-    n_a = (uint32_t)plan.items.size();
-    plan_tiles(g, ds, 0, 0, 0, P, false, blk, plan);
-    n_b = (uint32_t)plan.items.size() - n_a;
-    NX_TRY(ensure(g->hubs, std::max<uint64_t>(g->fwd.D, 1) * 4));
+  const int key = (int)strat * 16 + (int)ds.size();
+  uint32_t n_a = g->plan_na, n_b = g->plan_nb;
+  if (g->plan_key != key) {
+    const uint64_t total = g->m * ds.size();
+    const uint64_t blk = target_block_edges(total);
+    PlanOut plan;
+    if (strat == NX_SPU) {
+      plan_tiles(g, ds, 0, P, 0, P, true, blk, plan);
+      n_a = (uint32_t)plan.items.size();
+      n_b = 0;
+    } else {  // DPU: ToHub items (all rows), then FromHub tiles
+      for (uint32_t i = 0; i < P; ++i) plan_row(g, g->fwd, i, 0, P, blk, plan);
+      n_a = (uint32_t)plan.items.size();
+      plan_tiles(g, ds, 0, 0, 0, P, false, blk, plan);
+      n_b = (uint32_t)plan.items.size() - n_a;
+    }
+    NX_TRY(upload_items(g, plan));
+    g->plan_key = key;
+    g->plan_na = n_a;
+    g->plan_nb = n_b;
   }
-  NX_TRY(upload_items(g, plan));
+  if (strat == NX_DPU) NX_TRY(ensure(g->hubs, std::max<uint64_t>(g->fwd.D, 1) * 4));
   SweepArgs a = base_args(g, prog, p, tele);
   a.items = g->items.as<Item>();
   a.split = g->split_buf.p;

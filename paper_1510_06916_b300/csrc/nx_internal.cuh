@@ -146,6 +146,8 @@ struct nx_graph {
   nx::DevBuf hubs;          // hub values [D]
   int plan_key = -1;
   uint32_t nitems = 0;
+  uint32_t plan_na = 0, plan_nb = 0;
+  nx::DevBuf init_part;     // per-block partial sums of the init kernel
   uint64_t split_floats = 0;
   nx::DevBuf tele;          // float [n] teleport copy (PPR/WPR)
   nx::DevBuf lam[2], ybuf;  // adjoint scratch

@@ -44,8 +44,12 @@ struct PrSum {  // PageRank family: compensated sum of float contributions
     const float s = old + v;
     const float bb = s - old;
     const float err = (old - (s - bb)) + (v - bb);
-    if (err != 0.f) atomicAdd(acc.lo + k, err);
+    atomicAdd(acc.lo + k, err);
   }
+  // Runs that end inside one lane (at most 8 edges): a plain add. A destination
+  // gets few of these (at most two per piece), so their rounding stays small;
+  // long runs cross lanes and take the compensated path above.
+  __device__ static void emit_short(Acc<V> acc, uint32_t k, V v) { atomicAdd(acc.hi + k, v); }
   __device__ static V read(Acc<V> acc, uint32_t k) { return acc.hi[k] + acc.lo[k]; }
   __device__ static void emit_global(V* p, V v) { *p += v; }
 };
@@ -57,6 +61,7 @@ struct MinU {  // BFS / WCC: min of uint32
   __device__ static void emit(Acc<V> acc, uint32_t k, V v) {
     if (v != kInf) atomicMin(acc.hi + k, v);
   }
+  __device__ static void emit_short(Acc<V> acc, uint32_t k, V v) { emit(acc, k, v); }
   __device__ static V read(Acc<V> acc, uint32_t k) { return acc.hi[k]; }
   __device__ static void emit_global(V* p, V v) {
     if (v < *p) *p = v;
@@ -103,41 +108,63 @@ __device__ __forceinline__ float4 ld_stream_f(const float* p) {
 }
 
 // Folds edges [a, b) of one piece into the tile accumulator. Edge e is read at
-// ew[e - ew_lo]; its source value at g[sbase + src_local].
+// ew[e - ew_lo]; its source value at g[sbase + src_local]. The piece is cut
+// into 256-edge steps from a = floor8(a); step k goes to warp (k + rot) % 8 so
+// that short pieces do not all land on the same warps (rot advances by the
+// piece's step count). Each warp loads its next step's edge words before it
+// gathers and reduces the current one.
 template <class PG>
 __device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
                                             const float* __restrict__ wt, uint64_t ew_lo,
                                             uint64_t a, uint64_t b, const void* __restrict__ g,
                                             uint32_t sbase, uint32_t lb,
-                                            Acc<typename PG::V> acc) {
+                                            Acc<typename PG::V> acc, uint32_t& rot) {
   using V = typename PG::V;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t smask = (1u << lb) - 1u;
   const uint64_t a8 = a & ~7ull;
-  for (uint64_t base = a8 + (uint64_t)warp * 256; base < b; base += (uint64_t)kWarps * 256) {
+  const uint32_t nsteps = (uint32_t)((b - a8 + 255) >> 8);
+  const uint32_t k0 = (uint32_t)((warp - (int)rot) & (kWarps - 1));
+  rot = (rot + nsteps) & (kWarps - 1);
+  uint64_t base = a8 + (uint64_t)k0 * 256;
+  if (base >= b) return;
+  uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
+  float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = f0;
+  {
     const uint64_t p = base + (uint64_t)lane * 8;
-    uint32_t wv[8];
-    float wf[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      wv[k] = 0;
-      wf[k] = 0.f;
-    }
     if (p < b) {
-      uint4 q0 = ld_stream(ew + (p - ew_lo)), q1 = ld_stream(ew + (p - ew_lo) + 4);
-      wv[0] = q0.x; wv[1] = q0.y; wv[2] = q0.z; wv[3] = q0.w;
-      wv[4] = q1.x; wv[5] = q1.y; wv[6] = q1.z; wv[7] = q1.w;
+      q0 = ld_stream(ew + (p - ew_lo));
+      q1 = ld_stream(ew + (p - ew_lo) + 4);
       if (PG::weighted) {
-        float4 f0 = ld_stream_f(wt + (p - ew_lo)), f1 = ld_stream_f(wt + (p - ew_lo) + 4);
-        wf[0] = f0.x; wf[1] = f0.y; wf[2] = f0.z; wf[3] = f0.w;
-        wf[4] = f1.x; wf[5] = f1.y; wf[6] = f1.z; wf[7] = f1.w;
+        f0 = ld_stream_f(wt + (p - ew_lo));
+        f1 = ld_stream_f(wt + (p - ew_lo) + 4);
+      }
+    }
+  }
+  while (base < b) {
+    // valid edges of this step: offsets [lo, hi) from base (32-bit)
+    const uint32_t lo = base < a ? (uint32_t)(a - base) : 0u;
+    const uint32_t hi = (b - base) < 256 ? (uint32_t)(b - base) : 256u;
+    const uint32_t span = hi - lo;
+    const uint32_t wv[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+    const float wf[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+    const uint64_t nbase = base + (uint64_t)kWarps * 256;
+    {  // prefetch the warp's next step
+      const uint64_t pn = nbase + (uint64_t)lane * 8;
+      if (pn < b) {
+        q0 = ld_stream(ew + (pn - ew_lo));
+        q1 = ld_stream(ew + (pn - ew_lo) + 4);
+        if (PG::weighted) {
+          f0 = ld_stream_f(wt + (pn - ew_lo));
+          f1 = ld_stream_f(wt + (pn - ew_lo) + 4);
+        }
       }
     }
     uint32_t key[8];
     V val[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const bool valid = (p + k >= a) && (p + k < b);
+      const bool valid = ((uint32_t)(lane * 8 + k) - lo) < span;
       key[k] = valid ? (wv[k] >> lb) : kSent;
       val[k] = valid ? PG::gather(g, sbase + (wv[k] & smask), wf[k]) : PG::identity();
     }
@@ -147,19 +174,15 @@ __device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
     bool single = true;
 #pragma unroll
     for (int k = 1; k < 8; ++k) {
-      if (key[k] == ck) {
-        cs = PG::op(cs, val[k]);
-      } else {
-        if (single) {
-          hk = ck;
-          hs = cs;
-          single = false;
-        } else if (ck != kSent) {
-          PG::emit(acc, ck, cs);
-        }
-        ck = key[k];
-        cs = val[k];
+      const bool brk = key[k] != ck;
+      if (brk && !single && ck != kSent) PG::emit_short(acc, ck, cs);
+      if (brk && single) {
+        hk = ck;
+        hs = cs;
       }
+      single = single && !brk;
+      cs = brk ? val[k] : PG::op(cs, val[k]);
+      ck = key[k];
     }
     const uint32_t first_key = single ? ck : hk;
     uint32_t prev_tail = __shfl_up_sync(0xffffffffu, ck, 1);
@@ -178,8 +201,16 @@ __device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
       if (lane - d >= seg0) x = PG::op(y, x);
     }
     const V prev_x = __shfl_up_sync(0xffffffffu, x, 1);
-    if (!single && hk != kSent) PG::emit(acc, hk, (lane > 0 && hk == prev_tail) ? PG::op(prev_x, hs) : hs);
-    if (ck != kSent && next_first != ck) PG::emit(acc, ck, x);
+    // the head run joins the chain of the lanes before it when the key matches
+    if (!single && hk != kSent) {
+      if (lane > 0 && hk == prev_tail) PG::emit(acc, hk, PG::op(prev_x, hs));
+      else PG::emit_short(acc, hk, hs);
+    }
+    if (ck != kSent && next_first != ck) {
+      if (seg0 < lane) PG::emit(acc, ck, x);  // the run crossed lanes
+      else PG::emit_short(acc, ck, x);
+    }
+    base = nbase;
   }
 }
 
@@ -226,6 +257,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
   if (a.mode != 3) {
     // edges: pieces (i, t) for i in [src_lo, src_hi) of every DSSS of the sweep
     uint64_t vo = 0;
+    uint32_t rot = 0;
     const uint32_t i_lo = a.mode == 1 ? it.row : a.src_lo;
     const uint32_t i_hi = a.mode == 1 ? it.row + 1 : a.src_hi;
     for (int s = 0; s < a.nsrc && vo < it.vend; ++s) {
@@ -240,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
           const void* g = staged ? a.gstage : a.gsrc;
           const uint32_t sb = staged ? 0u : i * a.L;
           sweep_range<PG>(a.src[s].ew, a.src[s].wt, a.ew_lo[s], p0 + (lo - vo), p0 + (hi - vo), g,
-                          sb, a.lb, acc);
+                          sb, a.lb, acc, rot);
         }
         vo += len;
       }
