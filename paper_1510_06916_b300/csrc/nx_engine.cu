@@ -339,34 +339,231 @@ nx_status dpu_iteration(nx_graph* g, nx_program prog, SweepArgs& a, uint32_t n_t
   return NX_OK;
 }
 
+// ---------------------------------------------------------------- shard streaming
+// Edge words of columns [first_col, P) of DSSS d held in pinned host memory
+// (created on first use from the device copy).
+nx_status ensure_host_shards(nx_graph* g, Dsss& d, uint32_t first_col) {
+  const auto& tb = g->geo.h_col_tb;
+  const uint64_t e0 = d.h_piece_off[(uint64_t)g->geo.P * tb[first_col]] & ~7ull;
+  if (d.h_ew.p && d.h_ew_first <= e0) return NX_OK;
+  const uint64_t words = round_up(d.m, 8) + 8 - e0;
+  NX_TRY(d.h_ew.alloc(words * 4));
+  NX_CUDA(cudaMemcpyAsync(d.h_ew.p, d.ew.as<uint32_t>() + e0, words * 4, cudaMemcpyDeviceToHost,
+                          stream()));
+  NX_CUDA(cudaStreamSynchronize(stream()));
+  d.h_ew_first = e0;
+  return NX_OK;
+}
+
+struct Streamer {
+  cudaStream_t side = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
+  ~Streamer() {
+    for (int k = 0; k < 2; ++k) {
+      if (copied[k]) cudaEventDestroy(copied[k]);
+      if (used[k]) cudaEventDestroy(used[k]);
+    }
+    if (side) cudaStreamDestroy(side);
+  }
+  nx_status init() {
+    NX_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      NX_CUDA(cudaEventCreateWithFlags(&copied[k], cudaEventDisableTiming));
+      NX_CUDA(cudaEventCreateWithFlags(&used[k], cudaEventDisableTiming));
+      NX_CUDA(cudaEventRecord(used[k], stream()));
+    }
+    return NX_OK;
+  }
+};
+
+// ---------------------------------------------------------------- run
+struct RunCtx {
+  nx_graph* g;
+  nx_program prog;
+  std::vector<const Dsss*> ds;
+  uint32_t P, Q, Jc;
+  const float* tele;
+  uint64_t h2d = 0, d2h = 0;
+  uint32_t launches = 0;
+};
+
+// SPU iteration with columns [Jc, P) streamed from pinned host memory on a
+// side stream (double-buffered); columns [0, Jc) are read in place.
+nx_status spu_stream_iteration(RunCtx& c, SweepArgs& a, const std::vector<uint32_t>& col_off,
+                               Streamer& sm) {
+  nx_graph* g = c.g;
+  set_iter_ptrs(g, c.prog, a);
+  a.mode = 0;
+  const Item* all = g->items.as<Item>();
+  // resident columns
+  SweepArgs r = a;
+  r.items = all;
+  NX_TRY(launch_sweep(kind_of(c.prog), r, col_off[c.Jc], stream()));
+  ++c.launches;
+  const auto& tb = g->geo.h_col_tb;
+  for (uint32_t j = c.Jc; j < c.P; ++j) {
+    const int b = j & 1;
+    SweepArgs sa = a;
+    sa.items = all + col_off[j];
+    NX_CUDA(cudaStreamWaitEvent(sm.side, sm.used[b], 0));
+    for (size_t s = 0; s < c.ds.size(); ++s) {
+      const Dsss& d = *c.ds[s];
+      const uint64_t e0 = d.h_piece_off[(uint64_t)c.P * tb[j]] & ~7ull;
+      const uint64_t e1 = round_up(d.h_piece_off[(uint64_t)c.P * tb[j + 1]], 8) + 8;
+      const uint64_t words = e1 - e0;
+      // stage[b] holds one shard per DSSS of the sweep (second half: transpose)
+      uint32_t* dst = g->stage[b].as<uint32_t>() + (s ? (g->stage[b].bytes / 8) : 0);
+      NX_CUDA(cudaMemcpyAsync(dst, d.h_ew.as<uint32_t>() + (e0 - d.h_ew_first), words * 4,
+                              cudaMemcpyHostToDevice, sm.side));
+      c.h2d += words * 4;
+      sa.src[s].ew = dst;
+      sa.ew_lo[s] = e0;
+    }
+    NX_CUDA(cudaEventRecord(sm.copied[b], sm.side));
+    NX_CUDA(cudaStreamWaitEvent(stream(), sm.copied[b], 0));
+    NX_TRY(launch_sweep(kind_of(c.prog), sa, col_off[j + 1] - col_off[j], stream()));
+    ++c.launches;
+    NX_CUDA(cudaEventRecord(sm.used[b], stream()));
+  }
+  g->cur ^= 1;
+  return NX_OK;
+}
+
+// MPU iteration (Algorithm 7) with intervals [Q, P) in pinned host memory.
+struct Staged {
+  uint32_t n_res = 0, nh = 0;
+  std::vector<uint32_t> off;  // launch boundaries in the item array
+};
+
+nx_status mpu_iteration(RunCtx& c, SweepArgs& a, Staged& S) {
+  nx_graph* g = c.g;
+  const uint32_t P = c.P, Q = c.Q, L = g->geo.L, n = g->geo.n;
+  const bool pr = !is_min(c.prog);
+  const bool has_c = (c.prog == NX_PR || c.prog == NX_PPR);
+  const int cur = g->cur, nxt = 1 - g->cur;
+  set_iter_ptrs(g, c.prog, a);
+  const Item* all = g->items.as<Item>();
+  const ProgKind K = kind_of(c.prog);
+  uint32_t li = 0;  // launch index into S.off
+  auto items_of = [&](uint32_t k) { return std::make_pair(all + S.off[k], S.off[k + 1] - S.off[k]); };
+  // host arrays of this iteration
+  float* hv_old = g->hval[cur].as<float>();
+  float* hv_new = g->hval[nxt].as<float>();
+  const uint32_t nh = S.nh;
+  float* hc_old = has_c ? g->hval[cur].as<float>() + nh : nullptr;
+  float* hc_new = has_c ? g->hval[nxt].as<float>() + nh : nullptr;
+  // 1. resident block: sources [0, Q) into columns [0, Q), stored raw (lines 2-6)
+  {
+    auto [it, k] = items_of(li++);
+    SweepArgs m2 = a;
+    m2.mode = 2;
+    m2.items = it;
+    m2.src_lo = 0;
+    m2.src_hi = Q;
+    m2.accres = g->accres.p;
+    NX_TRY(launch_sweep(K, m2, k, stream()));
+    ++c.launches;
+  }
+  // 2. rows i >= Q: load I_i, update resident columns in place, ToHub the rest (lines 7-16)
+  std::vector<uint32_t> act_h(P, 1);
+  if (!pr) {
+    NX_CUDA(cudaMemcpyAsync(act_h.data(), a.act_in, P * 4, cudaMemcpyDeviceToHost, stream()));
+    NX_CUDA(cudaStreamSynchronize(stream()));
+  }
+  for (uint32_t i = Q; i < P; ++i) {
+    auto [it, k] = items_of(li++);
+    if (!act_h[i] || k == 0) continue;
+    const uint32_t v0 = i * L, v1 = std::min<uint32_t>(n, v0 + L);
+    if (v1 <= v0) continue;
+    const float* src_host = (has_c ? hc_old : hv_old) + (v0 - S.n_res);
+    NX_CUDA(cudaMemcpyAsync(g->vstage[0].p, src_host, (size_t)(v1 - v0) * 4,
+                            cudaMemcpyHostToDevice, stream()));
+    c.h2d += (uint64_t)(v1 - v0) * 4;
+    SweepArgs m1 = a;
+    m1.mode = 1;
+    m1.items = it;
+    m1.q_res = Q;
+    m1.accres = g->accres.p;
+    m1.hubs = g->hubs.p;
+    m1.gstage = g->vstage[0].p;
+    m1.stage_i = i;
+    NX_TRY(launch_sweep(K, m1, k, stream()));
+    ++c.launches;
+  }
+  // 3. epilogue of the resident columns from their accumulators
+  {
+    auto [it, k] = items_of(li++);
+    SweepArgs m3 = a;
+    m3.mode = 3;
+    m3.items = it;
+    m3.accres = g->accres.p;
+    NX_TRY(launch_sweep(K, m3, k, stream()));
+    ++c.launches;
+  }
+  // 4. columns j >= Q: SPU from resident rows + FromHub, save to the host (lines 17-26)
+  for (uint32_t j = Q; j < P; ++j) {
+    auto [it, k] = items_of(li++);
+    const uint32_t v0 = j * L, v1 = std::min<uint32_t>(n, v0 + L);
+    if (v1 <= v0) continue;
+    const size_t bytes = (size_t)(v1 - v0) * 4;
+    SweepArgs m0 = a;
+    m0.mode = 0;
+    m0.items = it;
+    m0.src_lo = 0;
+    m0.src_hi = Q;
+    m0.hub_lo = Q;
+    m0.hub_hi = P;
+    m0.hubs = g->hubs.p;
+    m0.out_base = v0;
+    m0.vnew = g->vstage[1].p;
+    m0.cnew = has_c ? g->vstage[2].as<float>() : nullptr;
+    if (!pr) {
+      NX_CUDA(cudaMemcpyAsync(g->vstage[3].p, hv_old + (v0 - S.n_res), bytes,
+                              cudaMemcpyHostToDevice, stream()));
+      c.h2d += bytes;
+      m0.vold = g->vstage[3].p;
+    }
+    NX_TRY(launch_sweep(K, m0, k, stream()));
+    ++c.launches;
+    NX_CUDA(cudaMemcpyAsync(hv_new + (v0 - S.n_res), g->vstage[1].p, bytes, cudaMemcpyDeviceToHost,
+                            stream()));
+    c.d2h += bytes;
+    if (has_c) {
+      NX_CUDA(cudaMemcpyAsync(hc_new + (v0 - S.n_res), g->vstage[2].p, bytes,
+                              cudaMemcpyDeviceToHost, stream()));
+      c.d2h += bytes;
+    }
+  }
+  g->cur ^= 1;
+  return NX_OK;
+}
+
 nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t iters,
                    nx_strategy strategy, uint64_t budget, nx_run_stats* st) {
-  const uint32_t n = g->geo.n, P = g->geo.P;
+  const uint32_t n = g->geo.n, P = g->geo.P, L = g->geo.L;
   if (prog == NX_WCC && !g->has_tr)
     return invalid("nx_run: WCC needs the transpose DSSS (build with NX_WITH_TRANSPOSE)");
   if (prog == NX_WPR && !g->has_w) return invalid("nx_run: WPR needs NX_WITH_WEIGHTS");
   if (prog == NX_BFS && p.root >= n) return invalid("nx_run: BFS root >= n");
-  if (prog == NX_WCC && strategy == NX_DPU) {
-    // hubs hold one DSSS; WCC sweeps two (forward + transpose)
-    return invalid("nx_run: DPU/MPU hubs support single-DSSS programs (PR, PPR, WPR, BFS)");
-  }
   // strategy from the budget (Section III-B3: Q <= B_M P / (2 n B_a))
   const double Ba = 4.0;
-  uint32_t Q = P;
-  if (budget) Q = (uint32_t)std::min<double>(P, std::floor((double)budget * P / (2.0 * n * Ba)));
+  uint32_t Qb = P;
+  if (budget) Qb = (uint32_t)std::min<double>(P, std::floor((double)budget * P / (2.0 * n * Ba)));
   nx_strategy strat = strategy;
-  if (strat == NX_AUTO) strat = (Q >= P) ? NX_SPU : NX_MPU;
-  if (strat == NX_SPU && Q < P) {
+  if (strat == NX_AUTO) strat = (Qb >= P) ? NX_SPU : NX_MPU;
+  if (strat == NX_SPU && Qb < P) {
     set_error("nx_run: SPU needs 2 n B_a bytes of budget for the ping-pong intervals");
     return NX_ERR_BUDGET_TOO_SMALL;
   }
-  if (strat == NX_MPU && Q >= P) strat = NX_SPU;  // Q = P: MPU is SPU (Section III-B3)
-  if (strat == NX_MPU) {
-    set_error("nx_run: MPU with Q < P is not available in this build");
-    return NX_ERR_INVALID_ARG;
+  if (strat == NX_MPU && Qb >= P) strat = NX_SPU;  // Q = P: MPU is SPU (Section III-B3)
+  const bool staged = (strat == NX_MPU) || (strat == NX_DPU && Qb < P);
+  const uint32_t Q = strat == NX_MPU ? Qb : (strat == NX_DPU ? 0 : P);
+  if ((strat == NX_DPU || strat == NX_MPU) && prog == NX_WCC)
+    return invalid("nx_run: hubs hold one DSSS; DPU/MPU run PR, PPR, WPR and BFS (WCC sweeps two)");
+  if (budget && (strat == NX_DPU || strat == NX_MPU) && budget < 2ull * L * 4) {
+    set_error("nx_run: the budget is below one interval pair (2 L B_a)");
+    return NX_ERR_BUDGET_TOO_SMALL;
   }
-  if (strat == NX_MPU && prog == NX_WCC)
-    return invalid("nx_run: DPU/MPU hubs support single-DSSS programs (PR, PPR, WPR, BFS)");
 
   NX_TRY(prepare(g));
   // teleport
@@ -391,7 +588,6 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   // initialize or resume
   const bool resume = (g->values_set_for == (int)prog);
   if (resume) {
-    // the resumed values sit in val[cur]; move them to val[0] through the init path
     DevBuf tmp;
     NX_TRY(tmp.alloc((size_t)n * 4));
     NX_CUDA(cudaMemcpyAsync(tmp.p, g->val[g->cur].p, (size_t)n * 4, cudaMemcpyDeviceToDevice,
@@ -403,43 +599,139 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   g->values_set_for = -1;
   g->last_prog = (int)prog;
 
-  // plan (cached per strategy and DSSS set; the graph never changes)
-  std::vector<const Dsss*> ds{&g->fwd};
-  if (prog == NX_WCC) ds.push_back(&g->tr);
-  const int key = (int)strat * 16 + (int)ds.size();
+  RunCtx c;
+  c.g = g;
+  c.prog = prog;
+  c.ds = {&g->fwd};
+  if (prog == NX_WCC) c.ds.push_back(&g->tr);
+  c.P = P;
+  c.Q = Q;
+  c.tele = tele;
+  const auto& tb = g->geo.h_col_tb;
+  // SPU: shards that do not fit next to the intervals stream from pinned host memory
+  c.Jc = P;
+  if (strat == NX_SPU && budget) {
+    const uint64_t vert = (uint64_t)2 * n * 4;
+    uint64_t left = budget > vert ? budget - vert : 0;
+    uint32_t j = 0;
+    for (; j < P; ++j) {
+      uint64_t bytes = 0;
+      for (const Dsss* d : c.ds)
+        bytes += 4 * (d->h_piece_off[(uint64_t)P * tb[j + 1]] - d->h_piece_off[(uint64_t)P * tb[j]]);
+      if (prog == NX_WPR) bytes *= 2;
+      if (bytes > left) break;
+      left -= bytes;
+    }
+    c.Jc = j;
+    if (c.Jc < P && prog == NX_WPR) {
+      set_error("nx_run: weighted PageRank needs its edges on the device (budget too small)");
+      return NX_ERR_BUDGET_TOO_SMALL;
+    }
+  }
+  const bool streaming = (strat == NX_SPU && c.Jc < P);
+
+  // plan (cached: the graph never changes)
+  const int key = ((int)strat * 16 + (int)c.ds.size()) * 4096 + (int)(staged ? Q + 1 : 0) +
+                  (streaming ? (int)(c.Jc + 2048) : 0);
   uint32_t n_a = g->plan_na, n_b = g->plan_nb;
+  static thread_local std::vector<uint32_t> launch_off;  // per-launch item offsets
   if (g->plan_key != key) {
-    const uint64_t total = g->m * ds.size();
+    const uint64_t total = g->m * c.ds.size();
     const uint64_t blk = target_block_edges(total);
     PlanOut plan;
-    if (strat == NX_SPU) {
-      plan_tiles(g, ds, 0, P, 0, P, true, blk, plan);
+    launch_off.clear();
+    if (strat == NX_SPU && !streaming) {
+      plan_tiles(g, c.ds, 0, P, 0, P, true, blk, plan);
       n_a = (uint32_t)plan.items.size();
       n_b = 0;
-    } else {  // DPU: ToHub items (all rows), then FromHub tiles
+    } else if (strat == NX_SPU) {  // per column groups: [0, Jc) then one per streamed column
+      launch_off.assign(P + 1, 0);
+      plan_tiles(g, c.ds, 0, P, 0, c.Jc, true, blk, plan);
+      for (uint32_t j = c.Jc; j < P; ++j) {
+        launch_off[j] = (uint32_t)plan.items.size();
+        plan_tiles(g, c.ds, 0, P, j, j + 1, true, blk, plan);
+      }
+      launch_off[P] = (uint32_t)plan.items.size();  // launch_off[Jc]: resident item count
+    } else if (!staged) {  // DPU, intervals resident: ToHub items (all rows), then FromHub tiles
       for (uint32_t i = 0; i < P; ++i) plan_row(g, g->fwd, i, 0, P, blk, plan);
       n_a = (uint32_t)plan.items.size();
-      plan_tiles(g, ds, 0, 0, 0, P, false, blk, plan);
+      plan_tiles(g, c.ds, 0, 0, 0, P, false, blk, plan);
       n_b = (uint32_t)plan.items.size() - n_a;
+    } else {  // MPU / staged DPU: launches of Algorithm 7
+      launch_off.push_back(0);
+      plan_tiles(g, c.ds, 0, Q, 0, Q, true, blk, plan);  // resident block (mode 2)
+      launch_off.push_back((uint32_t)plan.items.size());
+      for (uint32_t i = Q; i < P; ++i) {  // rows (mode 1)
+        plan_row(g, g->fwd, i, 0, P, blk, plan);
+        launch_off.push_back((uint32_t)plan.items.size());
+      }
+      plan_tiles(g, c.ds, 0, 0, 0, Q, false, blk, plan);  // resident epilogue (mode 3)
+      launch_off.push_back((uint32_t)plan.items.size());
+      for (uint32_t j = Q; j < P; ++j) {  // staged columns (mode 0)
+        plan_tiles(g, c.ds, 0, Q, j, j + 1, true, blk, plan);
+        launch_off.push_back((uint32_t)plan.items.size());
+      }
     }
     NX_TRY(upload_items(g, plan));
     g->plan_key = key;
     g->plan_na = n_a;
     g->plan_nb = n_b;
+    g->plan_off = launch_off;
   }
-  if (strat == NX_DPU) NX_TRY(ensure(g->hubs, std::max<uint64_t>(g->fwd.D, 1) * 4));
+  if (strat == NX_DPU || staged) NX_TRY(ensure(g->hubs, std::max<uint64_t>(g->fwd.D, 1) * 4));
+
   SweepArgs a = base_args(g, prog, p, tele);
   a.items = g->items.as<Item>();
   a.split = g->split_buf.p;
 
+  // streaming buffers
+  Streamer sm;
+  std::vector<uint32_t> col_off;
+  if (streaming) {
+    for (const Dsss* d : c.ds) NX_TRY(ensure_host_shards(g, *const_cast<Dsss*>(d), c.Jc));
+    uint64_t maxw = 0;
+    for (uint32_t j = c.Jc; j < P; ++j)
+      for (const Dsss* d : c.ds) {
+        const uint64_t e0 = d->h_piece_off[(uint64_t)P * tb[j]] & ~7ull;
+        const uint64_t e1 = round_up(d->h_piece_off[(uint64_t)P * tb[j + 1]], 8) + 8;
+        maxw = std::max(maxw, e1 - e0);
+      }
+    for (int b = 0; b < 2; ++b) NX_TRY(ensure(g->stage[b], maxw * 4 * 2));
+    NX_TRY(sm.init());
+    col_off = g->plan_off;
+  }
+  // staged intervals (MPU): device accumulators for resident columns, pinned
+  // host arrays for the rest, per-interval staging buffers
+  Staged S;
+  if (staged) {
+    S.n_res = std::min<uint64_t>((uint64_t)Q * L, n);
+    S.nh = n - S.n_res;
+    S.off = g->plan_off;
+    NX_TRY(ensure(g->accres, std::max<size_t>(S.n_res, 1) * 4));
+    for (int b = 0; b < 4; ++b) NX_TRY(ensure(g->vstage[b], (size_t)L * 4));
+    const bool has_c = (prog == NX_PR || prog == NX_PPR);
+    const size_t hbytes = (size_t)S.nh * 4 * (has_c ? 2 : 1);
+    for (int b = 0; b < 2; ++b)
+      if (g->hval[b].bytes < std::max<size_t>(hbytes, 4)) NX_TRY(g->hval[b].alloc(std::max<size_t>(hbytes, 4)));
+    // move the initial values of intervals [Q, P) to the host
+    const int cc = g->cur;
+    if (S.nh) {
+      NX_CUDA(cudaMemcpyAsync(g->hval[cc].p, g->val[cc].as<uint32_t>() + S.n_res, (size_t)S.nh * 4,
+                              cudaMemcpyDeviceToHost, stream()));
+      if (has_c)
+        NX_CUDA(cudaMemcpyAsync(g->hval[cc].as<uint32_t>() + S.nh, g->aux[cc].as<uint32_t>() + S.n_res,
+                                (size_t)S.nh * 4, cudaMemcpyDeviceToHost, stream()));
+    }
+    NX_CUDA(cudaStreamSynchronize(stream()));
+  }
+
   // per-interval edge counts (edges streamed by a sweep of active sources)
   std::vector<uint64_t> row_edges(P, 0);
   for (uint32_t j = 0; j < P; ++j) {
-    const auto& tb = g->geo.h_col_tb;
     const uint32_t nt = tb[j + 1] - tb[j];
     if (nt == 0) continue;  // empty trailing interval
     for (uint32_t i = 0; i < P; ++i)
-      for (const Dsss* d : ds) {
+      for (const Dsss* d : c.ds) {
         uint64_t p0 = d->h_piece_off[piece_index(P, tb[j], nt, i, tb[j])];
         uint64_t p1 = d->h_piece_off[piece_index(P, tb[j], nt, i, tb[j + 1] - 1) + 1];
         row_edges[i] += p1 - p0;
@@ -450,7 +742,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   NX_CUDA(cudaEventCreate(&e0));
   NX_CUDA(cudaEventCreate(&e1));
   Scal sc = scal_of(g);
-  uint64_t swept = 0, d2h = 0;
+  uint64_t swept = 0;
   uint32_t done = 0;
   std::vector<uint32_t> act_h(P + 1, 1);
   NX_CUDA(cudaEventRecord(e0, stream()));
@@ -459,18 +751,27 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       NX_CUDA(cudaMemcpyAsync(act_h.data(), g->act[g->cur].p, (size_t)P * 4,
                               cudaMemcpyDeviceToHost, stream()));
       NX_CUDA(cudaStreamSynchronize(stream()));
-      d2h += (uint64_t)P * 4;
+      c.d2h += (uint64_t)P * 4;
     }
     for (uint32_t i = 0; i < P; ++i)
       if (act_h[i]) swept += row_edges[i];
-    if (strat == NX_SPU) NX_TRY(spu_iteration(g, prog, a, n_a));
-    else NX_TRY(dpu_iteration(g, prog, a, n_a, n_b));
+    if (strat == NX_SPU && !streaming) {
+      NX_TRY(spu_iteration(g, prog, a, n_a));
+      ++c.launches;
+    } else if (streaming) {
+      NX_TRY(spu_stream_iteration(c, a, col_off, sm));
+    } else if (!staged) {
+      NX_TRY(dpu_iteration(g, prog, a, n_a, n_b));
+      c.launches += 2;
+    } else {
+      NX_TRY(mpu_iteration(c, a, S));
+    }
     ++done;
     if (is_min(prog)) {
       uint32_t cnt = 0;
       NX_CUDA(cudaMemcpyAsync(&cnt, sc.act_count, 4, cudaMemcpyDeviceToHost, stream()));
       NX_CUDA(cudaStreamSynchronize(stream()));
-      d2h += 4;
+      c.d2h += 4;
       if (cnt == 0) break;
     }
   }
@@ -480,20 +781,29 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   NX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (staged && S.nh) {  // results of the host-side intervals back into the value arrays
+    const int cc = g->cur;
+    const bool has_c = (prog == NX_PR || prog == NX_PPR);
+    NX_CUDA(cudaMemcpyAsync(g->val[cc].as<uint32_t>() + S.n_res, g->hval[cc].p, (size_t)S.nh * 4,
+                            cudaMemcpyHostToDevice, stream()));
+    if (has_c)
+      NX_CUDA(cudaMemcpyAsync(g->aux[cc].as<uint32_t>() + S.n_res, g->hval[cc].as<uint32_t>() + S.nh,
+                              (size_t)S.nh * 4, cudaMemcpyHostToDevice, stream()));
+    NX_CUDA(cudaStreamSynchronize(stream()));
+  }
   if (st) {
     memset(st, 0, sizeof *st);
     st->iters_done = done;
-    st->Q = strat == NX_SPU ? P : (strat == NX_DPU ? 0 : Q);
+    st->Q = (strat == NX_SPU) ? P : Q;
     st->strategy = (uint32_t)strat;
+    st->streamed_cols = streaming ? P - c.Jc : 0;
     st->ms = ms;
     st->edges_swept = swept;
-    st->bytes_model = 0;
-    // algorithmic bytes: edges streamed plus per-vertex traffic of each sweep
-    st->bytes_model = bytes_per_sweep(g, prog, 0) * done + 4 * swept +
-                      (prog == NX_WPR ? 4 * swept : 0);
-    if (strat == NX_DPU) st->bytes_model += (uint64_t)done * 3 * 4 * g->fwd.D;
-    st->d2h_bytes = d2h;
-    st->launches = done * (strat == NX_DPU ? 2u : 1u);
+    st->bytes_model = bytes_per_sweep(g, prog, 0) * done + 4 * swept + (prog == NX_WPR ? 4 * swept : 0);
+    if (strat == NX_DPU && !staged) st->bytes_model += (uint64_t)done * 3 * 4 * g->fwd.D;
+    st->h2d_bytes = c.h2d;
+    st->d2h_bytes = c.d2h;
+    st->launches = c.launches;
   }
   return NX_OK;
 }

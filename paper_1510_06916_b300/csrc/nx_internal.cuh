@@ -147,12 +147,13 @@ struct nx_graph {
   int plan_key = -1;
   uint32_t nitems = 0;
   uint32_t plan_na = 0, plan_nb = 0;
+  std::vector<uint32_t> plan_off;  // item offsets of each launch of the plan
   nx::DevBuf init_part;     // per-block partial sums of the init kernel
   uint64_t split_floats = 0;
   nx::DevBuf tele;          // float [n] teleport copy (PPR/WPR)
   nx::DevBuf lam[2], ybuf;  // adjoint scratch
   nx::DevBuf stage[2];      // staging for streamed shards
-  nx::DevBuf vstage[2];     // staging for non-resident intervals (MPU)
+  nx::DevBuf vstage[4];     // staging for non-resident intervals (MPU)
   nx::PinnedBuf hval[2];    // pinned host values of non-resident intervals
   nx::DevBuf accres;        // MPU resident-column accumulators
   cudaGraphExec_t gexec = nullptr;

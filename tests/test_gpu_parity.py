@@ -250,3 +250,56 @@ def test_full_size_rmat22_p16():
     assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
     st = g.run("pr", 20, "dpu")
     assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), "rmat22 PR DPU")
+
+
+# ------------------------------------------------------------------ budgets
+
+@pytest.mark.parametrize("P", [4, 7])
+def test_mpu_every_q(P):
+    # Section III-B3: Q = floor(B_M P / (2 n B_a)); Q = P is SPU, Q = 0 is DPU.
+    n = 1 << 13
+    s, d, _ = rmat(13, 16, 8)
+    g = nx.Graph(s, d, n, P)
+    ref_pr = oracle.pagerank(n, s, d, 0.85, 20)
+    ref_bfs = oracle.bfs(n, s, d, 0)
+    L = -(-n // P)
+    for Q in range(0, P + 1):
+        budget = max(2 * n * 4 * Q // P + 1, 2 * L * 4)
+        want_q = min(P, (budget * P) // (2 * n * 4))
+        st = g.run("pr", 20, "mpu", budget=budget)
+        assert st["Q"] == want_q and st["strategy"] == (nx.SPU if want_q == P else nx.MPU)
+        assert_pr_close(g.values(), ref_pr, f"MPU P={P} Q={want_q}")
+        st = g.run("bfs", 1000, "mpu", budget=budget, root=0)
+        assert (g.values(dtype=np.uint32) == ref_bfs).all(), (P, Q)
+        if want_q < P:
+            assert st["h2d_bytes"] > 0 and st["d2h_bytes"] > 0
+
+
+def test_dpu_with_small_budget_stages_intervals():
+    n = 1 << 13
+    s, d, _ = rmat(13, 16, 10)
+    g = nx.Graph(s, d, n, 8)
+    L = n // 8
+    st = g.run("pr", 20, "dpu", budget=3 * L * 4)
+    assert st["Q"] == 0 and st["h2d_bytes"] > 0
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), "staged DPU")
+    with pytest.raises(nx.NxError) as e:
+        g.run("pr", 5, "mpu", budget=L * 4)  # below one interval pair
+    assert e.value.code == nx.NX_ERR_BUDGET_TOO_SMALL
+
+
+@pytest.mark.parametrize("frac", [0.0, 0.3, 0.8])
+def test_spu_streams_shards_from_host(frac):
+    n = 1 << 14
+    s, d, _ = rmat(14, 16, 12)
+    g = nx.Graph(s, d, n, 8, transpose=True)
+    m = len(s)
+    budget = 2 * n * 4 + int(frac * 4 * m)
+    st = g.run("pr", 20, "spu", budget=budget)
+    assert st["streamed_cols"] > 0 and st["h2d_bytes"] > 0
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"streamed PR {frac}")
+    g.run("bfs", 1000, "spu", budget=budget, root=0)
+    assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 0)).all()
+    st = g.run("wcc", 1000, "spu", budget=budget + int(frac * 4 * m))
+    assert st["streamed_cols"] > 0
+    assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
