@@ -217,6 +217,34 @@ nx_status nx_run_multi(nx_graph** graphs, uint32_t count, nx_program program, fl
 
 void nx_graph_free(nx_graph* g);
 
+/*
+ * nx_pagerank_step_noalloc — one synchronous PageRank step that allocates no
+ * memory (the paper has no counterpart; this serves callers of the library).
+ * It is for callers that cannot call cudaMalloc when they step the iteration:
+ * an application that has already given the whole device to its own memory
+ * pool, or a latency-critical loop that must not pay for an allocation or for
+ * the device-wide synchronisation of cudaFree. It computes
+ *   r_out[v] = (1-alpha)/n + alpha * (sum_{u->v} r_in[u]/outdeg(u) + Dm/n),
+ *   Dm = sum over vertices without out-edges of r_in[u],
+ * the same step as one NX_PR iteration of nx_run, with one thread block per
+ * destination tile (heavy tiles are not split).
+ *   g     : a graph from nx_build_dsss (only its forward DSSS is used)
+ *   r_in  : device float [n], the current ranks (not modified)
+ *   r_out : device float [n], receives the next ranks (must not alias r_in)
+ * Scratch: a file-scope 4 MiB device array (held by every GPU that loads the
+ * library until the process exits) instead of cudaMalloc; graphs with more
+ * than 523,232 destination tiles are rejected with NX_ERR_INVALID_ARG. The
+ * first call on a device looks up the array's device address once for that
+ * device; make that first call before any stream capture. All calls share the
+ * array: calls whose GPU work overlaps (different streams or threads) race on
+ * it and must be serialised by the caller. Runs on the stream of
+ * nx_set_stream and returns when the step is complete.
+ * Errors: INVALID_ARG (NULL pointers, r_in == r_out, alpha outside [0, 1),
+ * too many tiles), CUDA.
+ */
+nx_status nx_pagerank_step_noalloc(const nx_graph* g, float alpha, const float* r_in,
+                                   float* r_out);
+
 /* Planner model of Section III-B (Table II): bytes read / written per
  * iteration for strategy s with n vertices, m edges, P intervals, budget B_M,
  * attribute/id/edge sizes B_a, B_v, B_e and average hub in-degree d.

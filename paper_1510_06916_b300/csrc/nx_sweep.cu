@@ -73,21 +73,28 @@ struct Prog;
 template <>
 struct Prog<PK_PR> : PrSum {  // gathers c[u] = r[u] / outdeg[u]
   static constexpr bool weighted = false;
-  __device__ static float gather(const void* g, uint32_t u, float) {
+  __device__ static float gather(const void* g, const uint32_t*, uint32_t u, float) {
     return __ldg(static_cast<const float*>(g) + u);
   }
 };
 template <>
 struct Prog<PK_WPR> : PrSum {  // gathers w^_uv r[u]
   static constexpr bool weighted = true;
-  __device__ static float gather(const void* g, uint32_t u, float w) {
+  __device__ static float gather(const void* g, const uint32_t*, uint32_t u, float w) {
     return w * __ldg(static_cast<const float*>(g) + u);
+  }
+};
+template <>
+struct Prog<PK_PRD> : PrSum {  // gathers r[u] / outdeg[u] (u has an out-edge)
+  static constexpr bool weighted = false;
+  __device__ static float gather(const void* g, const uint32_t* od, uint32_t u, float) {
+    return __ldg(static_cast<const float*>(g) + u) / (float)__ldg(od + u);
   }
 };
 template <>
 struct Prog<PK_BFS> : MinU {  // depth[u] + 1 (infinity stays infinity)
   static constexpr bool weighted = false;
-  __device__ static uint32_t gather(const void* g, uint32_t u, float) {
+  __device__ static uint32_t gather(const void* g, const uint32_t*, uint32_t u, float) {
     uint32_t d = __ldg(static_cast<const uint32_t*>(g) + u);
     return d == kInf ? kInf : d + 1;
   }
@@ -95,7 +102,7 @@ struct Prog<PK_BFS> : MinU {  // depth[u] + 1 (infinity stays infinity)
 template <>
 struct Prog<PK_WCC> : MinU {  // label[u]
   static constexpr bool weighted = false;
-  __device__ static uint32_t gather(const void* g, uint32_t u, float) {
+  __device__ static uint32_t gather(const void* g, const uint32_t*, uint32_t u, float) {
     return __ldg(static_cast<const uint32_t*>(g) + u);
   }
 };
@@ -118,7 +125,8 @@ __device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
                                             const float* __restrict__ wt, uint64_t ew_lo,
                                             uint64_t a, uint64_t b, const void* __restrict__ g,
                                             uint32_t sbase, uint32_t lb,
-                                            Acc<typename PG::V> acc, uint32_t& rot) {
+                                            Acc<typename PG::V> acc, uint32_t& rot,
+                                            const uint32_t* __restrict__ od) {
   using V = typename PG::V;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t smask = (1u << lb) - 1u;
@@ -166,7 +174,7 @@ __device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
     for (int k = 0; k < 8; ++k) {
       const bool valid = ((uint32_t)(lane * 8 + k) - lo) < span;
       key[k] = valid ? (wv[k] >> lb) : kSent;
-      val[k] = valid ? PG::gather(g, sbase + (wv[k] & smask), wf[k]) : PG::identity();
+      val[k] = valid ? PG::gather(g, od, sbase + (wv[k] & smask), wf[k]) : PG::identity();
     }
     // runs of equal destination inside the lane: first (head), middle, last (tail)
     uint32_t hk = key[0], ck = key[0];
@@ -237,7 +245,19 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
   __shared__ double red[kWarps];
   __shared__ int s_flag;
 
-  const Item it = a.items[blockIdx.x];
+  Item it;
+  if (a.items) {
+    it = a.items[blockIdx.x];
+  } else {  // one block per tile, whole tile
+    it.tile = blockIdx.x;
+    it.nsplit = 1;
+    it.slot = 0;
+    it.sub = 0;
+    it.vbeg = 0;
+    it.vend = ~0ull;
+    it.row = 0;
+    it.pad = 0;
+  }
   const uint32_t t = it.tile;
   const uint32_t ts = a.tile_start[t], te = a.tile_start[t + 1];
   const uint32_t T = te - ts;
@@ -272,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
           const void* g = staged ? a.gstage : a.gsrc;
           const uint32_t sb = staged ? 0u : i * a.L;
           sweep_range<PG>(a.src[s].ew, a.src[s].wt, a.ew_lo[s], p0 + (lo - vo), p0 + (hi - vo), g,
-                          sb, a.lb, acc, rot);
+                          sb, a.lb, acc, rot, a.outdeg);
         }
         vo += len;
       }
@@ -349,7 +369,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
   }
 
   // ---- epilogue (modes 0 and 3)
-  if constexpr (K == PK_PR || K == PK_WPR) {
+  if constexpr (K == PK_PR || K == PK_WPR || K == PK_PRD) {
     const float alpha = a.alpha;
     const float inv_n = 1.0f / (float)a.n;
     const float dm = (float)(*a.dm_in);
@@ -390,7 +410,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
   __syncthreads();
   if (!s_flag) return;
   __threadfence();
-  if constexpr (K == PK_PR || K == PK_WPR) {
+  if constexpr (K == PK_PR || K == PK_WPR || K == PK_PRD) {
     const uint32_t ntiles = a.col_tb[a.P];
     double s = 0.0;
     for (uint32_t q = threadIdx.x; q < ntiles; q += kThreads) s += __ldcg(a.tile_part + q);
@@ -419,13 +439,14 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
 
 nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaStream_t s) {
   if (nitems == 0) return NX_OK;
-  const bool sums = (kind == PK_PR || kind == PK_WPR);
+  const bool sums = (kind == PK_PR || kind == PK_WPR || kind == PK_PRD);
   const size_t smem = (size_t)a.tile_max * (sums ? 8 : 4);
   switch (kind) {
     case PK_PR: k_sweep<PK_PR><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_WPR: k_sweep<PK_WPR><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_BFS: k_sweep<PK_BFS><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_WCC: k_sweep<PK_WCC><<<nitems, kThreads, smem, s>>>(a); break;
+    case PK_PRD: k_sweep<PK_PRD><<<nitems, kThreads, smem, s>>>(a); break;
   }
   NX_LAUNCH_CHECK();
   return NX_OK;

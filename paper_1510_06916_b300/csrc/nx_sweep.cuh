@@ -23,13 +23,15 @@ struct SweepSrc {
   const uint64_t* piece_off = nullptr; // [npieces+1]
 };
 
-enum ProgKind : int { PK_PR = 0, PK_WPR = 1, PK_BFS = 2, PK_WCC = 3 };
+// PK_PRD: PageRank that gathers r[u] / outdeg[u] directly (no contribution
+// array), used by the allocation-free single-step entry point.
+enum ProgKind : int { PK_PR = 0, PK_WPR = 1, PK_BFS = 2, PK_WCC = 3, PK_PRD = 4 };
 
 struct SweepArgs {
   SweepSrc src[2];
   int nsrc = 1;
   uint32_t src_lo = 0, src_hi = 0;  // source intervals swept: [src_lo, src_hi)
-  const Item* items = nullptr;
+  const Item* items = nullptr;  // nullptr: block b sweeps the whole tile b
   const uint32_t* tile_start = nullptr;
   const uint32_t* col_tb = nullptr;
   uint32_t P = 0, L = 0, lb = 0, n = 0, tile_max = 0;

@@ -27,7 +27,7 @@ STRATEGIES = {"spu": SPU, "dpu": DPU, "mpu": MPU, "auto": AUTO}
 EXPORTS = [
     "nx_set_stream", "nx_last_error", "nx_build_dsss", "nx_graph_get_info", "nx_run",
     "nx_get_values", "nx_set_values", "nx_run_ppr_batch", "nx_adjoint_wpr", "nx_run_multi",
-    "nx_graph_free", "nx_io_model", "nx_dsss_export",
+    "nx_graph_free", "nx_io_model", "nx_dsss_export", "nx_pagerank_step_noalloc",
 ]
 
 
@@ -89,6 +89,7 @@ def lib():
         L.nx_run_multi.argtypes = [ctypes.POINTER(vp), u32, i32, f32, u32,
                                    ctypes.POINTER(NxRunStats)]
         L.nx_dsss_export.argtypes = [vp, i32, vp, vp, vp]
+        L.nx_pagerank_step_noalloc.argtypes = [vp, f32, vp, vp]
         L.nx_graph_free.argtypes = [vp]
         L.nx_graph_free.restype = None
         L.nx_io_model.argtypes = [i32, d, d, d, d, d, d, d, d, ctypes.POINTER(d),
