@@ -303,3 +303,38 @@ def test_spu_streams_shards_from_host(frac):
     st = g.run("wcc", 1000, "spu", budget=budget + int(frac * 4 * m))
     assert st["streamed_cols"] > 0
     assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+
+
+# ------------------------------------------------------------------ batched PPR
+
+@pytest.mark.parametrize("B", [1, 8, 33, 64])
+def test_ppr_batch_matches_per_vector_oracle(B):
+    n = 1 << 13
+    s, d, _ = rmat(13, 16, 14)
+    T = inputs.ppr_teleports(n, B, 3, max_seeds=50)
+    T[:, 0] = 1.0 / n  # one uniform column: equals global PageRank
+    g = nx.Graph(s, d, n, 4)
+    R, st = g.ppr_batch(T, iters=30)
+    assert st["iters_done"] == 30
+    for b in range(B):
+        ref = oracle.personalized_pagerank(n, s, d, T[:, b], 0.85, 30)
+        assert_pr_close(R[:, b], ref, f"batch B={B} col {b}")
+    assert_pr_close(R[:, 0], oracle.pagerank(n, s, d, 0.85, 30), "uniform column")
+
+
+def test_ppr_batch_device_pointers_and_hub():
+    import torch
+    k = 100_000
+    n = k + 1
+    s = np.concatenate([np.arange(1, n, dtype=np.uint32), np.array([0], np.uint32)])
+    d = np.concatenate([np.zeros(k, np.uint32), np.array([9], np.uint32)])
+    T = inputs.ppr_teleports(n, 5, 8, max_seeds=20)
+    g = nx.Graph(s, d, n, 2)
+    Tt = torch.from_numpy(T).cuda()
+    R, _ = g.ppr_batch(Tt, iters=20)
+    R = R.cpu().numpy()
+    for b in range(5):
+        ref = oracle.personalized_pagerank(n, s, d, T[:, b], 0.85, 20)
+        assert_pr_close(R[:, b], ref, f"hub batch col {b}")
+    R0, _ = g.ppr_batch(T, iters=0)
+    assert np.array_equal(R0, T)
