@@ -186,14 +186,21 @@ nx_status prepare(nx_graph* g) {
   return NX_OK;
 }
 
-nx_status upload_items(nx_graph* g, const PlanOut& plan) {
-  NX_TRY(ensure(g->items, std::max<size_t>(plan.items.size(), 1) * sizeof(Item)));
+nx_status upload_items(nx_graph* g, const PlanOut& plan, nx_graph::Plan& dst) {
+  NX_TRY(dst.items.alloc(std::max<size_t>(plan.items.size(), 1) * sizeof(Item)));
   if (!plan.items.empty())
-    NX_CUDA(cudaMemcpyAsync(g->items.p, plan.items.data(), plan.items.size() * sizeof(Item),
+    NX_CUDA(cudaMemcpyAsync(dst.items.p, plan.items.data(), plan.items.size() * sizeof(Item),
                             cudaMemcpyHostToDevice, stream()));
-  const uint64_t need = (uint64_t)plan.slots * g->geo.tile_max * 8;  // hi + lo per slot
-  NX_TRY(ensure(g->split_buf, std::max<uint64_t>(need, 4)));
+  dst.slots = plan.slots;
   return NX_OK;
+}
+
+// Split slots are transient within a launch: one buffer sized for the largest plan.
+nx_status ensure_split(nx_graph* g, uint32_t slots) {
+  const uint64_t need = (uint64_t)slots * g->geo.tile_max * 8;  // hi + lo per slot
+  if (g->split_buf.bytes >= std::max<uint64_t>(need, 4)) return NX_OK;
+  NX_CUDA(cudaStreamSynchronize(stream()));
+  return g->split_buf.alloc(std::max<uint64_t>(need, 4));
 }
 
 // ---------------------------------------------------------------- initialize
@@ -320,7 +327,7 @@ nx_status spu_iteration(nx_graph* g, nx_program prog, SweepArgs& a, uint32_t nit
 nx_status dpu_iteration(nx_graph* g, nx_program prog, SweepArgs& a, uint32_t n_tohub,
                         uint32_t n_fromhub) {
   set_iter_ptrs(g, prog, a);
-  const Item* all = g->items.as<Item>();
+  const Item* all = a.items;
   SweepArgs th = a;
   th.mode = 1;
   th.q_res = 0;
@@ -394,7 +401,7 @@ nx_status spu_stream_iteration(RunCtx& c, SweepArgs& a, const std::vector<uint32
   nx_graph* g = c.g;
   set_iter_ptrs(g, c.prog, a);
   a.mode = 0;
-  const Item* all = g->items.as<Item>();
+  const Item* all = a.items;
   // resident columns
   SweepArgs r = a;
   r.items = all;
@@ -442,7 +449,7 @@ nx_status mpu_iteration(RunCtx& c, SweepArgs& a, Staged& S) {
   const bool has_c = (c.prog == NX_PR || c.prog == NX_PPR);
   const int cur = g->cur, nxt = 1 - g->cur;
   set_iter_ptrs(g, c.prog, a);
-  const Item* all = g->items.as<Item>();
+  const Item* all = a.items;
   const ProgKind K = kind_of(c.prog);
   uint32_t li = 0;  // launch index into S.off
   auto items_of = [&](uint32_t k) { return std::make_pair(all + S.off[k], S.off[k + 1] - S.off[k]); };
@@ -598,6 +605,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   }
   g->values_set_for = -1;
   g->last_prog = (int)prog;
+  if (prog == NX_WPR) g->wpr_alpha = p.alpha;
 
   RunCtx c;
   c.g = g;
@@ -633,17 +641,18 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   // plan (cached: the graph never changes)
   const int key = ((int)strat * 16 + (int)c.ds.size()) * 4096 + (int)(staged ? Q + 1 : 0) +
                   (streaming ? (int)(c.Jc + 2048) : 0);
-  uint32_t n_a = g->plan_na, n_b = g->plan_nb;
-  static thread_local std::vector<uint32_t> launch_off;  // per-launch item offsets
-  if (g->plan_key != key) {
+  auto& slot_plan = g->plans[key];
+  if (!slot_plan) {
+    slot_plan.reset(new nx_graph::Plan());
+    nx_graph::Plan& pl = *slot_plan;
     const uint64_t total = g->m * c.ds.size();
     const uint64_t blk = target_block_edges(total);
     PlanOut plan;
-    launch_off.clear();
+    std::vector<uint32_t> launch_off;
+    uint32_t n_a = 0, n_b = 0;
     if (strat == NX_SPU && !streaming) {
       plan_tiles(g, c.ds, 0, P, 0, P, true, blk, plan);
       n_a = (uint32_t)plan.items.size();
-      n_b = 0;
     } else if (strat == NX_SPU) {  // per column groups: [0, Jc) then one per streamed column
       launch_off.assign(P + 1, 0);
       plan_tiles(g, c.ds, 0, P, 0, c.Jc, true, blk, plan);
@@ -672,16 +681,18 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
         launch_off.push_back((uint32_t)plan.items.size());
       }
     }
-    NX_TRY(upload_items(g, plan));
-    g->plan_key = key;
-    g->plan_na = n_a;
-    g->plan_nb = n_b;
-    g->plan_off = launch_off;
+    NX_TRY(upload_items(g, plan, pl));
+    pl.na = n_a;
+    pl.nb = n_b;
+    pl.off = launch_off;
   }
+  nx_graph::Plan& pl = *slot_plan;
+  NX_TRY(ensure_split(g, pl.slots));
+  const uint32_t n_a = pl.na, n_b = pl.nb;
   if (strat == NX_DPU || staged) NX_TRY(ensure(g->hubs, std::max<uint64_t>(g->fwd.D, 1) * 4));
 
   SweepArgs a = base_args(g, prog, p, tele);
-  a.items = g->items.as<Item>();
+  a.items = pl.items.as<Item>();
   a.split = g->split_buf.p;
 
   // streaming buffers
@@ -698,7 +709,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       }
     for (int b = 0; b < 2; ++b) NX_TRY(ensure(g->stage[b], maxw * 4 * 2));
     NX_TRY(sm.init());
-    col_off = g->plan_off;
+    col_off = pl.off;
   }
   // staged intervals (MPU): device accumulators for resident columns, pinned
   // host arrays for the rest, per-interval staging buffers
@@ -706,7 +717,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   if (staged) {
     S.n_res = std::min<uint64_t>((uint64_t)Q * L, n);
     S.nh = n - S.n_res;
-    S.off = g->plan_off;
+    S.off = pl.off;
     NX_TRY(ensure(g->accres, std::max<size_t>(S.n_res, 1) * 4));
     for (int b = 0; b < 4; ++b) NX_TRY(ensure(g->vstage[b], (size_t)L * 4));
     const bool has_c = (prog == NX_PR || prog == NX_PPR);
@@ -808,6 +819,157 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   return NX_OK;
 }
 
+// ---------------------------------------------------------------- adjoint
+// dL/dw_e = a r_u / W_u (lambda_v - y_u) for edge e = (u, v) in caller order;
+// dL/dt_v = (1 - a) lambda_v.
+__global__ void k_edge_grad(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                            uint64_t m, const float* __restrict__ r, const float* __restrict__ W,
+                            const float* __restrict__ lam, const float* __restrict__ y, float alpha,
+                            float* __restrict__ dw) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const uint32_t u = src[e], v = dst[e];
+    dw[e] = alpha * __ldg(r + u) / __ldg(W + u) * (__ldg(lam + v) - __ldg(y + u));
+  }
+}
+
+__global__ void k_scale(const float* __restrict__ x, uint32_t n, float f, float* __restrict__ out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    out[v] = f * x[v];
+}
+
+__global__ void k_partial_sum(const float* __restrict__ x, uint32_t n, double* __restrict__ part) {
+  __shared__ double red[8];
+  double s = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    s += (double)x[v];
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    part[blockIdx.x] = t;
+  }
+}
+
+constexpr int kAdjPlanKey = -7;
+
+nx_status adjoint_impl(nx_graph* g, const float* grad_r, uint32_t K, float* grad_w, float* grad_t,
+                       int dev, nx_run_stats* st) {
+  const uint32_t n = g->geo.n, P = g->geo.P;
+  const uint64_t m = g->m;
+  cudaStream_t s = stream();
+  NX_TRY(prepare(g));
+  for (int k = 0; k < 2; ++k) NX_TRY(ensure(g->lam[k], (size_t)n * 4));
+  NX_TRY(ensure(g->ybuf, (size_t)n * 4));
+  NX_TRY(ensure(g->tele, (size_t)n * 4));  // holds g = dL/dr
+  NX_CUDA(cudaMemcpyAsync(g->tele.p, grad_r, (size_t)n * 4,
+                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  NX_CUDA(cudaMemcpyAsync(g->lam[0].p, g->tele.p, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  // S0 = sum of lambda^0
+  Scal sc = scal_of(g);
+  const unsigned gb = grid_for(n);
+  NX_TRY(ensure(g->init_part, (size_t)gb * 8));
+  k_partial_sum<<<gb, 256, 0, s>>>(g->lam[0].as<float>(), n, g->init_part.as<double>());
+  k_sum_parts<<<1, 256, 0, s>>>(g->init_part.as<double>(), gb, sc.dm);
+  NX_LAUNCH_CHECK();
+  // plan over the transpose DSSS
+  auto& slot = g->plans[kAdjPlanKey];
+  if (!slot) {
+    slot.reset(new nx_graph::Plan());
+    PlanOut plan;
+    std::vector<const Dsss*> ds{&g->tr};
+    plan_tiles(g, ds, 0, P, 0, P, true, target_block_edges(m), plan);
+    NX_TRY(upload_items(g, plan, *slot));
+    slot->na = (uint32_t)plan.items.size();
+  }
+  NX_TRY(ensure_split(g, slot->slots));
+  nx_params p{};
+  p.alpha = g->wpr_alpha;
+  SweepArgs a = base_args(g, NX_WPR, p, nullptr);
+  a.src[0].ew = g->tr.ew.as<uint32_t>();
+  a.src[0].wt = g->tr.wt.as<float>();
+  a.src[0].piece_off = g->tr.piece_off.as<uint64_t>();
+  a.nsrc = 1;
+  a.items = slot->items.as<Item>();
+  a.split = g->split_buf.p;
+  a.tele = g->tele.as<float>();
+  a.alpha = g->wpr_alpha;
+  cudaEvent_t e0, e1;
+  NX_CUDA(cudaEventCreate(&e0));
+  NX_CUDA(cudaEventCreate(&e1));
+  NX_CUDA(cudaEventRecord(e0, s));
+  int cur = 0;
+  uint32_t launches = 0;
+  for (uint32_t k = 1; k < K; ++k) {  // lambda^{k} = M^T lambda^{k-1} + g
+    SweepArgs b = a;
+    b.mode = 0;
+    b.gsrc = g->lam[cur].p;
+    b.vnew = g->lam[1 - cur].p;
+    b.dm_in = sc.dm + cur;
+    b.dm_out = sc.dm + 1 - cur;
+    NX_TRY(launch_sweep(PK_ADJ, b, slot->na, s));
+    ++launches;
+    cur = 1 - cur;
+  }
+  {  // y_u = sum_v w^_uv lambda_v: the same sweep, raw accumulators stored
+    SweepArgs b = a;
+    b.mode = 2;
+    b.gsrc = g->lam[cur].p;
+    b.accres = g->ybuf.p;
+    NX_TRY(launch_sweep(PK_WPR, b, slot->na, s));
+    ++launches;
+  }
+  DevBuf dw_dev;
+  float* dwp = grad_w;
+  if (!dev) {
+    NX_TRY(dw_dev.alloc(std::max<uint64_t>(m, 1) * 4));
+    dwp = dw_dev.as<float>();
+  }
+  if (m) {
+    k_edge_grad<<<grid_for(m), 256, 0, s>>>(g->orig_src.as<uint32_t>(), g->orig_dst.as<uint32_t>(),
+                                            m, g->val[g->cur].as<float>(), g->wsum.as<float>(),
+                                            g->lam[cur].as<float>(), g->ybuf.as<float>(),
+                                            g->wpr_alpha, dwp);
+    NX_LAUNCH_CHECK();
+    ++launches;
+  }
+  NX_CUDA(cudaEventRecord(e1, s));
+  if (!dev && m) NX_CUDA(cudaMemcpyAsync(grad_w, dwp, m * 4, cudaMemcpyDeviceToHost, s));
+  if (grad_t) {
+    DevBuf dt_dev;
+    float* dtp = grad_t;
+    if (!dev) {
+      NX_TRY(dt_dev.alloc((size_t)n * 4));
+      dtp = dt_dev.as<float>();
+    }
+    k_scale<<<grid_for(n), 256, 0, s>>>(g->lam[cur].as<float>(), n, 1.0f - g->wpr_alpha, dtp);
+    NX_LAUNCH_CHECK();
+    if (!dev) NX_CUDA(cudaMemcpyAsync(grad_t, dtp, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    NX_CUDA(cudaStreamSynchronize(s));
+  }
+  NX_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  NX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  NX_CUDA(cudaStreamSynchronize(s));
+  if (st) {
+    memset(st, 0, sizeof *st);
+    st->iters_done = K;
+    st->Q = P;
+    st->ms = ms;
+    st->edges_swept = m * K;
+    // K transpose sweeps (edge word + weight per edge, 16 n per sweep) + the edge pass
+    st->bytes_model = (uint64_t)K * (8 * m + 16 * (uint64_t)n) + m * (4 + 4 + 4 + 4 * 4);
+    st->launches = launches;
+  }
+  return NX_OK;
+}
+
 }  // namespace
 }  // namespace nx
 
@@ -842,6 +1004,18 @@ extern "C" nx_status nx_run(nx_graph* g, nx_program program, const nx_params* pa
   if (params) p = *params;
   if (!(p.alpha >= 0.f && p.alpha < 1.f)) return nx::invalid("nx_run: alpha must be in [0, 1)");
   return nx::run_impl(g, program, p, iters, strategy, mem_budget_bytes, stats);
+}
+
+extern "C" nx_status nx_adjoint_wpr(nx_graph* g, const float* grad_r, uint32_t adj_terms,
+                                    float* grad_w, float* grad_t, int32_t ptrs_are_device,
+                                    nx_run_stats* stats) {
+  if (!g || !grad_r || !grad_w) return nx::invalid("nx_adjoint_wpr: NULL argument");
+  if (!g->has_w || !g->has_tr)
+    return nx::invalid("nx_adjoint_wpr: needs NX_WITH_WEIGHTS and NX_WITH_TRANSPOSE");
+  if (g->last_prog != NX_WPR)
+    return nx::invalid("nx_adjoint_wpr: run NX_WPR first (its ranks are the forward state)");
+  if (adj_terms == 0) return nx::invalid("nx_adjoint_wpr: adj_terms must be >= 1");
+  return nx::adjoint_impl(g, grad_r, adj_terms, grad_w, grad_t, ptrs_are_device, stats);
 }
 
 extern "C" nx_status nx_get_values(const nx_graph* g, void* out, uint64_t count,

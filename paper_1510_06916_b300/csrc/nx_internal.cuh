@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -142,16 +144,19 @@ struct nx_graph {
   nx::DevBuf tile_part;     // double [ntiles] per-tile dangling partials
   nx::DevBuf split_buf;     // split-tile partial accumulators
   nx::DevBuf tile_ticket;   // uint32 [ntiles]
-  nx::DevBuf items;         // work items of the current plan
   nx::DevBuf hubs;          // hub values [D]
-  int plan_key = -1;
-  uint32_t nitems = 0;
-  uint32_t plan_na = 0, plan_nb = 0;
-  std::vector<uint32_t> plan_off;  // item offsets of each launch of the plan
+  // Work plans (item lists) cached by strategy / DSSS set / placement.
+  struct Plan {
+    nx::DevBuf items;
+    uint32_t na = 0, nb = 0, slots = 0;
+    std::vector<uint32_t> off;  // item offsets of each launch of the plan
+  };
+  std::map<int, std::unique_ptr<Plan>> plans;
   nx::DevBuf init_part;     // per-block partial sums of the init kernel
   uint64_t split_floats = 0;
   nx::DevBuf tele;          // float [n] teleport copy (PPR/WPR)
   nx::DevBuf lam[2], ybuf;  // adjoint scratch
+  float wpr_alpha = 0.85f;  // damping of the last weighted PageRank run
   nx::DevBuf stage[2];      // staging for streamed shards
   nx::DevBuf vstage[4];     // staging for non-resident intervals (MPU)
   nx::PinnedBuf hval[2];    // pinned host values of non-resident intervals

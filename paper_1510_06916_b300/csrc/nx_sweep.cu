@@ -85,6 +85,13 @@ struct Prog<PK_WPR> : PrSum {  // gathers w^_uv r[u]
   }
 };
 template <>
+struct Prog<PK_ADJ> : PrSum {  // gathers w^_uv lambda[v] over the transpose DSSS
+  static constexpr bool weighted = true;
+  __device__ static float gather(const void* g, const uint32_t*, uint32_t u, float w) {
+    return w * __ldg(static_cast<const float*>(g) + u);
+  }
+};
+template <>
 struct Prog<PK_PRD> : PrSum {  // gathers r[u] / outdeg[u] (u has an out-edge)
   static constexpr bool weighted = false;
   __device__ static float gather(const void* g, const uint32_t* od, uint32_t u, float) {
@@ -369,7 +376,22 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
   }
 
   // ---- epilogue (modes 0 and 3)
-  if constexpr (K == PK_PR || K == PK_WPR || K == PK_PRD) {
+  if constexpr (K == PK_ADJ) {
+    // lambda' = g + a (acc + [dangling] S / n); the fold sums lambda' over all vertices
+    const float alpha = a.alpha;
+    const float sn = (float)(*a.dm_in) / (float)a.n;
+    float* ln = static_cast<float*>(a.vnew);
+    double part = 0.0;
+    for (uint32_t k = threadIdx.x; k < T; k += kThreads) {
+      const uint32_t v = ts + k;
+      const float dang = a.outdeg[v] == 0 ? sn : 0.0f;
+      const float l = a.tele[v] + alpha * (PG::read(acc, k) + dang);
+      ln[v] = l;
+      part += (double)l;
+    }
+    const double tot = block_sum_d(part, red);
+    if (threadIdx.x == 0) a.tile_part[t] = tot;
+  } else if constexpr (K == PK_PR || K == PK_WPR || K == PK_PRD) {
     const float alpha = a.alpha;
     const float inv_n = 1.0f / (float)a.n;
     const float dm = (float)(*a.dm_in);
@@ -410,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
   __syncthreads();
   if (!s_flag) return;
   __threadfence();
-  if constexpr (K == PK_PR || K == PK_WPR || K == PK_PRD) {
+  if constexpr (K == PK_PR || K == PK_WPR || K == PK_PRD || K == PK_ADJ) {
     const uint32_t ntiles = a.col_tb[a.P];
     double s = 0.0;
     for (uint32_t q = threadIdx.x; q < ntiles; q += kThreads) s += __ldcg(a.tile_part + q);
@@ -439,7 +461,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
 
 nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaStream_t s) {
   if (nitems == 0) return NX_OK;
-  const bool sums = (kind == PK_PR || kind == PK_WPR || kind == PK_PRD);
+  const bool sums = (kind == PK_PR || kind == PK_WPR || kind == PK_PRD || kind == PK_ADJ);
   const size_t smem = (size_t)a.tile_max * (sums ? 8 : 4);
   switch (kind) {
     case PK_PR: k_sweep<PK_PR><<<nitems, kThreads, smem, s>>>(a); break;
@@ -447,6 +469,7 @@ nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaS
     case PK_BFS: k_sweep<PK_BFS><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_WCC: k_sweep<PK_WCC><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_PRD: k_sweep<PK_PRD><<<nitems, kThreads, smem, s>>>(a); break;
+    case PK_ADJ: k_sweep<PK_ADJ><<<nitems, kThreads, smem, s>>>(a); break;
   }
   NX_LAUNCH_CHECK();
   return NX_OK;

@@ -25,7 +25,9 @@ struct SweepSrc {
 
 // PK_PRD: PageRank that gathers r[u] / outdeg[u] directly (no contribution
 // array), used by the allocation-free single-step entry point.
-enum ProgKind : int { PK_PR = 0, PK_WPR = 1, PK_BFS = 2, PK_WCC = 3, PK_PRD = 4 };
+// PK_ADJ: the weighted-PageRank adjoint step over the transpose DSSS,
+// lambda'_u = g_u + a (sum_v w^_uv lambda_v + [outdeg(u) = 0] S / n), S = sum lambda.
+enum ProgKind : int { PK_PR = 0, PK_WPR = 1, PK_BFS = 2, PK_WCC = 3, PK_PRD = 4, PK_ADJ = 5 };
 
 struct SweepArgs {
   SweepSrc src[2];

@@ -338,3 +338,54 @@ def test_ppr_batch_device_pointers_and_hub():
         assert_pr_close(R[:, b], ref, f"hub batch col {b}")
     R0, _ = g.ppr_batch(T, iters=0)
     assert np.array_equal(R0, T)
+
+
+# ------------------------------------------------------------------ adjoint
+
+def _grad_close(got, ref, what, rel_l1=1e-5):
+    got = got.astype(np.float64)
+    l1 = np.abs(got - ref).sum() / max(np.abs(ref).sum(), 1e-300)
+    floor = 1e-4 * np.abs(ref).max()
+    big = np.abs(ref) > floor
+    rel = (np.abs(got - ref)[big] / np.abs(ref[big])).max() if big.any() else 0.0
+    print(f"{what}: rel_L1={l1:.3e} max_rel={rel:.3e}")
+    assert l1 <= rel_l1 and rel <= 1e-3, (what, l1, rel)
+
+
+def test_adjoint_matches_fp64_oracle():
+    n = 1 << 13
+    s, d, w = rmat(13, 16, 4, weights=True)
+    T = inputs.targets(n, 64, 4)
+    gvec = np.zeros(n, np.float32)
+    gvec[T] = 1.0
+    g = nx.Graph(s, d, n, 8, transpose=True, weights=w)
+    g.run("wpr", 50)
+    dw = np.empty(len(s), np.float32)
+    dt = np.empty(n, np.float32)
+    st = g.adjoint_wpr(gvec, 50, dw, dt)
+    ref = oracle.wpr_adjoint(n, s, d, w.astype(np.float64), gvec.astype(np.float64), 0.85, 50, 50)
+    _grad_close(dt, ref["dt"], "dL/dt")
+    _grad_close(dw, ref["dw"], "dL/dw")
+    assert st["iters_done"] == 50
+
+
+def test_autograd_function():
+    import torch
+    from paper_1510_06916_b300.autograd import weighted_pagerank
+    n = 1 << 12
+    s, d, w = rmat(12, 16, 6, weights=True)
+    T = inputs.targets(n, 32, 6)
+    src = torch.from_numpy(s.view(np.int32)).cuda()
+    dst = torch.from_numpy(d.view(np.int32)).cuda()
+    wt = torch.from_numpy(w).cuda().requires_grad_(True)
+    t = torch.full((n,), 1.0 / n, device="cuda", requires_grad=True)
+    r = weighted_pagerank(wt, t, src, dst, n, 4, iters=50, adj_terms=50)
+    loss = r[torch.from_numpy(T).cuda()].sum()
+    loss.backward()
+    gv = np.zeros(n)
+    gv[T] = 1.0
+    ref = oracle.wpr_adjoint(n, s, d, w.astype(np.float64), gv, 0.85, 50, 50,
+                             tele=np.full(n, 1.0 / n))
+    assert_pr_close(r.detach().cpu().numpy(), ref["r"], "autograd forward")
+    _grad_close(wt.grad.cpu().numpy(), ref["dw"], "autograd dw")
+    _grad_close(t.grad.cpu().numpy(), ref["dt"], "autograd dt")
