@@ -75,6 +75,7 @@ bool is_min(nx_program p) { return p == NX_BFS || p == NX_WCC; }
 // ---------------------------------------------------------------- plans
 struct PlanOut {
   std::vector<Item> items;
+  std::vector<uint64_t> cost;  // edges per item (sort key)
   uint32_t slots = 0;
 };
 
@@ -117,7 +118,10 @@ void plan_tiles(const nx_graph* g, const std::vector<const Dsss*>& ds, uint32_t 
     }
   std::stable_sort(tmp.begin(), tmp.end(),
                    [](const auto& a, const auto& b) { return a.first > b.first; });
-  for (auto& p : tmp) out.items.push_back(p.second);
+  for (auto& p : tmp) {
+    out.items.push_back(p.second);
+    out.cost.push_back(p.first);
+  }
 }
 
 // Single pieces (i, t) of row i for tiles of columns [c0, c1) (ToHub / row pass).
@@ -145,7 +149,10 @@ void plan_row(const nx_graph* g, const Dsss& d, uint32_t i, uint32_t c0, uint32_
     }
   std::stable_sort(tmp.begin(), tmp.end(),
                    [](const auto& a, const auto& b) { return a.first > b.first; });
-  for (auto& p : tmp) out.items.push_back(p.second);
+  for (auto& p : tmp) {
+    out.items.push_back(p.second);
+    out.cost.push_back(p.first);
+  }
 }
 
 // ---------------------------------------------------------------- buffers
@@ -191,7 +198,10 @@ nx_status upload_items(nx_graph* g, const PlanOut& plan, nx_graph::Plan& dst) {
   if (!plan.items.empty())
     NX_CUDA(cudaMemcpyAsync(dst.items.p, plan.items.data(), plan.items.size() * sizeof(Item),
                             cudaMemcpyHostToDevice, stream()));
+  NX_CUDA(cudaStreamSynchronize(stream()));  // plan.items is a host temporary
   dst.slots = plan.slots;
+  dst.h_cost = plan.cost;
+  dst.h_items = plan.items;
   return NX_OK;
 }
 
@@ -970,6 +980,139 @@ nx_status adjoint_impl(nx_graph* g, const float* grad_r, uint32_t K, float* grad
   return NX_OK;
 }
 
+// ---------------------------------------------------------------- many graphs
+nx_status multi_impl(nx_graph** gs, uint32_t count, nx_program prog, float alpha, uint32_t iters,
+                     nx_run_stats* st) {
+  nx_params p{};
+  p.alpha = alpha;
+  p.root = 0;
+  const ProgKind K = kind_of(prog);
+  std::vector<SweepArgs> args(2 * (size_t)count);
+  std::vector<MItem> items;
+  std::vector<uint64_t> costs;
+  uint32_t tile_max = 1;
+  uint64_t edges = 0;
+  for (uint32_t gi = 0; gi < count; ++gi) {
+    nx_graph* g = gs[gi];
+    NX_TRY(prepare(g));
+    NX_TRY(initialize(g, prog, p, nullptr, nullptr));  // sets cur = 0
+    g->values_set_for = -1;
+    g->last_prog = (int)prog;
+    std::vector<const Dsss*> ds{&g->fwd};
+    if (prog == NX_WCC) ds.push_back(&g->tr);
+    const int key = ((int)NX_SPU * 16 + (int)ds.size()) * 4096;
+    auto& slot = g->plans[key];
+    if (!slot) {
+      slot.reset(new nx_graph::Plan());
+      PlanOut plan;
+      plan_tiles(g, ds, 0, g->geo.P, 0, g->geo.P, true, target_block_edges(g->m * ds.size()), plan);
+      NX_TRY(upload_items(g, plan, *slot));
+      slot->na = (uint32_t)plan.items.size();
+    }
+    NX_TRY(ensure_split(g, slot->slots));
+    SweepArgs a = base_args(g, prog, p, nullptr);
+    a.items = nullptr;
+    a.split = g->split_buf.p;
+    for (int par = 0; par < 2; ++par) {
+      g->cur = par;
+      set_iter_ptrs(g, prog, a);
+      args[2 * (size_t)gi + par] = a;
+    }
+    g->cur = 0;
+    for (size_t q = 0; q < slot->h_items.size(); ++q) {
+      MItem mi;
+      mi.gid = gi;
+      mi.pad = 0;
+      mi.it = slot->h_items[q];
+      items.push_back(mi);
+      costs.push_back(slot->h_cost[q]);
+    }
+    tile_max = std::max(tile_max, g->geo.tile_max);
+    edges += g->m * ds.size();
+  }
+  // heaviest items first over all graphs
+  std::vector<uint32_t> order(items.size());
+  for (uint32_t q = 0; q < order.size(); ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](uint32_t x, uint32_t y) { return costs[x] > costs[y]; });
+  std::vector<MItem> sorted(items.size());
+  for (size_t q = 0; q < order.size(); ++q) sorted[q] = items[order[q]];
+  DevBuf d_args, d_items, d_ctr, d_sync;
+  NX_TRY(d_args.alloc(args.size() * sizeof(SweepArgs)));
+  NX_TRY(d_items.alloc(std::max<size_t>(sorted.size(), 1) * sizeof(MItem)));
+  NX_TRY(d_ctr.alloc(std::max<size_t>(iters, 1) * 4));
+  NX_TRY(d_sync.alloc(sizeof(MultiSync)));
+  cudaStream_t s = stream();
+  NX_CUDA(cudaMemcpyAsync(d_args.p, args.data(), args.size() * sizeof(SweepArgs),
+                          cudaMemcpyHostToDevice, s));
+  if (!sorted.empty())
+    NX_CUDA(cudaMemcpyAsync(d_items.p, sorted.data(), sorted.size() * sizeof(MItem),
+                            cudaMemcpyHostToDevice, s));
+  NX_CUDA(cudaStreamSynchronize(s));
+  uint32_t nblocks = 0;
+  NX_TRY(multi_blocks(K, tile_max, &nblocks));
+  // the whole iteration loop as one CUDA graph: counters reset, then the kernel
+  cudaStream_t cs = nullptr;
+  NX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  nx_status rc = NX_OK;
+  {
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaMemsetAsync(d_ctr.p, 0, std::max<size_t>(iters, 1) * 4, cs);
+      cudaMemsetAsync(d_sync.p, 0, sizeof(MultiSync), cs);
+      rc = launch_multi(K, d_args.as<SweepArgs>(), d_items.as<MItem>(), (uint32_t)sorted.size(),
+                        iters, d_ctr.as<uint32_t>(), d_sync.as<MultiSync>(), tile_max, nblocks, cs);
+      cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+      if (rc == NX_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture", __FILE__, __LINE__);
+    } else {
+      rc = cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+    }
+  }
+  if (rc == NX_OK) {
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  }
+  float ms = 0.f;
+  if (rc == NX_OK) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    cudaError_t e = cudaGraphLaunch(exec, s);
+    cudaEventRecord(e1, s);
+    cudaError_t e3 = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__);
+    else if (e3 != cudaSuccess) rc = cuda_fail(e3, "multi-graph kernel", __FILE__, __LINE__);
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  NX_TRY(rc);
+  MultiSync hs{};
+  NX_CUDA(cudaMemcpy(&hs, d_sync.p, sizeof hs, cudaMemcpyDeviceToHost));
+  if (hs.err) {
+    set_error("nx_run_multi: a grid barrier timed out; values are undefined");
+    return NX_ERR_TIMEOUT;
+  }
+  for (uint32_t gi = 0; gi < count; ++gi) gs[gi]->cur = (int)(iters & 1u);
+  if (st) {
+    memset(st, 0, sizeof *st);
+    st->iters_done = iters;
+    st->ms = ms;
+    st->edges_swept = edges * iters;
+    st->launches = 1;
+    uint64_t bytes = 0;
+    for (uint32_t gi = 0; gi < count; ++gi) bytes += bytes_per_sweep(gs[gi], prog, gs[gi]->m);
+    st->bytes_model = bytes * iters;
+  }
+  return NX_OK;
+}
+
 }  // namespace
 }  // namespace nx
 
@@ -1016,6 +1159,23 @@ extern "C" nx_status nx_adjoint_wpr(nx_graph* g, const float* grad_r, uint32_t a
     return nx::invalid("nx_adjoint_wpr: run NX_WPR first (its ranks are the forward state)");
   if (adj_terms == 0) return nx::invalid("nx_adjoint_wpr: adj_terms must be >= 1");
   return nx::adjoint_impl(g, grad_r, adj_terms, grad_w, grad_t, ptrs_are_device, stats);
+}
+
+extern "C" nx_status nx_run_multi(nx_graph** graphs, uint32_t count, nx_program program,
+                                  float alpha, uint32_t iters, nx_run_stats* stats) {
+  if (!graphs || count == 0) return nx::invalid("nx_run_multi: no graphs");
+  if (program == NX_PPR) return nx::invalid("nx_run_multi: PPR needs a teleport; use PR, WPR, BFS, WCC");
+  if ((int)program < 0 || (int)program > 4) return nx::invalid("nx_run_multi: unknown program");
+  if (!(alpha >= 0.f && alpha < 1.f)) return nx::invalid("nx_run_multi: alpha must be in [0, 1)");
+  for (uint32_t q = 0; q < count; ++q) {
+    const nx_graph* g = graphs[q];
+    if (!g) return nx::invalid("nx_run_multi: a graph is NULL");
+    for (uint32_t r = 0; r < q; ++r)
+      if (graphs[r] == g) return nx::invalid("nx_run_multi: a graph appears twice");
+    if (program == NX_WCC && !g->has_tr) return nx::invalid("nx_run_multi: WCC needs the transpose");
+    if (program == NX_WPR && !g->has_w) return nx::invalid("nx_run_multi: WPR needs weights");
+  }
+  return nx::multi_impl(graphs, count, program, alpha, iters, stats);
 }
 
 extern "C" nx_status nx_get_values(const nx_graph* g, void* out, uint64_t count,

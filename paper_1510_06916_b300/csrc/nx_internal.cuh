@@ -115,6 +115,19 @@ struct Geometry {
   std::vector<uint32_t> h_tile_start, h_col_tb;
 };
 
+// One thread block's work: a destination tile, or a contiguous part of the
+// tile's "virtual edge sequence" (its pieces (i, t) for i = 0..P-1, over each
+// DSSS in the sweep, concatenated) when the tile is too heavy for one block.
+struct Item {
+  uint32_t tile;
+  uint32_t nsplit;  // blocks sharing this tile (1: not split)
+  uint32_t slot;    // first split slot of the tile (split tiles only)
+  uint32_t sub;     // this block's index among them
+  uint64_t vbeg, vend;
+  uint32_t row;     // mode 1: the source interval i of the piece
+  uint32_t pad;
+};
+
 // Piece (i, t) of tile t in column j: P*tb_j + i*nt_j + (t - tb_j).
 __host__ __device__ inline uint64_t piece_index(uint32_t P, uint32_t tb_j, uint32_t nt_j,
                                                 uint32_t i, uint32_t t) {
@@ -148,6 +161,8 @@ struct nx_graph {
   // Work plans (item lists) cached by strategy / DSSS set / placement.
   struct Plan {
     nx::DevBuf items;
+    std::vector<uint64_t> h_cost;  // per item: its share of edges (host)
+    std::vector<nx::Item> h_items;
     uint32_t na = 0, nb = 0, slots = 0;
     std::vector<uint32_t> off;  // item offsets of each launch of the plan
   };

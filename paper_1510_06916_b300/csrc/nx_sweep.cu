@@ -241,30 +241,17 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
   return t;  // valid in thread 0
 }
 
+// One work item: the tile's pieces, the split merge and the epilogue. Called
+// by k_sweep (one item per block) and by the persistent multi-graph kernel.
 template <int K>
-__global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
+__device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned char* smem_raw) {
   using PG = Prog<K>;
   using V = typename PG::V;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc<V> acc;
   acc.hi = reinterpret_cast<V*>(smem_raw);
   acc.lo = PG::compensated ? reinterpret_cast<float*>(smem_raw) + a.tile_max : nullptr;
   __shared__ double red[kWarps];
   __shared__ int s_flag;
-
-  Item it;
-  if (a.items) {
-    it = a.items[blockIdx.x];
-  } else {  // one block per tile, whole tile
-    it.tile = blockIdx.x;
-    it.nsplit = 1;
-    it.slot = 0;
-    it.sub = 0;
-    it.vbeg = 0;
-    it.vend = ~0ull;
-    it.row = 0;
-    it.pad = 0;
-  }
   const uint32_t t = it.tile;
   const uint32_t ts = a.tile_start[t], te = a.tile_start[t + 1];
   const uint32_t T = te - ts;
@@ -457,7 +444,131 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SweepArgs a) {
   if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_sweep(const __grid_constant__ SweepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Item it;
+  if (a.items) {
+    it = a.items[blockIdx.x];
+  } else {  // one block per tile, whole tile
+    it.tile = blockIdx.x;
+    it.nsplit = 1;
+    it.slot = 0;
+    it.sub = 0;
+    it.vbeg = 0;
+    it.vend = ~0ull;
+    it.row = 0;
+    it.pad = 0;
+  }
+  sweep_item<K>(a, it, smem_raw);
+}
+
+// ---------------------------------------------------------------- many graphs
+// Persistent kernel over several independent graphs: every iteration, blocks
+// pull (graph, item) pairs from a shared counter, sweep them with the graph's
+// own arguments (args[2*gid + parity]), then meet at a grid barrier before the
+// next iteration. The barrier spins a bounded number of cycles; on expiry it
+// sets *err and every block returns.
+__device__ __forceinline__ bool grid_barrier(MultiSync* sy, unsigned nblocks, long long limit) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &sy->gen;
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(&sy->count, 1u) == nblocks - 1) {
+      sy->count = 0;
+      __threadfence();
+      atomicAdd(&sy->gen, 1u);
+      s_ok = 1;
+    } else {
+      const long long t0 = clock64();
+      s_ok = 1;
+      while (*gen == g0) {
+        if (*(volatile unsigned*)&sy->err) {
+          s_ok = 0;
+          break;
+        }
+        if (clock64() - t0 > limit) {
+          atomicExch(&sy->err, 1u);
+          s_ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_multi(const SweepArgs* __restrict__ args,
+                                                    const MItem* __restrict__ items,
+                                                    uint32_t nitems, uint32_t iters,
+                                                    uint32_t* __restrict__ ctr, MultiSync* sy,
+                                                    long long limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t s_idx;
+  for (uint32_t itn = 0; itn < iters; ++itn) {
+    const uint32_t par = itn & 1u;
+    for (;;) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_idx = atomicAdd(ctr + itn, 1u);
+      __syncthreads();
+      const uint32_t q = s_idx;
+      if (q >= nitems) break;
+      const MItem mi = items[q];
+      sweep_item<K>(args[2 * mi.gid + par], mi.it, smem_raw);
+    }
+    if (!grid_barrier(sy, gridDim.x, limit)) return;
+  }
+}
+
 }  // namespace
+
+nx_status launch_multi(ProgKind kind, const SweepArgs* args, const MItem* items, uint32_t nitems,
+                       uint32_t iters, uint32_t* ctr, MultiSync* sy, uint32_t tile_max,
+                       uint32_t nblocks, cudaStream_t s) {
+  const bool sums = (kind == PK_PR || kind == PK_WPR);
+  const size_t smem = (size_t)tile_max * (sums ? 8 : 4);
+  const long long limit = 4000000000ll;  // about two seconds at 2 GHz
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  switch (kind) {
+    case PK_PR: NX_CUDA(cudaLaunchKernelEx(&cfg, k_multi<PK_PR>, args, items, nitems, iters, ctr, sy, limit)); break;
+    case PK_WPR: NX_CUDA(cudaLaunchKernelEx(&cfg, k_multi<PK_WPR>, args, items, nitems, iters, ctr, sy, limit)); break;
+    case PK_BFS: NX_CUDA(cudaLaunchKernelEx(&cfg, k_multi<PK_BFS>, args, items, nitems, iters, ctr, sy, limit)); break;
+    case PK_WCC: NX_CUDA(cudaLaunchKernelEx(&cfg, k_multi<PK_WCC>, args, items, nitems, iters, ctr, sy, limit)); break;
+    default: return invalid("launch_multi: program not supported");
+  }
+  return NX_OK;
+}
+
+nx_status multi_blocks(ProgKind kind, uint32_t tile_max, uint32_t* nblocks) {
+  const bool sums = (kind == PK_PR || kind == PK_WPR);
+  const size_t smem = (size_t)tile_max * (sums ? 8 : 4);
+  int per_sm = 0;
+  switch (kind) {
+    case PK_PR: NX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi<PK_PR>, kThreads, smem)); break;
+    case PK_WPR: NX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi<PK_WPR>, kThreads, smem)); break;
+    case PK_BFS: NX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi<PK_BFS>, kThreads, smem)); break;
+    case PK_WCC: NX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi<PK_WCC>, kThreads, smem)); break;
+    default: return invalid("multi_blocks: program not supported");
+  }
+  if (per_sm < 1) return invalid("multi_blocks: kernel does not fit on an SM");
+  *nblocks = (uint32_t)per_sm * (uint32_t)num_sms();
+  return NX_OK;
+}
 
 nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaStream_t s) {
   if (nitems == 0) return NX_OK;

@@ -4,19 +4,6 @@
 
 namespace nx {
 
-// One thread block's work: a destination tile, or a contiguous part of the
-// tile's "virtual edge sequence" (its pieces (i, t) for i = 0..P-1, over each
-// DSSS in the sweep, concatenated) when the tile is too heavy for one block.
-struct Item {
-  uint32_t tile;
-  uint32_t nsplit;  // blocks sharing this tile (1: not split)
-  uint32_t slot;    // first split slot of the tile (split tiles only)
-  uint32_t sub;     // this block's index among them
-  uint64_t vbeg, vend;
-  uint32_t row;     // mode 1: the source interval i of the piece
-  uint32_t pad;
-};
-
 struct SweepSrc {
   const uint32_t* ew = nullptr;        // edge words; index e addresses edge e of the DSSS
   const float* wt = nullptr;           // normalised weights (weighted PageRank), same indexing
@@ -81,5 +68,20 @@ struct SweepArgs {
 
 // Launches one sweep over `nitems` items (kind selects the program).
 nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaStream_t s);
+
+// Persistent multi-graph run: item q of iteration i sweeps graph items[q].gid
+// with args[2 * gid + (i & 1)].
+struct MItem {
+  uint32_t gid, pad;
+  Item it;
+};
+struct MultiSync {
+  unsigned count, gen, err, pad;
+};
+nx_status launch_multi(ProgKind kind, const SweepArgs* args, const MItem* items, uint32_t nitems,
+                       uint32_t iters, uint32_t* ctr, MultiSync* sy, uint32_t tile_max,
+                       uint32_t nblocks, cudaStream_t s);
+// Co-resident blocks of the multi-graph kernel (occupancy x SMs).
+nx_status multi_blocks(ProgKind kind, uint32_t tile_max, uint32_t* nblocks);
 
 }  // namespace nx

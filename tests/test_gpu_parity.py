@@ -389,3 +389,31 @@ def test_autograd_function():
     assert_pr_close(r.detach().cpu().numpy(), ref["r"], "autograd forward")
     _grad_close(wt.grad.cpu().numpy(), ref["dw"], "autograd dw")
     _grad_close(t.grad.cpu().numpy(), ref["dt"], "autograd dt")
+
+
+# ------------------------------------------------------------------ many graphs
+
+def test_run_multi_uneven_graphs():
+    scales = inputs.multigraph_scales(12, lo=6, hi=12)
+    graphs, edges = [], []
+    for gi, sc in enumerate(scales):
+        n = 1 << sc
+        s, d, _ = inputs.rmat_edges(sc, 16 << sc, inputs.multigraph_seed(gi))
+        graphs.append(nx.Graph(s, d, n, 1 + gi % 5, transpose=True))
+        edges.append((n, s, d))
+    st = nx.run_multi(graphs, "pr", 20)
+    assert st["iters_done"] == 20 and st["launches"] == 1
+    for g, (n, s, d) in zip(graphs, edges):
+        assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"multi PR n={n}")
+    nx.run_multi(graphs, "bfs", 40)
+    for g, (n, s, d) in zip(graphs, edges):
+        assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 0)).all()
+    nx.run_multi(graphs, "wcc", 40)
+    for g, (n, s, d) in zip(graphs, edges):
+        assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+    # a single graph and repeated calls give the same as nx_run
+    g0 = graphs[-1]
+    nx.run_multi([g0], "pr", 20)
+    a = g0.values().copy()
+    g0.run("pr", 20)
+    assert_pr_close(a, g0.values().astype(np.float64), "multi vs run")
