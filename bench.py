@@ -185,6 +185,94 @@ def run_reference(args, w):
     return 0
 
 
+def measure_ppr_batch(nx, inputs, torch, B=64, iters=30, scale=24, seed=3, P=16):
+    """Batched PPR (R-MAT scale 24, 64 seed sets, 30 iterations) vs one vector."""
+    n, m = 1 << scale, 16 << scale
+    src, dst, _ = inputs.rmat_edges_device(scale, m, seed)
+    g = nx.Graph(src, dst, n, P)
+    del src, dst
+    v, b, t = inputs.ppr_seed_lists(n, B, seed)
+    T = torch.zeros((n, B), dtype=torch.float32, device="cuda")
+    T[torch.from_numpy(v).cuda(), torch.from_numpy(b).cuda()] = torch.from_numpy(t).cuda()
+    R = torch.empty_like(T)
+    g.ppr_batch(T, iters=2, out=R)  # warm-up
+    _, st = g.ppr_batch(T, iters=iters, out=R)
+    t0 = T[:, 0].contiguous()
+    g.run("ppr", 2, teleport=t0)
+    one = g.run("ppr", iters, teleport=t0)
+    out = {
+        "workload": f"R-MAT scale {scale} ef 16 seed {seed}, P={P}, {B} PPR vectors x {iters} iterations",
+        "batched_ms": st["ms"], "single_vector_ms": one["ms"],
+        "vector_edges_per_s_batched": m * B * iters / (st["ms"] / 1e3),
+        "vector_edges_per_s_single": m * iters / (one["ms"] / 1e3),
+        "speedup_vs_64_single": B * one["ms"] / st["ms"],
+        "launches": st["launches"],
+    }
+    del T, R
+    g.free()
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_adjoint(nx, inputs, torch, scale=24, seed=4, P=16, iters=50, terms=50, ntarget=1024):
+    """Weighted PageRank 50 iterations forward + 50-term adjoint (R-MAT scale 24)."""
+    n, m = 1 << scale, 16 << scale
+    src, dst, w = inputs.rmat_edges_device(scale, m, seed, weights=True)
+    g = nx.Graph(src, dst, n, P, transpose=True, weights=w)
+    del src, dst, w
+    T = inputs.targets(n, ntarget, seed)
+    gvec = torch.zeros(n, dtype=torch.float32, device="cuda")
+    gvec[torch.from_numpy(T).cuda()] = 1.0
+    dw = torch.empty(m, dtype=torch.float32, device="cuda")
+    dt = torch.empty(n, dtype=torch.float32, device="cuda")
+    g.run("wpr", 2)
+    g.adjoint_wpr(gvec, 2, dw, dt)
+    fwd = g.run("wpr", iters)
+    adj = g.adjoint_wpr(gvec, terms, dw, dt)
+    out = {
+        "workload": f"R-MAT scale {scale} ef 16 seed {seed}, w~U(0.5,1.5), |T|={ntarget}, "
+                    f"{iters} forward + {terms} adjoint iterations",
+        "forward_ms": fwd["ms"], "adjoint_ms": adj["ms"],
+        "adjoint_gteps": m * terms / (adj["ms"] / 1e3) / 1e9,
+        "forward_gteps": m * iters / (fwd["ms"] / 1e3) / 1e9,
+        "adjoint_over_forward": adj["ms"] / fwd["ms"],
+    }
+    g.free()
+    del dw, dt, gvec
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_multi(nx, inputs, torch, count=256, iters=20):
+    """256 R-MAT graphs of scales U{10..18} (ef 16): PageRank in one persistent launch."""
+    scales = inputs.multigraph_scales(count)
+    graphs = []
+    m_tot = 0
+    for gi, sc in enumerate(scales):
+        n, m = 1 << sc, 16 << sc
+        src, dst, _ = inputs.rmat_edges_device(sc, m, inputs.multigraph_seed(gi))
+        graphs.append(nx.Graph(src, dst, n, max(1, min(16, n >> 12)), transpose=True))
+        m_tot += m
+    nx.run_multi(graphs, "pr", 2)
+    st = nx.run_multi(graphs, "pr", iters)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ms_sep = 0.0
+    for g in graphs:
+        ms_sep += g.run("pr", iters)["ms"]
+    wall_sep = (time.perf_counter() - t0) * 1e3
+    bfs = nx.run_multi(graphs, "bfs", 40)
+    wcc = nx.run_multi(graphs, "wcc", 40)
+    for g in graphs:
+        g.free()
+    return {
+        "workload": f"{count} R-MAT graphs, scales U{{10..18}}, ef 16 ({m_tot} edges), PR x{iters}",
+        "multi_ms": st["ms"], "gteps": m_tot * iters / (st["ms"] / 1e3) / 1e9,
+        "separate_runs_wall_ms": wall_sep, "separate_runs_kernel_ms": ms_sep,
+        "bfs40_ms": bfs["ms"], "wcc40_ms": wcc["ms"], "launches": st["launches"],
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,6 +282,8 @@ def main():
     ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-PPR, adjoint and multi-graph measurements")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -250,9 +340,13 @@ def main():
     achieved = bytes_per_launch / t_launch / 1e9
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
+    if os.path.exists(prof):  # only while the profiled kernel source is unchanged
         try:
-            traffic = json.load(open(prof)).get(args.workload)
+            import hashlib
+            ent = json.load(open(prof)).get(args.workload)
+            src = open(os.path.join(ROOT, ent["source"]), "rb").read()
+            if hashlib.sha256(src).hexdigest() == ent["source_sha256"]:
+                traffic = ent["bytes_per_launch"]
         except Exception:
             traffic = None
 
@@ -290,6 +384,16 @@ def main():
         except Exception as e:  # pragma: no cover
             cpu = {"value": None, "unit": "GTEPS", "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
 
+    extras = None
+    if not args.no_extras:
+        extras = {}
+        for name, fn in (("ppr_batch", measure_ppr_batch), ("adjoint", measure_adjoint),
+                         ("multi_graph", measure_multi)):
+            try:
+                extras[name] = fn(nx, inputs, torch)
+            except Exception as e:  # pragma: no cover
+                extras[name] = {"error": str(e)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
@@ -310,6 +414,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     g.free()

@@ -120,6 +120,19 @@ def ppr_teleports(n: int, batch: int, seed: int, max_seeds: int = 1000) -> np.nd
     return T
 
 
+def ppr_seed_lists(n: int, batch: int, seed: int, max_seeds: int = 1000):
+    """Sparse form of ppr_teleports: (vertex, column, value) arrays of the nonzeros."""
+    vs, bs, ts = [], [], []
+    for bi in range(batch):
+        k0 = bi << 32
+        kb = 1 + int(draws(seed, k0, 1)[0] % np.uint64(max_seeds))
+        seeds = _distinct(seed, k0, kb, n)
+        vs.append(seeds)
+        bs.append(np.full(len(seeds), bi, dtype=np.int64))
+        ts.append(np.full(len(seeds), 1.0 / len(seeds), dtype=np.float32))
+    return np.concatenate(vs), np.concatenate(bs), np.concatenate(ts)
+
+
 def targets(n: int, count: int, seed: int) -> np.ndarray:
     """`count` distinct target vertices (stream seed, draws 1, 2, ...)."""
     return _distinct(seed, 0, count, n)
