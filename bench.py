@@ -273,6 +273,17 @@ def measure_multi(nx, inputs, torch, count=256, iters=20):
     }
 
 
+def measure_autotune(nx, inputs, torch, scale=22, seed=2):
+    """P autotuned over {8, 16, 32, 64} for PageRank on the scale-22 graph."""
+    n, m = 1 << scale, 16 << scale
+    src, dst, _ = inputs.rmat_edges_device(scale, m, seed)
+    P, ms = nx.autotune(src, dst, n, candidates=(8, 16, 32, 64), iters=10)
+    del src, dst
+    torch.cuda.empty_cache()
+    return {"workload": f"R-MAT scale {scale} ef 16 seed {seed}, PageRank x10 per candidate",
+            "best_P": P, "ms_per_iter": dict(zip(("8", "16", "32", "64"), ms))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,7 +399,7 @@ def main():
     if not args.no_extras:
         extras = {}
         for name, fn in (("ppr_batch", measure_ppr_batch), ("adjoint", measure_adjoint),
-                         ("multi_graph", measure_multi)):
+                         ("multi_graph", measure_multi), ("autotune", measure_autotune)):
             try:
                 extras[name] = fn(nx, inputs, torch)
             except Exception as e:  # pragma: no cover

@@ -76,7 +76,11 @@ typedef struct {
   uint32_t root;          /* BFS root vertex                                   */
   const float* teleport;  /* PPR/WPR teleport vector [n], or NULL = uniform 1/n */
   int32_t teleport_is_device;
-  int32_t use_graph;      /* 1: capture fixed-count iteration loops in a CUDA graph */
+  int32_t use_graph;      /* reserved, set to 0                                  */
+  uint32_t band_intervals;/* SPU: source intervals per launch (0 = automatic: one
+                             launch when the gathered value array fits the L2,
+                             else bands whose values do); accumulators carry
+                             between bands in device memory                      */
 } nx_params;
 
 typedef struct {
@@ -244,6 +248,25 @@ void nx_graph_free(nx_graph* g);
  */
 nx_status nx_pagerank_step_noalloc(const nx_graph* g, float alpha, const float* r_in,
                                    float* r_out);
+
+/*
+ * Autotuner (Exp 2, Section IV-B2: the paper finds P = 12..48 good): builds
+ * the DSSS for every candidate P, times `iters` iterations of `program` under
+ * SPU (after one warm-up run) and returns the fastest P.
+ *   src, dst, m, n, flags, w : as nx_build_dsss
+ *   candidates, count        : P values to try (each 1 <= P <= min(n, 1024))
+ *   best_P                   : receives the fastest candidate
+ *   ms_per_iter              : [count] measured ms per iteration (nullable)
+ *   cache_path               : text file of earlier results keyed by GPU name,
+ *                              n, m, program and candidates (nullable: none).
+ *                              A hit returns the stored P without timing
+ *                              (ms_per_iter then holds -1).
+ * Errors: as nx_build_dsss and nx_run.
+ */
+nx_status nx_autotune(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n,
+                      uint32_t flags, const float* w, nx_program program,
+                      const uint32_t* candidates, uint32_t count, uint32_t iters,
+                      uint32_t* best_P, float* ms_per_iter, const char* cache_path);
 
 /* Planner model of Section III-B (Table II): bytes read / written per
  * iteration for strategy s with n vertices, m edges, P intervals, budget B_M,

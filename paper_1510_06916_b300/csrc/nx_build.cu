@@ -210,7 +210,7 @@ nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geom
     NX_LAUNCH_CHECK();
     NX_TRY(radix_sort_u64(keys.as<uint64_t>(), wn ? idx.as<uint32_t>() : nullptr, m, key_bits));
   }
-  const uint64_t mpad = round_up(m, 8) + 8;
+  const uint64_t mpad = round_up(m, kEdgeAlign) + kEdgeAlign;
   NX_TRY(out.ew.alloc(mpad * sizeof(uint32_t)));
   NX_CUDA(cudaMemsetAsync(out.ew.p, 0, mpad * sizeof(uint32_t), stream()));
   NX_TRY(out.piece_off.alloc((npieces + 1) * sizeof(uint64_t)));

@@ -85,8 +85,6 @@ uint64_t piece_len(const nx_graph* g, const Dsss& d, uint32_t i, uint32_t t, uin
   return d.h_piece_off[pc + 1] - d.h_piece_off[pc];
 }
 
-uint32_t col_of_tile(const nx_graph* g, uint32_t t) { return g->geo.h_tile_start[t] / g->geo.L; }
-
 uint64_t target_block_edges(uint64_t total) {
   uint64_t e = total / ((uint64_t)num_sms() * 8);
   return std::max<uint64_t>(4096, e);
@@ -361,9 +359,9 @@ nx_status dpu_iteration(nx_graph* g, nx_program prog, SweepArgs& a, uint32_t n_t
 // (created on first use from the device copy).
 nx_status ensure_host_shards(nx_graph* g, Dsss& d, uint32_t first_col) {
   const auto& tb = g->geo.h_col_tb;
-  const uint64_t e0 = d.h_piece_off[(uint64_t)g->geo.P * tb[first_col]] & ~7ull;
+  const uint64_t e0 = d.h_piece_off[(uint64_t)g->geo.P * tb[first_col]] & ~(kEdgeAlign - 1);
   if (d.h_ew.p && d.h_ew_first <= e0) return NX_OK;
-  const uint64_t words = round_up(d.m, 8) + 8 - e0;
+  const uint64_t words = round_up(d.m, kEdgeAlign) + kEdgeAlign - e0;
   NX_TRY(d.h_ew.alloc(words * 4));
   NX_CUDA(cudaMemcpyAsync(d.h_ew.p, d.ew.as<uint32_t>() + e0, words * 4, cudaMemcpyDeviceToHost,
                           stream()));
@@ -425,8 +423,8 @@ nx_status spu_stream_iteration(RunCtx& c, SweepArgs& a, const std::vector<uint32
     NX_CUDA(cudaStreamWaitEvent(sm.side, sm.used[b], 0));
     for (size_t s = 0; s < c.ds.size(); ++s) {
       const Dsss& d = *c.ds[s];
-      const uint64_t e0 = d.h_piece_off[(uint64_t)c.P * tb[j]] & ~7ull;
-      const uint64_t e1 = round_up(d.h_piece_off[(uint64_t)c.P * tb[j + 1]], 8) + 8;
+      const uint64_t e0 = d.h_piece_off[(uint64_t)c.P * tb[j]] & ~(kEdgeAlign - 1);
+      const uint64_t e1 = round_up(d.h_piece_off[(uint64_t)c.P * tb[j + 1]], kEdgeAlign) + kEdgeAlign;
       const uint64_t words = e1 - e0;
       // stage[b] holds one shard per DSSS of the sweep (second half: transpose)
       uint32_t* dst = g->stage[b].as<uint32_t>() + (s ? (g->stage[b].bytes / 8) : 0);
@@ -441,6 +439,30 @@ nx_status spu_stream_iteration(RunCtx& c, SweepArgs& a, const std::vector<uint32
     NX_TRY(launch_sweep(kind_of(c.prog), sa, col_off[j + 1] - col_off[j], stream()));
     ++c.launches;
     NX_CUDA(cudaEventRecord(sm.used[b], stream()));
+  }
+  g->cur ^= 1;
+  return NX_OK;
+}
+
+// SPU iteration in bands of source intervals: band 0 stores the raw tile
+// accumulators, the middle bands add to them, the last band adds and applies
+// the epilogue. Every tile is owned by one block per band (split tiles merge
+// their slots first), so no band needs atomics in device memory.
+nx_status spu_band_iteration(RunCtx& c, SweepArgs& a, const std::vector<uint32_t>& off,
+                             uint32_t band) {
+  nx_graph* g = c.g;
+  set_iter_ptrs(g, c.prog, a);
+  const uint32_t nb = (uint32_t)off.size() - 1;
+  for (uint32_t b = 0; b < nb; ++b) {
+    SweepArgs ab = a;
+    ab.items = a.items + off[b];
+    ab.src_lo = b * band;
+    ab.src_hi = std::min(c.P, (b + 1) * band);
+    ab.acc_in = b == 0 ? nullptr : g->accres.p;
+    ab.accres = g->accres.p;
+    ab.mode = (b + 1 == nb) ? 0 : 2;
+    NX_TRY(launch_sweep(kind_of(c.prog), ab, off[b + 1] - off[b], stream()));
+    ++c.launches;
   }
   g->cur ^= 1;
   return NX_OK;
@@ -647,10 +669,20 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     }
   }
   const bool streaming = (strat == NX_SPU && c.Jc < P);
+  // SPU bands: launches over groups of source intervals whose gathered values
+  // fit in L2 together (the value array of the whole graph may not)
+  uint32_t band = P;
+  if (strat == NX_SPU && !streaming) {
+    const uint64_t kBandBytes = 48ull << 20;
+    if (p.band_intervals) band = std::min<uint32_t>(p.band_intervals, P);
+    else if ((uint64_t)n * 4 > kBandBytes)
+      band = (uint32_t)std::max<uint64_t>(1, kBandBytes / ((uint64_t)L * 4));
+  }
+  const uint32_t nbands = (uint32_t)ceil_div(P, band);
 
   // plan (cached: the graph never changes)
-  const int key = ((int)strat * 16 + (int)c.ds.size()) * 4096 + (int)(staged ? Q + 1 : 0) +
-                  (streaming ? (int)(c.Jc + 2048) : 0);
+  const int key = (((int)strat * 16 + (int)c.ds.size()) * 4096 + (int)(staged ? Q + 1 : 0) +
+                   (streaming ? (int)(c.Jc + 2048) : 0)) * 2048 + (int)(nbands > 1 ? band : 0);
   auto& slot_plan = g->plans[key];
   if (!slot_plan) {
     slot_plan.reset(new nx_graph::Plan());
@@ -660,9 +692,16 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     PlanOut plan;
     std::vector<uint32_t> launch_off;
     uint32_t n_a = 0, n_b = 0;
-    if (strat == NX_SPU && !streaming) {
+    if (strat == NX_SPU && !streaming && nbands == 1) {
       plan_tiles(g, c.ds, 0, P, 0, P, true, blk, plan);
       n_a = (uint32_t)plan.items.size();
+    } else if (strat == NX_SPU && !streaming) {  // one launch per band of source intervals
+      for (uint32_t i0 = 0; i0 < P; i0 += band) {
+        launch_off.push_back((uint32_t)plan.items.size());
+        plan_tiles(g, c.ds, i0, std::min(P, i0 + band), 0, P, true,
+                   std::max<uint64_t>(blk / nbands, 4096), plan);
+      }
+      launch_off.push_back((uint32_t)plan.items.size());
     } else if (strat == NX_SPU) {  // per column groups: [0, Jc) then one per streamed column
       launch_off.assign(P + 1, 0);
       plan_tiles(g, c.ds, 0, P, 0, c.Jc, true, blk, plan);
@@ -701,6 +740,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   const uint32_t n_a = pl.na, n_b = pl.nb;
   if (strat == NX_DPU || staged) NX_TRY(ensure(g->hubs, std::max<uint64_t>(g->fwd.D, 1) * 4));
 
+  if (nbands > 1) NX_TRY(ensure(g->accres, (size_t)n * 4));
   SweepArgs a = base_args(g, prog, p, tele);
   a.items = pl.items.as<Item>();
   a.split = g->split_buf.p;
@@ -713,8 +753,8 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     uint64_t maxw = 0;
     for (uint32_t j = c.Jc; j < P; ++j)
       for (const Dsss* d : c.ds) {
-        const uint64_t e0 = d->h_piece_off[(uint64_t)P * tb[j]] & ~7ull;
-        const uint64_t e1 = round_up(d->h_piece_off[(uint64_t)P * tb[j + 1]], 8) + 8;
+        const uint64_t e0 = d->h_piece_off[(uint64_t)P * tb[j]] & ~(kEdgeAlign - 1);
+        const uint64_t e1 = round_up(d->h_piece_off[(uint64_t)P * tb[j + 1]], kEdgeAlign) + kEdgeAlign;
         maxw = std::max(maxw, e1 - e0);
       }
     for (int b = 0; b < 2; ++b) NX_TRY(ensure(g->stage[b], maxw * 4 * 2));
@@ -776,9 +816,11 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     }
     for (uint32_t i = 0; i < P; ++i)
       if (act_h[i]) swept += row_edges[i];
-    if (strat == NX_SPU && !streaming) {
+    if (strat == NX_SPU && !streaming && nbands == 1) {
       NX_TRY(spu_iteration(g, prog, a, n_a));
       ++c.launches;
+    } else if (strat == NX_SPU && !streaming) {
+      NX_TRY(spu_band_iteration(c, a, pl.off, band));
     } else if (streaming) {
       NX_TRY(spu_stream_iteration(c, a, col_off, sm));
     } else if (!staged) {

@@ -80,6 +80,10 @@ inline uint64_t round_up(uint64_t a, uint64_t b) { return ceil_div(a, b) * b; }
 
 int num_sms();
 
+// Edge arrays are padded and streamed staging copies aligned to this many
+// words, so a lane's vector loads past the end of a range stay in the buffer.
+constexpr uint64_t kEdgeAlign = 16;
+
 // ---------------------------------------------------------------- primitives
 // Exclusive scan of in[0..n) into out[0..n); *total (device, nullable) gets the
 // sum. out may alias in. Scratch is allocated internally.

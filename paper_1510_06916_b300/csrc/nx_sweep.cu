@@ -68,13 +68,27 @@ struct MinU {  // BFS / WCC: min of uint32
   }
 };
 
+// Load of a gathered source value (random 4-byte access). NX_GATHER_MODE picks
+// the cache operator: 0 = read-only path (ld.global.nc), 1 = L2 only (.cg).
+#ifndef NX_GATHER_MODE
+#define NX_GATHER_MODE 0
+#endif
+template <class T>
+__device__ __forceinline__ T ld_gather(const T* p) {
+#if NX_GATHER_MODE == 1
+  return __ldcg(p);
+#else
+  return __ldg(p);
+#endif
+}
+
 template <int K>
 struct Prog;
 template <>
 struct Prog<PK_PR> : PrSum {  // gathers c[u] = r[u] / outdeg[u]
   static constexpr bool weighted = false;
   __device__ static float gather(const void* g, const uint32_t*, uint32_t u, float) {
-    return __ldg(static_cast<const float*>(g) + u);
+    return ld_gather(static_cast<const float*>(g) + u);
   }
 };
 template <>
@@ -102,7 +116,7 @@ template <>
 struct Prog<PK_BFS> : MinU {  // depth[u] + 1 (infinity stays infinity)
   static constexpr bool weighted = false;
   __device__ static uint32_t gather(const void* g, const uint32_t*, uint32_t u, float) {
-    uint32_t d = __ldg(static_cast<const uint32_t*>(g) + u);
+    uint32_t d = ld_gather(static_cast<const uint32_t*>(g) + u);
     return d == kInf ? kInf : d + 1;
   }
 };
@@ -110,7 +124,7 @@ template <>
 struct Prog<PK_WCC> : MinU {  // label[u]
   static constexpr bool weighted = false;
   __device__ static uint32_t gather(const void* g, const uint32_t*, uint32_t u, float) {
-    return __ldg(static_cast<const uint32_t*>(g) + u);
+    return ld_gather(static_cast<const uint32_t*>(g) + u);
   }
 };
 
@@ -127,6 +141,37 @@ __device__ __forceinline__ float4 ld_stream_f(const float* p) {
 // that short pieces do not all land on the same warps (rot advances by the
 // piece's step count). Each warp loads its next step's edge words before it
 // gathers and reduces the current one.
+// Edges per lane in one warp step (8 or 16): two or four 16-byte loads.
+#ifndef NX_EPL
+#define NX_EPL 8
+#endif
+constexpr int kEPL = NX_EPL;
+constexpr int kStep = 32 * kEPL;  // edges per warp step
+static_assert(kEPL == 8 || kEPL == 16, "edges per lane");
+static_assert(kEPL <= (int)kEdgeAlign, "edge padding");
+
+template <int N>
+struct EdgeRegs {
+  uint4 q[N / 4];
+  float4 f[N / 4];
+};
+
+template <class PG>
+__device__ __forceinline__ void load_step(EdgeRegs<kEPL>& r, const uint32_t* __restrict__ ew,
+                                          const float* __restrict__ wt, uint64_t idx) {
+#pragma unroll
+  for (int k = 0; k < kEPL / 4; ++k) {
+    r.q[k] = ld_stream(ew + idx + 4 * k);
+    if (PG::weighted) r.f[k] = ld_stream_f(wt + idx + 4 * k);
+  }
+}
+
+// Folds edges [a, b) of one piece into the tile accumulator. Edge e is read at
+// ew[e - ew_lo]; its source value at g[sbase + src_local]. The piece is cut
+// into kStep-edge steps from a rounded down to kEPL; step k goes to warp
+// (k + rot) % 8 so that short pieces do not all land on the same warps (rot
+// advances by the piece's step count). Each warp loads its next step's edge
+// words before it gathers and reduces the current one.
 template <class PG>
 __device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
                                             const float* __restrict__ wt, uint64_t ew_lo,
@@ -137,58 +182,51 @@ __device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
   using V = typename PG::V;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t smask = (1u << lb) - 1u;
-  const uint64_t a8 = a & ~7ull;
-  const uint32_t nsteps = (uint32_t)((b - a8 + 255) >> 8);
+  const uint64_t a0 = a & ~(uint64_t)(kEPL - 1);
+  const uint32_t nsteps = (uint32_t)((b - a0 + kStep - 1) / kStep);
   const uint32_t k0 = (uint32_t)((warp - (int)rot) & (kWarps - 1));
   rot = (rot + nsteps) & (kWarps - 1);
-  uint64_t base = a8 + (uint64_t)k0 * 256;
+  uint64_t base = a0 + (uint64_t)k0 * kStep;
   if (base >= b) return;
-  uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
-  float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = f0;
+  EdgeRegs<kEPL> nxt;
+#pragma unroll
+  for (int k = 0; k < kEPL / 4; ++k) {
+    nxt.q[k] = make_uint4(0, 0, 0, 0);
+    nxt.f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   {
-    const uint64_t p = base + (uint64_t)lane * 8;
-    if (p < b) {
-      q0 = ld_stream(ew + (p - ew_lo));
-      q1 = ld_stream(ew + (p - ew_lo) + 4);
-      if (PG::weighted) {
-        f0 = ld_stream_f(wt + (p - ew_lo));
-        f1 = ld_stream_f(wt + (p - ew_lo) + 4);
-      }
-    }
+    const uint64_t p = base + (uint64_t)lane * kEPL;
+    if (p < b) load_step<PG>(nxt, ew, wt, p - ew_lo);
   }
   while (base < b) {
     // valid edges of this step: offsets [lo, hi) from base (32-bit)
     const uint32_t lo = base < a ? (uint32_t)(a - base) : 0u;
-    const uint32_t hi = (b - base) < 256 ? (uint32_t)(b - base) : 256u;
+    const uint32_t hi = (b - base) < (uint64_t)kStep ? (uint32_t)(b - base) : (uint32_t)kStep;
     const uint32_t span = hi - lo;
-    const uint32_t wv[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-    const float wf[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-    const uint64_t nbase = base + (uint64_t)kWarps * 256;
+    const EdgeRegs<kEPL> cur = nxt;
+    const uint64_t nbase = base + (uint64_t)kWarps * kStep;
     {  // prefetch the warp's next step
-      const uint64_t pn = nbase + (uint64_t)lane * 8;
-      if (pn < b) {
-        q0 = ld_stream(ew + (pn - ew_lo));
-        q1 = ld_stream(ew + (pn - ew_lo) + 4);
-        if (PG::weighted) {
-          f0 = ld_stream_f(wt + (pn - ew_lo));
-          f1 = ld_stream_f(wt + (pn - ew_lo) + 4);
-        }
-      }
+      const uint64_t pn = nbase + (uint64_t)lane * kEPL;
+      if (pn < b) load_step<PG>(nxt, ew, wt, pn - ew_lo);
     }
-    uint32_t key[8];
-    V val[8];
+    uint32_t key[kEPL];
+    V val[kEPL];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const bool valid = ((uint32_t)(lane * 8 + k) - lo) < span;
-      key[k] = valid ? (wv[k] >> lb) : kSent;
-      val[k] = valid ? PG::gather(g, od, sbase + (wv[k] & smask), wf[k]) : PG::identity();
+    for (int k = 0; k < kEPL; ++k) {
+      const uint4 q = cur.q[k / 4];
+      const float4 f = cur.f[k / 4];
+      const uint32_t w = (k & 3) == 0 ? q.x : (k & 3) == 1 ? q.y : (k & 3) == 2 ? q.z : q.w;
+      const float wf = (k & 3) == 0 ? f.x : (k & 3) == 1 ? f.y : (k & 3) == 2 ? f.z : f.w;
+      const bool valid = ((uint32_t)(lane * kEPL + k) - lo) < span;
+      key[k] = valid ? (w >> lb) : kSent;
+      val[k] = valid ? PG::gather(g, od, sbase + (w & smask), wf) : PG::identity();
     }
     // runs of equal destination inside the lane: first (head), middle, last (tail)
     uint32_t hk = key[0], ck = key[0];
     V hs = val[0], cs = val[0];
     bool single = true;
 #pragma unroll
-    for (int k = 1; k < 8; ++k) {
+    for (int k = 1; k < kEPL; ++k) {
       const bool brk = key[k] != ck;
       if (brk && !single && ck != kSent) PG::emit_short(acc, ck, cs);
       if (brk && single) {
@@ -261,6 +299,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
   if (a.mode == 3) {  // epilogue from the stored accumulators of resident columns
     const V* ar = static_cast<const V*>(a.accres);
     for (uint32_t k = threadIdx.x; k < T; k += kThreads) acc.hi[k] = ar[ts + k];
+  } else if (a.acc_in && it.sub == 0) {  // banded sweep: continue from the earlier bands
+    const V* ai = static_cast<const V*>(a.acc_in);
+    for (uint32_t k = threadIdx.x; k < T; k += kThreads) acc.hi[k] = ai[ts + k];
   } else {
     for (uint32_t k = threadIdx.x; k < T; k += kThreads) acc.hi[k] = PG::identity();
   }

@@ -20,6 +20,10 @@ struct SweepArgs {
   SweepSrc src[2];
   int nsrc = 1;
   uint32_t src_lo = 0, src_hi = 0;  // source intervals swept: [src_lo, src_hi)
+  // Banded sweeps: when non-null, the tile accumulator starts from acc_in
+  // (the bands before this one) instead of the identity (block 0 of a split
+  // tile only).
+  const void* acc_in = nullptr;
   const Item* items = nullptr;  // nullptr: block b sweeps the whole tile b
   const uint32_t* tile_start = nullptr;
   const uint32_t* col_tb = nullptr;

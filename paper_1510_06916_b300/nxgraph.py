@@ -28,13 +28,14 @@ EXPORTS = [
     "nx_set_stream", "nx_last_error", "nx_build_dsss", "nx_graph_get_info", "nx_run",
     "nx_get_values", "nx_set_values", "nx_run_ppr_batch", "nx_adjoint_wpr", "nx_run_multi",
     "nx_graph_free", "nx_io_model", "nx_dsss_export", "nx_pagerank_step_noalloc",
+    "nx_autotune",
 ]
 
 
 class NxParams(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_float), ("root", ctypes.c_uint32),
                 ("teleport", ctypes.c_void_p), ("teleport_is_device", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("band_intervals", ctypes.c_uint32)]
 
 
 class NxRunStats(ctypes.Structure):
@@ -90,6 +91,8 @@ def lib():
                                    ctypes.POINTER(NxRunStats)]
         L.nx_dsss_export.argtypes = [vp, i32, vp, vp, vp]
         L.nx_pagerank_step_noalloc.argtypes = [vp, f32, vp, vp]
+        L.nx_autotune.argtypes = [vp, vp, u64, u32, u32, vp, i32, vp, u32, u32,
+                                  ctypes.POINTER(u32), vp, ctypes.c_char_p]
         L.nx_graph_free.argtypes = [vp]
         L.nx_graph_free.restype = None
         L.nx_io_model.argtypes = [i32, d, d, d, d, d, d, d, d, ctypes.POINTER(d),
@@ -223,8 +226,9 @@ class Graph:
         return s, d, off
 
     def run(self, program="pr", iters=20, strategy="spu", budget=0, alpha=0.85, root=0,
-            teleport=None, use_graph=False) -> dict:
+            teleport=None, use_graph=False, band=0) -> dict:
         prm = NxParams()
+        prm.band_intervals = band
         prm.alpha = alpha
         prm.root = root
         tp, td = _ptr(teleport)
@@ -269,6 +273,24 @@ class Graph:
         st = NxRunStats()
         check(lib().nx_adjoint_wpr(self._h, gp, adj_terms, wp, tp, gd, ctypes.byref(st)))
         return st.as_dict()
+
+
+def autotune(src, dst, n, candidates=(8, 16, 32, 64), program="pr", iters=10, cache=None,
+             transpose=False):
+    """Fastest P among `candidates` (builds and times each). Returns (P, ms_per_iter list)."""
+    if isinstance(src, np.ndarray):
+        src = np.ascontiguousarray(src, dtype=np.uint32)
+        dst = np.ascontiguousarray(dst, dtype=np.uint32)
+    sp, sd = _ptr(src)
+    dp, _ = _ptr(dst)
+    cand = np.ascontiguousarray(candidates, dtype=np.uint32)
+    ms = np.empty(len(cand), dtype=np.float32)
+    best = ctypes.c_uint32()
+    flags = (DEV_PTRS if sd else HOST_PTRS) | (WITH_TRANSPOSE if transpose else 0)
+    check(lib().nx_autotune(sp, dp, len(src), n, flags, None, PROGRAMS.get(program, program),
+                            cand.ctypes.data, len(cand), iters, ctypes.byref(best), ms.ctypes.data,
+                            cache.encode() if cache else None))
+    return int(best.value), ms.tolist()
 
 
 def run_multi(graphs, program="pr", iters=20, alpha=0.85) -> dict:

@@ -417,3 +417,29 @@ def test_run_multi_uneven_graphs():
     a = g0.values().copy()
     g0.run("pr", 20)
     assert_pr_close(a, g0.values().astype(np.float64), "multi vs run")
+
+
+@pytest.mark.parametrize("band", [1, 2, 3])
+def test_banded_spu(band):
+    # SPU in launches over bands of source intervals, accumulators carried in HBM
+    n = 1 << 13
+    s, d, _ = rmat(13, 16, 15)
+    g = nx.Graph(s, d, n, 7, transpose=True)
+    st = g.run("pr", 20, band=band)
+    assert st["launches"] == 20 * -(-7 // band)
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"band {band} PR")
+    g.run("bfs", 1000, root=0, band=band)
+    assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 0)).all()
+    g.run("wcc", 1000, band=band)
+    assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+
+
+def test_autotune_picks_a_candidate_and_caches(tmp_path):
+    n = 1 << 14
+    s, d, _ = rmat(14, 16, 16)
+    cache = str(tmp_path / "tune.txt")
+    P, ms = nx.autotune(s, d, n, candidates=(2, 4, 8), iters=5, cache=cache)
+    assert P in (2, 4, 8) and all(x > 0 for x in ms)
+    assert P == (2, 4, 8)[int(np.argmin(ms))]
+    P2, ms2 = nx.autotune(s, d, n, candidates=(2, 4, 8), iters=5, cache=cache)
+    assert P2 == P and all(x == -1 for x in ms2)  # served from the cache file
