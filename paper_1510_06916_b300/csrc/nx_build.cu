@@ -258,7 +258,7 @@ nx_status build_geometry(nx_graph* g, const uint32_t* deg_a, const uint32_t* deg
   Geometry& geo = g->geo;
   const uint32_t n = geo.n;
   uint64_t E = m_bal / ((uint64_t)num_sms() * 8);
-  E = std::max<uint64_t>(2048, std::min<uint64_t>(E, 65536));
+  E = std::max<uint64_t>(16384, std::min<uint64_t>(E, 65536));
   DevBuf pre, flag;
   NX_TRY(pre.alloc((uint64_t)n * sizeof(uint64_t)));
   NX_TRY(flag.alloc((uint64_t)n * sizeof(uint32_t)));

@@ -87,7 +87,7 @@ uint64_t piece_len(const nx_graph* g, const Dsss& d, uint32_t i, uint32_t t, uin
 
 uint64_t target_block_edges(uint64_t total) {
   uint64_t e = total / ((uint64_t)num_sms() * 8);
-  return std::max<uint64_t>(4096, e);
+  return std::max<uint64_t>(16384, e);
 }
 
 // Tiles of columns [c0, c1), sweeping sources [i0, i1) over `ds`.
@@ -743,6 +743,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   if (nbands > 1) NX_TRY(ensure(g->accres, (size_t)n * 4));
   SweepArgs a = base_args(g, prog, p, tele);
   a.items = pl.items.as<Item>();
+
   a.split = g->split_buf.p;
 
   // streaming buffers

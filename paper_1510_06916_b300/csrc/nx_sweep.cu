@@ -84,48 +84,41 @@ __device__ __forceinline__ T ld_gather(const T* p) {
 
 template <int K>
 struct Prog;
+// gather(raw, od, u, w): the contribution of source u whose stored value is
+// `raw` (its value read from device memory).
 template <>
-struct Prog<PK_PR> : PrSum {  // gathers c[u] = r[u] / outdeg[u]
+struct Prog<PK_PR> : PrSum {  // c[u] = r[u] / outdeg[u]
   static constexpr bool weighted = false;
-  __device__ static float gather(const void* g, const uint32_t*, uint32_t u, float) {
-    return ld_gather(static_cast<const float*>(g) + u);
-  }
+  __device__ static float gather(float raw, const uint32_t*, uint32_t, float) { return raw; }
 };
 template <>
-struct Prog<PK_WPR> : PrSum {  // gathers w^_uv r[u]
+struct Prog<PK_WPR> : PrSum {  // w^_uv r[u]
   static constexpr bool weighted = true;
-  __device__ static float gather(const void* g, const uint32_t*, uint32_t u, float w) {
-    return w * __ldg(static_cast<const float*>(g) + u);
-  }
+  __device__ static float gather(float raw, const uint32_t*, uint32_t, float w) { return w * raw; }
 };
 template <>
-struct Prog<PK_ADJ> : PrSum {  // gathers w^_uv lambda[v] over the transpose DSSS
+struct Prog<PK_ADJ> : PrSum {  // w^_uv lambda[v] over the transpose DSSS
   static constexpr bool weighted = true;
-  __device__ static float gather(const void* g, const uint32_t*, uint32_t u, float w) {
-    return w * __ldg(static_cast<const float*>(g) + u);
-  }
+  __device__ static float gather(float raw, const uint32_t*, uint32_t, float w) { return w * raw; }
 };
 template <>
-struct Prog<PK_PRD> : PrSum {  // gathers r[u] / outdeg[u] (u has an out-edge)
+struct Prog<PK_PRD> : PrSum {  // r[u] / outdeg[u] (u has an out-edge)
   static constexpr bool weighted = false;
-  __device__ static float gather(const void* g, const uint32_t* od, uint32_t u, float) {
-    return __ldg(static_cast<const float*>(g) + u) / (float)__ldg(od + u);
+  __device__ static float gather(float raw, const uint32_t* od, uint32_t u, float) {
+    return raw / (float)__ldg(od + u);
   }
 };
 template <>
 struct Prog<PK_BFS> : MinU {  // depth[u] + 1 (infinity stays infinity)
   static constexpr bool weighted = false;
-  __device__ static uint32_t gather(const void* g, const uint32_t*, uint32_t u, float) {
-    uint32_t d = ld_gather(static_cast<const uint32_t*>(g) + u);
-    return d == kInf ? kInf : d + 1;
+  __device__ static uint32_t gather(uint32_t raw, const uint32_t*, uint32_t, float) {
+    return raw == kInf ? kInf : raw + 1;
   }
 };
 template <>
 struct Prog<PK_WCC> : MinU {  // label[u]
   static constexpr bool weighted = false;
-  __device__ static uint32_t gather(const void* g, const uint32_t*, uint32_t u, float) {
-    return ld_gather(static_cast<const uint32_t*>(g) + u);
-  }
+  __device__ static uint32_t gather(uint32_t raw, const uint32_t*, uint32_t, float) { return raw; }
 };
 
 __device__ __forceinline__ uint4 ld_stream(const uint32_t* p) {
@@ -219,7 +212,10 @@ __device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
       const float wf = (k & 3) == 0 ? f.x : (k & 3) == 1 ? f.y : (k & 3) == 2 ? f.z : f.w;
       const bool valid = ((uint32_t)(lane * kEPL + k) - lo) < span;
       key[k] = valid ? (w >> lb) : kSent;
-      val[k] = valid ? PG::gather(g, od, sbase + (w & smask), wf) : PG::identity();
+      const uint32_t u = sbase + (w & smask);
+      V raw = PG::identity();
+      if (valid) raw = ld_gather(static_cast<const V*>(g) + u);
+      val[k] = valid ? PG::gather(raw, od, u, wf) : PG::identity();
     }
     // runs of equal destination inside the lane: first (head), middle, last (tail)
     uint32_t hk = key[0], ck = key[0];
@@ -552,6 +548,9 @@ __global__ void __launch_bounds__(kThreads) k_multi(const SweepArgs* __restrict_
                                                     long long limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t s_idx;
+  // the item's arguments live in shared memory: reading them through a global
+  // reference would reload them after every store the sweep makes
+  __shared__ __align__(16) SweepArgs s_args;
   for (uint32_t itn = 0; itn < iters; ++itn) {
     const uint32_t par = itn & 1u;
     for (;;) {
@@ -561,7 +560,13 @@ __global__ void __launch_bounds__(kThreads) k_multi(const SweepArgs* __restrict_
       const uint32_t q = s_idx;
       if (q >= nitems) break;
       const MItem mi = items[q];
-      sweep_item<K>(args[2 * mi.gid + par], mi.it, smem_raw);
+      {
+        const uint32_t* srcw = reinterpret_cast<const uint32_t*>(args + 2 * mi.gid + par);
+        uint32_t* dstw = reinterpret_cast<uint32_t*>(&s_args);
+        for (uint32_t w = threadIdx.x; w < sizeof(SweepArgs) / 4; w += blockDim.x) dstw[w] = srcw[w];
+      }
+      __syncthreads();
+      sweep_item<K>(s_args, mi.it, smem_raw);
     }
     if (!grid_barrier(sy, gridDim.x, limit)) return;
   }
@@ -615,6 +620,22 @@ nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaS
   if (nitems == 0) return NX_OK;
   const bool sums = (kind == PK_PR || kind == PK_WPR || kind == PK_PRD || kind == PK_ADJ);
   const size_t smem = (size_t)a.tile_max * (sums ? 8 : 4);
+  if (smem > 40 * 1024) {  // dynamic + static shared memory above the 48 KB default
+    static bool raised[8] = {};
+    if (!raised[kind]) {
+      cudaError_t e = cudaSuccess;
+      switch (kind) {
+        case PK_PR: e = cudaFuncSetAttribute(k_sweep<PK_PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
+        case PK_WPR: e = cudaFuncSetAttribute(k_sweep<PK_WPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
+        case PK_BFS: e = cudaFuncSetAttribute(k_sweep<PK_BFS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
+        case PK_WCC: e = cudaFuncSetAttribute(k_sweep<PK_WCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
+        case PK_PRD: e = cudaFuncSetAttribute(k_sweep<PK_PRD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
+        case PK_ADJ: e = cudaFuncSetAttribute(k_sweep<PK_ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
+      raised[kind] = true;
+    }
+  }
   switch (kind) {
     case PK_PR: k_sweep<PK_PR><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_WPR: k_sweep<PK_WPR><<<nitems, kThreads, smem, s>>>(a); break;
