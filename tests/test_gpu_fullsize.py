@@ -1,0 +1,130 @@
+"""Full-size parity: the workloads the benchmark measures, against the FP64 oracle.
+
+These build the full graphs (up to R-MAT scale 26, 1,476,395,008 edges) and run
+the oracle on the host cores, so they take minutes. Tolerances as in
+test_gpu_parity.py: BFS/WCC bit-exact; PageRank L1 <= 1e-6 and max relative
+error <= 1e-4; gradients relative L1 <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_06916_b300 import inputs
+from paper_1510_06916_b300 import nxgraph as nx
+
+pytestmark = pytest.mark.gpu
+
+
+def _pr_close(gpu, ref, what):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    l1 = float(np.abs(gpu - ref).sum())
+    nz = ref != 0
+    rel = float((np.abs(gpu - ref)[nz] / np.abs(ref[nz])).max())
+    print(f"{what}: L1={l1:.3e} max_rel={rel:.3e}")
+    assert l1 <= 1e-6 and rel <= 1e-4, (what, l1, rel)
+
+
+def test_rmat26_p64_spu_and_mpu_6gb():
+    # R-MAT scale 26, edge factor 22, seed 5, P = 64: PageRank 10 iterations, BFS, WCC
+    # under SPU in HBM, and PageRank / BFS under MPU with a 6 GB device budget.
+    scale, ef, seed, P = 26, 22, 5, 64
+    n, m = 1 << scale, ef << scale
+    s, d, _ = inputs.rmat_edges(scale, m, seed)
+    import torch
+
+    src = torch.from_numpy(s.view(np.int32)).cuda()
+    dst = torch.from_numpy(d.view(np.int32)).cuda()
+    g = nx.Graph(src, dst, n, P, transpose=True)
+    del src, dst
+    torch.cuda.empty_cache()
+    ref = oracle.pagerank(n, s, d, 0.85, 10)
+    g.run("pr", 10, "spu")
+    _pr_close(g.values(), ref, "rmat26 PR SPU")
+    st = g.run("pr", 10, "mpu", budget=6 * 10**9)
+    assert st["streamed_cols"] > 0 and st["Q"] == P
+    _pr_close(g.values(), ref, "rmat26 PR MPU 6GB")
+    del ref
+    bfs = oracle.bfs(n, s, d, 0)
+    g.run("bfs", 1000, "spu", root=0)
+    assert (g.values(dtype=np.uint32) == bfs).all()
+    g.run("bfs", 1000, "mpu", budget=6 * 10**9, root=0)
+    assert (g.values(dtype=np.uint32) == bfs).all()
+    del bfs
+    wcc = oracle.wcc(n, s, d)
+    g.run("wcc", 1000, "spu")
+    assert (g.values(dtype=np.uint32) == wcc).all()
+    g.free()
+
+
+def test_rmat24_ppr_batch_64_vectors():
+    # R-MAT scale 24, seed 3: 64 PPR teleports (1..1000 seeds), 30 iterations in one sweep
+    import torch
+
+    scale, seed, B = 24, 3, 64
+    n, m = 1 << scale, 16 << scale
+    s, d, _ = inputs.rmat_edges(scale, m, seed)
+    g = nx.Graph(s, d, n, 16)
+    v, b, t = inputs.ppr_seed_lists(n, B, seed)
+    T = torch.zeros((n, B), dtype=torch.float32, device="cuda")
+    T[torch.from_numpy(v).cuda(), torch.from_numpy(b).cuda()] = torch.from_numpy(t).cuda()
+    R, _ = g.ppr_batch(T, iters=30)
+    R = R.cpu().numpy()
+    sums = R.astype(np.float64).sum(axis=0)
+    assert np.abs(sums - 1.0).max() < 1e-5  # every column keeps unit mass
+    for col in (0, 37):  # two columns against the oracle
+        tv = np.zeros(n)
+        sel = b == col
+        tv[v[sel]] = t[sel]
+        _pr_close(R[:, col], oracle.personalized_pagerank(n, s, d, tv, 0.85, 30), f"batch col {col}")
+    g.free()
+
+
+def test_rmat24_adjoint_50_50():
+    # weighted PageRank on R-MAT scale 24 (seed 4), w ~ U(0.5, 1.5), loss = sum over
+    # 1,024 targets; 50 forward and 50 adjoint iterations vs the FP64 adjoint.
+    scale, seed = 24, 4
+    n, m = 1 << scale, 16 << scale
+    s, d, w = inputs.rmat_edges(scale, m, seed, weights=True)
+    T = inputs.targets(n, 1024, seed)
+    gv = np.zeros(n, np.float32)
+    gv[T] = 1.0
+    g = nx.Graph(s, d, n, 16, transpose=True, weights=w)
+    g.run("wpr", 50)
+    dw = np.empty(m, np.float32)
+    dt = np.empty(n, np.float32)
+    g.adjoint_wpr(gv, 50, dw, dt)
+    ref = oracle.wpr_adjoint(n, s, d, w.astype(np.float64), gv.astype(np.float64), 0.85, 50, 50)
+    _pr_close(g.values(), ref["r"], "rmat24 WPR forward")
+    for got, want, what in ((dt, ref["dt"], "dL/dt"), (dw, ref["dw"], "dL/dw")):
+        rl1 = np.abs(got.astype(np.float64) - want).sum() / np.abs(want).sum()
+        print(f"{what}: rel_L1={rl1:.3e}")
+        assert rl1 <= 1e-5, (what, rl1)
+    g.free()
+
+
+def test_256_graphs_one_launch():
+    # 256 R-MAT graphs, scales U{10..18}, edge factor 16: PR x20 / BFS / WCC per graph
+    scales = inputs.multigraph_scales(256)
+    graphs, data = [], []
+    for gi, sc in enumerate(scales):
+        n = 1 << sc
+        s, d, _ = inputs.rmat_edges(sc, 16 << sc, inputs.multigraph_seed(gi))
+        graphs.append(nx.Graph(s, d, n, max(1, min(16, n >> 12)), transpose=True))
+        data.append((n, s, d))
+    nx.run_multi(graphs, "pr", 20)
+    worst = 0.0
+    for g, (n, s, d) in zip(graphs, data):
+        r = g.values().astype(np.float64)
+        ref = oracle.pagerank(n, s, d, 0.85, 20)
+        l1 = np.abs(r - ref).sum()
+        worst = max(worst, l1)
+        assert l1 <= 1e-6
+    print(f"256 graphs PR: worst L1={worst:.3e}")
+    nx.run_multi(graphs, "bfs", 60)
+    for g, (n, s, d) in zip(graphs, data):
+        assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 0)).all()
+    nx.run_multi(graphs, "wcc", 60)
+    for g, (n, s, d) in zip(graphs, data):
+        assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+    for g in graphs:
+        g.free()
