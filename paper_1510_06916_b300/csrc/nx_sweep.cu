@@ -128,12 +128,6 @@ __device__ __forceinline__ float4 ld_stream_f(const float* p) {
   return __ldcs(reinterpret_cast<const float4*>(p));
 }
 
-// Folds edges [a, b) of one piece into the tile accumulator. Edge e is read at
-// ew[e - ew_lo]; its source value at g[sbase + src_local]. The piece is cut
-// into 256-edge steps from a = floor8(a); step k goes to warp (k + rot) % 8 so
-// that short pieces do not all land on the same warps (rot advances by the
-// piece's step count). Each warp loads its next step's edge words before it
-// gathers and reduces the current one.
 // Edges per lane in one warp step (8 or 16): two or four 16-byte loads.
 #ifndef NX_EPL
 #define NX_EPL 8
@@ -156,6 +150,79 @@ __device__ __forceinline__ void load_step(EdgeRegs<kEPL>& r, const uint32_t* __r
   for (int k = 0; k < kEPL / 4; ++k) {
     r.q[k] = ld_stream(ew + idx + 4 * k);
     if (PG::weighted) r.f[k] = ld_stream_f(wt + idx + 4 * k);
+  }
+}
+
+// One warp step: the kStep edge words in `cur` start at edge index `base`;
+// edges outside [a, b) are masked. Gathers the sources, reduces runs of equal
+// destination in registers and across lanes, and folds them into `acc`.
+template <class PG>
+__device__ __forceinline__ void process_step(const EdgeRegs<kEPL>& cur, uint64_t base, uint64_t a,
+                                             uint64_t b, const void* __restrict__ g,
+                                             uint32_t sbase, uint32_t lb, Acc<typename PG::V> acc,
+                                             const uint32_t* __restrict__ od) {
+  using V = typename PG::V;
+  const int lane = threadIdx.x & 31;
+  const uint32_t smask = (1u << lb) - 1u;
+  const uint32_t lo = base < a ? (uint32_t)(a - base) : 0u;
+  const uint32_t hi = (b - base) < (uint64_t)kStep ? (uint32_t)(b - base) : (uint32_t)kStep;
+  const uint32_t span = hi - lo;
+  uint32_t key[kEPL];
+  V val[kEPL];
+#pragma unroll
+  for (int k = 0; k < kEPL; ++k) {
+    const uint4 q = cur.q[k / 4];
+    const float4 f = cur.f[k / 4];
+    const uint32_t w = (k & 3) == 0 ? q.x : (k & 3) == 1 ? q.y : (k & 3) == 2 ? q.z : q.w;
+    const float wf = (k & 3) == 0 ? f.x : (k & 3) == 1 ? f.y : (k & 3) == 2 ? f.z : f.w;
+    const bool valid = ((uint32_t)(lane * kEPL + k) - lo) < span;
+    key[k] = valid ? (w >> lb) : kSent;
+    const uint32_t u = sbase + (w & smask);
+    V raw = PG::identity();
+    if (valid) raw = ld_gather(static_cast<const V*>(g) + u);
+    val[k] = valid ? PG::gather(raw, od, u, wf) : PG::identity();
+  }
+  // runs of equal destination inside the lane: first (head), middle, last (tail)
+  uint32_t hk = key[0], ck = key[0];
+  V hs = val[0], cs = val[0];
+  bool single = true;
+#pragma unroll
+  for (int k = 1; k < kEPL; ++k) {
+    const bool brk = key[k] != ck;
+    if (brk && !single && ck != kSent) PG::emit_short(acc, ck, cs);
+    if (brk && single) {
+      hk = ck;
+      hs = cs;
+    }
+    single = single && !brk;
+    cs = brk ? val[k] : PG::op(cs, val[k]);
+    ck = key[k];
+  }
+  const uint32_t first_key = single ? ck : hk;
+  uint32_t prev_tail = __shfl_up_sync(0xffffffffu, ck, 1);
+  if (lane == 0) prev_tail = kSent;
+  uint32_t next_first = __shfl_down_sync(0xffffffffu, first_key, 1);
+  if (lane == 31) next_first = kSent;
+  // segmented inclusive scan of the tail runs across lanes
+  const bool starts = (lane == 0) || !single || (ck != prev_tail);
+  const uint32_t smask_b = __ballot_sync(0xffffffffu, starts);
+  const uint32_t le = smask_b & (0xffffffffu >> (31 - lane));
+  const int seg0 = 31 - __clz(le);
+  V x = cs;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    V y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane - d >= seg0) x = PG::op(y, x);
+  }
+  const V prev_x = __shfl_up_sync(0xffffffffu, x, 1);
+  // the head run joins the chain of the lanes before it when the key matches
+  if (!single && hk != kSent) {
+    if (lane > 0 && hk == prev_tail) PG::emit(acc, hk, PG::op(prev_x, hs));
+    else PG::emit_short(acc, hk, hs);
+  }
+  if (ck != kSent && next_first != ck) {
+    if (seg0 < lane) PG::emit(acc, ck, x);  // the run crossed lanes
+    else PG::emit_short(acc, ck, x);
   }
 }
 
@@ -192,74 +259,133 @@ __device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
     if (p < b) load_step<PG>(nxt, ew, wt, p - ew_lo);
   }
   while (base < b) {
-    // valid edges of this step: offsets [lo, hi) from base (32-bit)
-    const uint32_t lo = base < a ? (uint32_t)(a - base) : 0u;
-    const uint32_t hi = (b - base) < (uint64_t)kStep ? (uint32_t)(b - base) : (uint32_t)kStep;
-    const uint32_t span = hi - lo;
     const EdgeRegs<kEPL> cur = nxt;
     const uint64_t nbase = base + (uint64_t)kWarps * kStep;
     {  // prefetch the warp's next step
       const uint64_t pn = nbase + (uint64_t)lane * kEPL;
       if (pn < b) load_step<PG>(nxt, ew, wt, pn - ew_lo);
     }
-    uint32_t key[kEPL];
-    V val[kEPL];
-#pragma unroll
-    for (int k = 0; k < kEPL; ++k) {
-      const uint4 q = cur.q[k / 4];
-      const float4 f = cur.f[k / 4];
-      const uint32_t w = (k & 3) == 0 ? q.x : (k & 3) == 1 ? q.y : (k & 3) == 2 ? q.z : q.w;
-      const float wf = (k & 3) == 0 ? f.x : (k & 3) == 1 ? f.y : (k & 3) == 2 ? f.z : f.w;
-      const bool valid = ((uint32_t)(lane * kEPL + k) - lo) < span;
-      key[k] = valid ? (w >> lb) : kSent;
-      const uint32_t u = sbase + (w & smask);
-      V raw = PG::identity();
-      if (valid) raw = ld_gather(static_cast<const V*>(g) + u);
-      val[k] = valid ? PG::gather(raw, od, u, wf) : PG::identity();
-    }
-    // runs of equal destination inside the lane: first (head), middle, last (tail)
-    uint32_t hk = key[0], ck = key[0];
-    V hs = val[0], cs = val[0];
-    bool single = true;
-#pragma unroll
-    for (int k = 1; k < kEPL; ++k) {
-      const bool brk = key[k] != ck;
-      if (brk && !single && ck != kSent) PG::emit_short(acc, ck, cs);
-      if (brk && single) {
-        hk = ck;
-        hs = cs;
-      }
-      single = single && !brk;
-      cs = brk ? val[k] : PG::op(cs, val[k]);
-      ck = key[k];
-    }
-    const uint32_t first_key = single ? ck : hk;
-    uint32_t prev_tail = __shfl_up_sync(0xffffffffu, ck, 1);
-    if (lane == 0) prev_tail = kSent;
-    uint32_t next_first = __shfl_down_sync(0xffffffffu, first_key, 1);
-    if (lane == 31) next_first = kSent;
-    // segmented inclusive scan of the tail runs across lanes
-    const bool starts = (lane == 0) || !single || (ck != prev_tail);
-    const uint32_t smask_b = __ballot_sync(0xffffffffu, starts);
-    const uint32_t le = smask_b & (0xffffffffu >> (31 - lane));
-    const int seg0 = 31 - __clz(le);
-    V x = cs;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      V y = __shfl_up_sync(0xffffffffu, x, d);
-      if (lane - d >= seg0) x = PG::op(y, x);
-    }
-    const V prev_x = __shfl_up_sync(0xffffffffu, x, 1);
-    // the head run joins the chain of the lanes before it when the key matches
-    if (!single && hk != kSent) {
-      if (lane > 0 && hk == prev_tail) PG::emit(acc, hk, PG::op(prev_x, hs));
-      else PG::emit_short(acc, hk, hs);
-    }
-    if (ck != kSent && next_first != ck) {
-      if (seg0 < lane) PG::emit(acc, ck, x);  // the run crossed lanes
-      else PG::emit_short(acc, ck, x);
-    }
+    process_step<PG>(cur, base, a, b, g, sbase, lb, acc, od);
     base = nbase;
+  }
+}
+
+// Block-wide exclusive scan (all kThreads threads call it); returns this
+// thread's prefix and writes the total to *total.
+template <class T>
+__device__ __forceinline__ T block_scan_excl(T v, T* total) {
+  __shared__ T wsum[kWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  T before = 0, all = 0;
+#pragma unroll
+  for (int q = 0; q < kWarps; ++q) {
+    const T t = wsum[q];
+    before += q < w ? t : T(0);
+    all += t;
+  }
+  __syncthreads();
+  *total = all;
+  return before + x - v;
+}
+
+// The item's pieces as one sequence of warp steps (at most kThreads pieces):
+// warps take steps w, w + 8, ... over the whole sequence, so they stay
+// balanced and each prefetches its next step even across piece boundaries.
+// The table lives in dynamic shared memory after the accumulators, 16 bytes
+// per piece: valid range [a, b) (edge indices < 2^32), the warp steps before
+// the piece (low 24 bits) with the DSSS index (bit 24) and a staged-source
+// flag (bit 25), and the source interval base.
+struct FlatEnt {
+  uint32_t a, b, cum, sb;
+};
+
+template <class PG>
+__device__ __forceinline__ void sweep_flat(const SweepArgs& a, const Item& it, uint32_t t,
+                                           uint32_t tb, uint32_t nt, uint32_t i_lo, uint32_t i_hi,
+                                           Acc<typename PG::V> acc, FlatEnt* tab) {
+  const uint32_t npi = i_hi - i_lo;
+  const uint32_t np = (uint32_t)a.nsrc * npi;
+  const uint32_t k = threadIdx.x;
+  uint64_t p0 = 0, len = 0;
+  bool active = false;
+  uint32_t s = 0, i = 0;
+  if (k < np) {
+    s = k / npi;
+    i = i_lo + k % npi;
+    const uint64_t* po = a.src[s].piece_off;
+    const uint64_t pc = piece_index(a.P, tb, nt, i, t);
+    p0 = po[pc];
+    len = po[pc + 1] - p0;
+    active = !a.act_in || a.act_in[i];
+  }
+  uint64_t vtot;
+  const uint64_t vo = block_scan_excl<uint64_t>(len, &vtot);
+  uint32_t steps = 0;
+  uint64_t ea = 0, eb = 0;
+  if (k < np && active) {
+    const uint64_t lo = vo > it.vbeg ? vo : it.vbeg;
+    const uint64_t hi = (vo + len) < it.vend ? (vo + len) : it.vend;
+    if (lo < hi) {
+      ea = p0 + (lo - vo);
+      eb = p0 + (hi - vo);
+      steps = (uint32_t)((eb - (ea & ~(uint64_t)(kEPL - 1)) + kStep - 1) / kStep);
+    }
+  }
+  uint32_t stot;
+  const uint32_t before = block_scan_excl<uint32_t>(steps, &stot);
+  const bool staged = (i == a.stage_i);
+  if (k < np) {
+    FlatEnt e;
+    e.a = (uint32_t)ea;
+    e.b = (uint32_t)eb;
+    e.cum = before | (s << 24) | (staged ? (1u << 25) : 0u);
+    e.sb = staged ? 0u : i * a.L;
+    tab[k] = e;
+  }
+  if (k == 0) tab[np].cum = stot;
+  __syncthreads();
+  constexpr uint32_t kCum = (1u << 24) - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t q = warp, p = 0;
+  if (q >= stot) return;
+  while ((tab[p + 1].cum & kCum) <= q) ++p;
+  FlatEnt ep = tab[p];
+  uint64_t base = (uint64_t)(ep.a & ~(uint32_t)(kEPL - 1)) + (uint64_t)(q - (ep.cum & kCum)) * kStep;
+  EdgeRegs<kEPL> nxt;
+#pragma unroll
+  for (int z = 0; z < kEPL / 4; ++z) {
+    nxt.q[z] = make_uint4(0, 0, 0, 0);
+    nxt.f[z] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  {
+    const uint32_t sx = (ep.cum >> 24) & 1u;
+    const uint64_t e = base + (uint64_t)lane * kEPL;
+    if (e < ep.b) load_step<PG>(nxt, a.src[sx].ew, a.src[sx].wt, e - a.ew_lo[sx]);
+  }
+  while (q < stot) {
+    const EdgeRegs<kEPL> cur = nxt;
+    const FlatEnt ec = ep;
+    const uint64_t bc = base;
+    const uint32_t qn = q + kWarps;
+    if (qn < stot) {  // prefetch the warp's next step, possibly in a later piece
+      while ((tab[p + 1].cum & kCum) <= qn) ++p;
+      ep = tab[p];
+      base = (uint64_t)(ep.a & ~(uint32_t)(kEPL - 1)) + (uint64_t)(qn - (ep.cum & kCum)) * kStep;
+      const uint32_t sx = (ep.cum >> 24) & 1u;
+      const uint64_t e = base + (uint64_t)lane * kEPL;
+      if (e < ep.b) load_step<PG>(nxt, a.src[sx].ew, a.src[sx].wt, e - a.ew_lo[sx]);
+    }
+    const void* g = (ec.cum & (1u << 25)) ? a.gstage : a.gsrc;
+    process_step<PG>(cur, bc, ec.a, ec.b, g, ec.sb, a.lb, acc, a.outdeg);
+    q = qn;
   }
 }
 
@@ -311,6 +437,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
     uint32_t rot = 0;
     const uint32_t i_lo = a.mode == 1 ? it.row : a.src_lo;
     const uint32_t i_hi = a.mode == 1 ? it.row + 1 : a.src_hi;
+    const bool flat = a.flat_cap && (uint32_t)a.nsrc * (i_hi - i_lo) <= a.flat_cap;
+    if (flat) {
+      FlatEnt* tab = reinterpret_cast<FlatEnt*>(smem_raw + (size_t)a.tile_max * (PG::compensated ? 8 : 4));
+      if (i_hi > i_lo) sweep_flat<PG>(a, it, t, tb, nt, i_lo, i_hi, acc, tab);
+    } else
     for (int s = 0; s < a.nsrc && vo < it.vend; ++s) {
       const uint64_t* po = a.src[s].piece_off;
       for (uint32_t i = i_lo; i < i_hi && vo < it.vend; ++i) {
@@ -578,7 +709,7 @@ nx_status launch_multi(ProgKind kind, const SweepArgs* args, const MItem* items,
                        uint32_t iters, uint32_t* ctr, MultiSync* sy, uint32_t tile_max,
                        uint32_t nblocks, cudaStream_t s) {
   const bool sums = (kind == PK_PR || kind == PK_WPR);
-  const size_t smem = (size_t)tile_max * (sums ? 8 : 4);
+  const size_t smem = (size_t)tile_max * (sums ? 8 : 4) + (size_t)(kThreads + 1) * sizeof(FlatEnt);
   const long long limit = 4000000000ll;  // about two seconds at 2 GHz
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -602,7 +733,7 @@ nx_status launch_multi(ProgKind kind, const SweepArgs* args, const MItem* items,
 
 nx_status multi_blocks(ProgKind kind, uint32_t tile_max, uint32_t* nblocks) {
   const bool sums = (kind == PK_PR || kind == PK_WPR);
-  const size_t smem = (size_t)tile_max * (sums ? 8 : 4);
+  const size_t smem = (size_t)tile_max * (sums ? 8 : 4) + (size_t)(kThreads + 1) * sizeof(FlatEnt);
   int per_sm = 0;
   switch (kind) {
     case PK_PR: NX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi<PK_PR>, kThreads, smem)); break;
@@ -616,10 +747,14 @@ nx_status multi_blocks(ProgKind kind, uint32_t tile_max, uint32_t* nblocks) {
   return NX_OK;
 }
 
+size_t flat_table_bytes(const SweepArgs& a) {
+  return a.flat_cap ? (size_t)(a.flat_cap + 1) * sizeof(FlatEnt) : 0;
+}
+
 nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaStream_t s) {
   if (nitems == 0) return NX_OK;
   const bool sums = (kind == PK_PR || kind == PK_WPR || kind == PK_PRD || kind == PK_ADJ);
-  const size_t smem = (size_t)a.tile_max * (sums ? 8 : 4);
+  const size_t smem = (size_t)a.tile_max * (sums ? 8 : 4) + flat_table_bytes(a);
   if (smem > 40 * 1024) {  // dynamic + static shared memory above the 48 KB default
     static bool raised[8] = {};
     if (!raised[kind]) {

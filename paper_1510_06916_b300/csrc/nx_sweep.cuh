@@ -24,6 +24,10 @@ struct SweepArgs {
   // (the bands before this one) instead of the identity (block 0 of a split
   // tile only).
   const void* acc_in = nullptr;
+  // Items whose piece count (DSSS x source intervals) is at most flat_cap
+  // (<= 256) are swept as one flattened step sequence; the table takes
+  // 16 B x (flat_cap + 1) of dynamic shared memory. 0: per-piece loop.
+  uint32_t flat_cap = 0;
   const Item* items = nullptr;  // nullptr: block b sweeps the whole tile b
   const uint32_t* tile_start = nullptr;
   const uint32_t* col_tb = nullptr;
