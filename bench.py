@@ -118,13 +118,20 @@ def dist_setup():
 
 
 def barrier_max(val, world):
+    """Max of `val` over all ranks (NCCL on GPUs, gloo on CPU)."""
     if world == 1:
         return val
     import torch
     import torch.distributed as dist
-    t = torch.tensor([val], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([val], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_gteps(m, iters, steps, world, ms_max):
+    """Whole-job GTEPS: every rank sweeps its own replica; time = slowest rank."""
+    return m * iters * steps * world / (ms_max / 1e3) / 1e9
 
 
 def barrier(world):
@@ -342,7 +349,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     ms_max = barrier_max(ms, world)
     ms_per_step = ms_max / args.steps
-    value = m * iters * args.steps * world / (ms_max / 1e3) / 1e9
+    value = aggregate_gteps(m, iters, args.steps, world, ms_max)
 
     # roofline of the sweep kernel: algorithmic bytes per launch / launch time
     bytes_per_launch = 4 * m + 16 * n

@@ -1,0 +1,61 @@
+"""The multi-rank path of bench.py on CPU (gloo, world size 2): max-over-ranks
+timing, barriers, the aggregate throughput formula, and the reference arm
+running on rank 0 only."""
+import multiprocessing as mp
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    import torch.distributed as dist
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    v = bench.barrier_max(10.0 * (rank + 1), world)
+    bench.barrier(world)
+    q.put((rank, v))
+    dist.destroy_process_group()
+
+
+def test_barrier_max_over_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got == {0: 20.0, 1: 20.0}
+
+
+def test_aggregate_throughput_is_weak_scaling():
+    m, iters, steps = 1 << 26, 20, 10
+    one = bench.aggregate_gteps(m, iters, steps, 1, 100.0)
+    assert bench.aggregate_gteps(m, iters, steps, 4, 100.0) == pytest.approx(4 * one)
+    # the slowest rank sets the time
+    assert bench.aggregate_gteps(m, iters, steps, 2, 200.0) == pytest.approx(one)
+
+
+def test_reference_arm_runs_on_rank0_only(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class Args:
+        steps, warmup, workload = 1, 0, "rmat16"
+
+    assert bench.run_reference(Args(), bench.WORKLOADS["rmat16"]) == 0
+    assert capsys.readouterr().out == ""
