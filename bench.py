@@ -302,6 +302,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-PPR, adjoint and multi-graph measurements")
+    ap.add_argument("--extras-only", default=None,
+                    choices=["ppr_batch", "adjoint", "multi_graph", "autotune"],
+                    help="diagnostic: run one extra measurement and print it (for profiling)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -312,6 +315,15 @@ def main():
     world, rank, local = dist_setup()
     from paper_1510_06916_b300 import inputs
     from paper_1510_06916_b300 import nxgraph as nx
+
+    extra_fns = {"ppr_batch": measure_ppr_batch, "adjoint": measure_adjoint,
+                 "multi_graph": measure_multi, "autotune": measure_autotune}
+    if args.extras_only:
+        nx.set_stream(torch.cuda.current_stream())
+        out = extra_fns[args.extras_only](nx, inputs, torch)
+        if rank == 0:
+            print(json.dumps({"extras_only": args.extras_only, "result": out}), flush=True)
+        return 0
 
     n = 1 << w["scale"]
     m = w["ef"] << w["scale"]
@@ -405,8 +417,7 @@ def main():
     extras = None
     if not args.no_extras:
         extras = {}
-        for name, fn in (("ppr_batch", measure_ppr_batch), ("adjoint", measure_adjoint),
-                         ("multi_graph", measure_multi), ("autotune", measure_autotune)):
+        for name, fn in extra_fns.items():
             try:
                 extras[name] = fn(nx, inputs, torch)
             except Exception as e:  # pragma: no cover

@@ -30,6 +30,10 @@ namespace {
 constexpr int kBT = 256;  // threads per block
 constexpr int kBW = kBT / 32;
 constexpr uint32_t kSub = 128;  // destinations per sub-tile
+#ifndef NX_ROWS
+#define NX_ROWS 4
+#endif
+constexpr int kRows = NX_ROWS;  // source rows in flight per warp
 
 struct BItem {
   uint32_t tile, sub;      // tile and sub-tile index inside it
@@ -128,11 +132,11 @@ __global__ void __launch_bounds__(kBT) k_ppr_batch(const BArgs a) {
       uint32_t curk = 0xFFFFFFFFu;
 #pragma unroll
       for (int q = 0; q < C; ++q) s[q] = cmp[q] = 0.f;
-      for (uint32_t x = 0; x < cnt; x += 4) {
-        float row[4][C];
-        uint32_t key[4];
+      for (uint32_t x = 0; x < cnt; x += kRows) {
+        float row[kRows][C];
+        uint32_t key[kRows];
 #pragma unroll
-        for (int y = 0; y < 4; ++y) {  // four rows in flight
+        for (int y = 0; y < kRows; ++y) {  // kRows rows in flight
           const uint32_t wy = __shfl_sync(0xffffffffu, w, (x + y) & 31);
           const bool ok = x + y < cnt;
           key[y] = ok ? (wy >> a.lb) - k0 : 0xFFFFFFFFu;
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(kBT) k_ppr_batch(const BArgs a) {
           for (int q = 0; q < C; ++q) row[y][q] = ok ? __ldg(src + q) : 0.f;
         }
 #pragma unroll
-        for (int y = 0; y < 4; ++y) {
+        for (int y = 0; y < kRows; ++y) {
           if (key[y] == 0xFFFFFFFFu) continue;
           if (key[y] != curk) {
             if (curk != 0xFFFFFFFFu)
