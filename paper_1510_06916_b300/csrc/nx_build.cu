@@ -416,7 +416,7 @@ uint64_t nx_graph::device_bytes() const {
                               &fwd.hub_off, &fwd.hub_dst, &tr.ew, &tr.wt, &tr.piece_off,
                               &tr.hub_off, &tr.hub_dst, &outdeg, &wsum, &orig_src, &orig_dst,
                               &val[0], &val[1], &aux[0], &aux[1], &act[0], &act[1], &scal,
-                              &tile_part, &split_buf, &tile_ticket, &hubs, &tele,
+                              &tile_part, &split_buf, &tile_ticket, &hubs, &hubs_t, &tele,
                               &lam[0], &lam[1], &ybuf, &stage[0], &stage[1], &vstage[0],
                               &vstage[1], &vstage[2], &vstage[3], &accres, &init_part};
   uint64_t s = 0;

@@ -123,9 +123,10 @@ void plan_tiles(const nx_graph* g, const std::vector<const Dsss*>& ds, uint32_t 
   }
 }
 
-// Single pieces (i, t) of row i for tiles of columns [c0, c1) (ToHub / row pass).
-void plan_row(const nx_graph* g, const Dsss& d, uint32_t i, uint32_t c0, uint32_t c1, uint64_t blk,
-              PlanOut& out) {
+// Single pieces (i, t) of row i of DSSS number `sx` for tiles of columns
+// [c0, c1) (ToHub / row pass).
+void plan_row(const nx_graph* g, const Dsss& d, uint32_t sx, uint32_t i, uint32_t c0, uint32_t c1,
+              uint64_t blk, PlanOut& out) {
   const auto& tb = g->geo.h_col_tb;
   std::vector<std::pair<uint64_t, Item>> tmp;
   for (uint32_t j = c0; j < c1; ++j)
@@ -140,6 +141,7 @@ void plan_row(const nx_graph* g, const Dsss& d, uint32_t i, uint32_t c0, uint32_
         it.slot = k > 1 ? out.slots : 0;
         it.sub = q;
         it.row = i;
+        it.pad = sx;
         it.vbeg = cost * q / k;
         it.vend = (q + 1 == k) ? ~0ull : cost * (q + 1) / k;
         tmp.push_back({cost / k + 1, it});
@@ -185,9 +187,9 @@ nx_status prepare(nx_graph* g) {
     NX_CUDA(cudaMemsetAsync(g->scal.p, 0, 64, stream()));
   }
   if (!g->tile_part.p) NX_TRY(g->tile_part.alloc(((size_t)g->geo.ntiles + 1) * 8));
-  if (!g->tile_ticket.p) {
-    NX_TRY(g->tile_ticket.alloc(((size_t)g->geo.ntiles + 1) * 4));
-    NX_CUDA(cudaMemsetAsync(g->tile_ticket.p, 0, ((size_t)g->geo.ntiles + 1) * 4, stream()));
+  if (!g->tile_ticket.p) {  // per (tile, DSSS)
+    NX_TRY(g->tile_ticket.alloc((2 * (size_t)g->geo.ntiles + 1) * 4));
+    NX_CUDA(cudaMemsetAsync(g->tile_ticket.p, 0, (2 * (size_t)g->geo.ntiles + 1) * 4, stream()));
   }
   return NX_OK;
 }
@@ -289,8 +291,14 @@ SweepArgs base_args(nx_graph* g, nx_program prog, const nx_params& p, const floa
   a.n_epi = g->geo.ntiles;
   a.src_lo = 0;
   a.src_hi = g->geo.P;
-  a.hub_off = g->fwd.hub_off.as<uint64_t>();
-  a.hub_dst = g->fwd.hub_dst.as<uint16_t>();
+  a.hub_off[0] = g->fwd.hub_off.as<uint64_t>();
+  a.hub_dst[0] = g->fwd.hub_dst.as<uint16_t>();
+  a.hubs[0] = g->hubs.p;
+  if (tr) {
+    a.hub_off[1] = g->tr.hub_off.as<uint64_t>();
+    a.hub_dst[1] = g->tr.hub_dst.as<uint16_t>();
+    a.hubs[1] = g->hubs_t.p;
+  }
   // Flattened step schedule: measured faster for BFS / WCC (short, activity-
   // filtered pieces), slightly slower for the PageRank family on one graph.
   const uint32_t npieces = (uint32_t)a.nsrc * g->geo.P;
@@ -345,7 +353,6 @@ nx_status dpu_iteration(nx_graph* g, nx_program prog, SweepArgs& a, uint32_t n_t
   th.mode = 1;
   th.q_res = 0;
   th.items = all;
-  th.hubs = g->hubs.p;
   NX_TRY(launch_sweep(kind_of(prog), th, n_tohub, stream()));
   SweepArgs fh = a;
   fh.mode = 0;
@@ -353,7 +360,6 @@ nx_status dpu_iteration(nx_graph* g, nx_program prog, SweepArgs& a, uint32_t n_t
   fh.src_lo = fh.src_hi = 0;
   fh.hub_lo = 0;
   fh.hub_hi = g->geo.P;
-  fh.hubs = g->hubs.p;
   NX_TRY(launch_sweep(kind_of(prog), fh, n_fromhub, stream()));
   g->cur ^= 1;
   return NX_OK;
@@ -528,7 +534,6 @@ nx_status mpu_iteration(RunCtx& c, SweepArgs& a, Staged& S) {
     m1.items = it;
     m1.q_res = Q;
     m1.accres = g->accres.p;
-    m1.hubs = g->hubs.p;
     m1.gstage = g->vstage[0].p;
     m1.stage_i = i;
     NX_TRY(launch_sweep(K, m1, k, stream()));
@@ -557,7 +562,6 @@ nx_status mpu_iteration(RunCtx& c, SweepArgs& a, Staged& S) {
     m0.src_hi = Q;
     m0.hub_lo = Q;
     m0.hub_hi = P;
-    m0.hubs = g->hubs.p;
     m0.out_base = v0;
     m0.vnew = g->vstage[1].p;
     m0.cnew = has_c ? g->vstage[2].as<float>() : nullptr;
@@ -602,8 +606,6 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   if (strat == NX_MPU && Qb >= P) strat = NX_SPU;  // Q = P: MPU is SPU (Section III-B3)
   const bool staged = (strat == NX_MPU) || (strat == NX_DPU && Qb < P);
   const uint32_t Q = strat == NX_MPU ? Qb : (strat == NX_DPU ? 0 : P);
-  if ((strat == NX_DPU || strat == NX_MPU) && prog == NX_WCC)
-    return invalid("nx_run: hubs hold one DSSS; DPU/MPU run PR, PPR, WPR and BFS (WCC sweeps two)");
   if (budget && (strat == NX_DPU || strat == NX_MPU) && budget < 2ull * L * 4) {
     set_error("nx_run: the budget is below one interval pair (2 L B_a)");
     return NX_ERR_BUDGET_TOO_SMALL;
@@ -716,7 +718,8 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       }
       launch_off[P] = (uint32_t)plan.items.size();  // launch_off[Jc]: resident item count
     } else if (!staged) {  // DPU, intervals resident: ToHub items (all rows), then FromHub tiles
-      for (uint32_t i = 0; i < P; ++i) plan_row(g, g->fwd, i, 0, P, blk, plan);
+      for (size_t sx = 0; sx < c.ds.size(); ++sx)
+        for (uint32_t i = 0; i < P; ++i) plan_row(g, *c.ds[sx], (uint32_t)sx, i, 0, P, blk, plan);
       n_a = (uint32_t)plan.items.size();
       plan_tiles(g, c.ds, 0, 0, 0, P, false, blk, plan);
       n_b = (uint32_t)plan.items.size() - n_a;
@@ -724,8 +727,9 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       launch_off.push_back(0);
       plan_tiles(g, c.ds, 0, Q, 0, Q, true, blk, plan);  // resident block (mode 2)
       launch_off.push_back((uint32_t)plan.items.size());
-      for (uint32_t i = Q; i < P; ++i) {  // rows (mode 1)
-        plan_row(g, g->fwd, i, 0, P, blk, plan);
+      for (uint32_t i = Q; i < P; ++i) {  // rows (mode 1), every DSSS of the program
+        for (size_t sx = 0; sx < c.ds.size(); ++sx)
+          plan_row(g, *c.ds[sx], (uint32_t)sx, i, 0, P, blk, plan);
         launch_off.push_back((uint32_t)plan.items.size());
       }
       plan_tiles(g, c.ds, 0, 0, 0, Q, false, blk, plan);  // resident epilogue (mode 3)
@@ -743,7 +747,10 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   nx_graph::Plan& pl = *slot_plan;
   NX_TRY(ensure_split(g, pl.slots));
   const uint32_t n_a = pl.na, n_b = pl.nb;
-  if (strat == NX_DPU || staged) NX_TRY(ensure(g->hubs, std::max<uint64_t>(g->fwd.D, 1) * 4));
+  if (strat == NX_DPU || staged) {
+    NX_TRY(ensure(g->hubs, std::max<uint64_t>(g->fwd.D, 1) * 4));
+    if (prog == NX_WCC) NX_TRY(ensure(g->hubs_t, std::max<uint64_t>(g->tr.D, 1) * 4));
+  }
 
   if (nbands > 1) NX_TRY(ensure(g->accres, (size_t)n * 4));
   SweepArgs a = base_args(g, prog, p, tele);

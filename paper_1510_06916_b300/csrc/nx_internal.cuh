@@ -129,7 +129,7 @@ struct Item {
   uint32_t sub;     // this block's index among them
   uint64_t vbeg, vend;
   uint32_t row;     // mode 1: the source interval i of the piece
-  uint32_t pad;
+  uint32_t pad;     // mode 1: the DSSS of the piece (0 forward, 1 transpose)
 };
 
 // Piece (i, t) of tile t in column j: P*tb_j + i*nt_j + (t - tb_j).
@@ -161,7 +161,8 @@ struct nx_graph {
   nx::DevBuf tile_part;     // double [ntiles] per-tile dangling partials
   nx::DevBuf split_buf;     // split-tile partial accumulators
   nx::DevBuf tile_ticket;   // uint32 [ntiles]
-  nx::DevBuf hubs;          // hub values [D]
+  nx::DevBuf hubs;          // hub values [D] (forward DSSS)
+  nx::DevBuf hubs_t;        // hub values [D_t] (transpose DSSS, WCC)
   // Work plans (item lists) cached by strategy / DSSS set / placement.
   struct Plan {
     nx::DevBuf items;

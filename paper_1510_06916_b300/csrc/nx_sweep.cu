@@ -63,8 +63,10 @@ struct MinU {  // BFS / WCC: min of uint32
   }
   __device__ static void emit_short(Acc<V> acc, uint32_t k, V v) { emit(acc, k, v); }
   __device__ static V read(Acc<V> acc, uint32_t k) { return acc.hi[k]; }
+  // row passes of WCC update a resident label from the forward and the
+  // transpose DSSS in the same launch: an atomic min keeps that race benign
   __device__ static void emit_global(V* p, V v) {
-    if (v < *p) *p = v;
+    if (v < *p) atomicMin(p, v);
   }
 };
 
@@ -437,12 +439,15 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
     uint32_t rot = 0;
     const uint32_t i_lo = a.mode == 1 ? it.row : a.src_lo;
     const uint32_t i_hi = a.mode == 1 ? it.row + 1 : a.src_hi;
-    const bool flat = a.flat_cap && (uint32_t)a.nsrc * (i_hi - i_lo) <= a.flat_cap;
+    const bool flat = a.flat_cap && a.mode != 1 && (uint32_t)a.nsrc * (i_hi - i_lo) <= a.flat_cap;
+    // a row-pass item sweeps one piece of one DSSS
+    const int s_lo = a.mode == 1 ? (int)it.pad : 0;
+    const int s_hi = a.mode == 1 ? (int)it.pad + 1 : a.nsrc;
     if (flat) {
       FlatEnt* tab = reinterpret_cast<FlatEnt*>(smem_raw + (size_t)a.tile_max * (PG::compensated ? 8 : 4));
       if (i_hi > i_lo) sweep_flat<PG>(a, it, t, tb, nt, i_lo, i_hi, acc, tab);
     } else
-    for (int s = 0; s < a.nsrc && vo < it.vend; ++s) {
+    for (int s = s_lo; s < s_hi && vo < it.vend; ++s) {
       const uint64_t* po = a.src[s].piece_off;
       for (uint32_t i = i_lo; i < i_hi && vo < it.vend; ++i) {
         const uint64_t pc = piece_index(a.P, tb, nt, i, t);
@@ -461,12 +466,16 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
     }
     // FromHub (Algorithm 6, 7): fold hub entries of pieces (i, t), i in [hub_lo, hub_hi)
     if (a.mode == 0 && it.sub == 0 && a.hub_lo < a.hub_hi) {
-      const V* hv = static_cast<const V*>(a.hubs);
-      for (uint32_t i = a.hub_lo; i < a.hub_hi; ++i) {
-        if (a.act_in && !a.act_in[i]) continue;
-        const uint64_t pc = piece_index(a.P, tb, nt, i, t);
-        const uint64_t h0 = a.hub_off[pc], h1 = a.hub_off[pc + 1];
-        for (uint64_t k = h0 + threadIdx.x; k < h1; k += kThreads) PG::emit(acc, a.hub_dst[k], hv[k]);
+      for (int s = 0; s < a.nsrc; ++s) {
+        const V* hv = static_cast<const V*>(a.hubs[s]);
+        const uint64_t* ho = a.hub_off[s];
+        const uint16_t* hd = a.hub_dst[s];
+        for (uint32_t i = a.hub_lo; i < a.hub_hi; ++i) {
+          if (a.act_in && !a.act_in[i]) continue;
+          const uint64_t pc = piece_index(a.P, tb, nt, i, t);
+          const uint64_t h0 = ho[pc], h1 = ho[pc + 1];
+          for (uint64_t k = h0 + threadIdx.x; k < h1; k += kThreads) PG::emit(acc, hd[k], hv[k]);
+        }
       }
     }
     __syncthreads();
@@ -482,11 +491,13 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
       }
       __threadfence();
       __syncthreads();
-      if (threadIdx.x == 0) s_flag = (atomicAdd(&a.tile_ticket[t], 1u) == it.nsplit - 1);
+      // one completion counter per (tile, DSSS of a row-pass item)
+      const uint32_t tix = t + (a.mode == 1 ? it.pad * a.col_tb[a.P] : 0u);
+      if (threadIdx.x == 0) s_flag = (atomicAdd(&a.tile_ticket[tix], 1u) == it.nsplit - 1);
       __syncthreads();
       if (!s_flag) return;
       __threadfence();
-      if (threadIdx.x == 0) a.tile_ticket[t] = 0;
+      if (threadIdx.x == 0) a.tile_ticket[tix] = 0;
       for (uint32_t k = threadIdx.x; k < T; k += kThreads) {
         if constexpr (PG::compensated) {
           double v = 0.0;  // fixed slot order, double precision
@@ -510,17 +521,20 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
 
   if (a.mode == 1) {  // row pass of one source interval (Algorithm 6 ToHub / 7 lines 9-14)
     const uint32_t i = it.row;
+    const uint32_t sx = it.pad;
     const uint64_t pc = piece_index(a.P, tb, nt, i, t);
-    const uint64_t h0 = a.hub_off[pc], h1 = a.hub_off[pc + 1];
+    const uint64_t* ho = a.hub_off[sx];
+    const uint16_t* hd = a.hub_dst[sx];
+    const uint64_t h0 = ho[pc], h1 = ho[pc + 1];
     if (j < a.q_res) {  // destination resident: update it in place
       V* ar = static_cast<V*>(a.accres);
       for (uint64_t k = h0 + threadIdx.x; k < h1; k += kThreads) {
-        const uint32_t o = a.hub_dst[k];
+        const uint32_t o = hd[k];
         PG::emit_global(ar + ts + o, PG::read(acc, o));
       }
     } else {  // destination on the host side: write the hub
-      V* hv = static_cast<V*>(a.hubs);
-      for (uint64_t k = h0 + threadIdx.x; k < h1; k += kThreads) hv[k] = PG::read(acc, a.hub_dst[k]);
+      V* hv = static_cast<V*>(a.hubs[sx]);
+      for (uint64_t k = h0 + threadIdx.x; k < h1; k += kThreads) hv[k] = PG::read(acc, hd[k]);
     }
     return;
   }

@@ -59,9 +59,10 @@ struct SweepArgs {
   // from accres (no edges).
   int mode = 0;
   uint32_t q_res = 0;
-  const uint64_t* hub_off = nullptr;  // of src[0]
-  const uint16_t* hub_dst = nullptr;
-  void* hubs = nullptr;               // hub values [D]
+  // hubs of each DSSS of the sweep (row-pass items name theirs in Item::pad)
+  const uint64_t* hub_off[2] = {nullptr, nullptr};
+  const uint16_t* hub_dst[2] = {nullptr, nullptr};
+  void* hubs[2] = {nullptr, nullptr};  // hub values [D_s]
   uint32_t hub_lo = 0, hub_hi = 0;
   void* accres = nullptr;             // accumulators of resident columns [n_res]
   // staged (non-resident) intervals: the source interval stage_i is read from

@@ -206,7 +206,7 @@ def test_weighted_pagerank_forward():
 def test_dpu_equals_spu(P):
     n = 1 << 14
     s, d, _ = rmat(14, 16, 5)
-    g = nx.Graph(s, d, n, P)
+    g = nx.Graph(s, d, n, P, transpose=True)
     g.run("bfs", 1000, "spu", root=0)
     b_spu = g.values(dtype=np.uint32)
     st = g.run("bfs", 1000, "dpu", root=0)
@@ -215,6 +215,8 @@ def test_dpu_equals_spu(P):
     assert (b_spu == oracle.bfs(n, s, d, 0)).all()
     g.run("pr", 20, "dpu")
     assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"DPU P={P}")
+    g.run("wcc", 1000, "dpu")  # hubs of the forward and the transpose DSSS
+    assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
 
 
 def test_resume_from_values():
@@ -259,9 +261,10 @@ def test_mpu_every_q(P):
     # Section III-B3: Q = floor(B_M P / (2 n B_a)); Q = P is SPU, Q = 0 is DPU.
     n = 1 << 13
     s, d, _ = rmat(13, 16, 8)
-    g = nx.Graph(s, d, n, P)
+    g = nx.Graph(s, d, n, P, transpose=True)
     ref_pr = oracle.pagerank(n, s, d, 0.85, 20)
     ref_bfs = oracle.bfs(n, s, d, 0)
+    ref_wcc = oracle.wcc(n, s, d)
     L = -(-n // P)
     for Q in range(0, P + 1):
         budget = max(2 * n * 4 * Q // P + 1, 2 * L * 4)
@@ -273,6 +276,8 @@ def test_mpu_every_q(P):
         assert (g.values(dtype=np.uint32) == ref_bfs).all(), (P, Q)
         if want_q < P:
             assert st["h2d_bytes"] > 0 and st["d2h_bytes"] > 0
+        g.run("wcc", 1000, "mpu", budget=budget)
+        assert (g.values(dtype=np.uint32) == ref_wcc).all(), (P, Q)
 
 
 def test_dpu_with_small_budget_stages_intervals():
