@@ -280,6 +280,27 @@ def measure_multi(nx, inputs, torch, count=256, iters=20):
     }
 
 
+def measure_strategies(nx, inputs, torch, scale=22, seed=2, P=16):
+    """PR x20, BFS, WCC on the scale-22 graph under SPU, DPU and MPU (Q = P/2)."""
+    n, m = 1 << scale, 16 << scale
+    src, dst, _ = inputs.rmat_edges_device(scale, m, seed)
+    g = nx.Graph(src, dst, n, P, transpose=True)
+    del src, dst
+    half = 2 * n * 4 // 2 + 1  # budget for half of the ping-pong intervals
+    out = {"workload": f"R-MAT scale {scale} ef 16 seed {seed}, P={P}, with transpose"}
+    for strat, budget in (("spu", 0), ("dpu", 0), ("mpu", half)):
+        for prog, it in (("pr", 20), ("bfs", 1000), ("wcc", 1000)):
+            g.run(prog, it, strat, budget=budget)
+            st = g.run(prog, it, strat, budget=budget)
+            out[f"{strat}_{prog}_ms"] = st["ms"]
+            if strat == "mpu":
+                out["mpu_Q"] = st["Q"]
+    out["dpu_over_spu_pr"] = out["dpu_pr_ms"] / out["spu_pr_ms"]
+    g.free()
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_autotune(nx, inputs, torch, scale=22, seed=2):
     """P autotuned over {8, 16, 32, 64} for PageRank on the scale-22 graph."""
     n, m = 1 << scale, 16 << scale
@@ -303,7 +324,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-PPR, adjoint and multi-graph measurements")
     ap.add_argument("--extras-only", default=None,
-                    choices=["ppr_batch", "adjoint", "multi_graph", "autotune"],
+                    choices=["ppr_batch", "adjoint", "multi_graph", "autotune", "strategies"],
                     help="diagnostic: run one extra measurement and print it (for profiling)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -317,7 +338,8 @@ def main():
     from paper_1510_06916_b300 import nxgraph as nx
 
     extra_fns = {"ppr_batch": measure_ppr_batch, "adjoint": measure_adjoint,
-                 "multi_graph": measure_multi, "autotune": measure_autotune}
+                 "multi_graph": measure_multi, "autotune": measure_autotune,
+                 "strategies": measure_strategies}
     if args.extras_only:
         nx.set_stream(torch.cuda.current_stream())
         out = extra_fns[args.extras_only](nx, inputs, torch)
