@@ -23,7 +23,12 @@
 namespace nx {
 namespace {
 
-constexpr uint32_t kTileMaxCap = 4096;  // float accumulators: 16 KB of shared memory
+#ifndef NX_TILE_CAP
+#define NX_TILE_CAP 2048
+#endif
+// Most vertices in a destination tile: the block's accumulators (hi + lo
+// floats) take 8 B per vertex of shared memory.
+constexpr uint32_t kTileMaxCap = NX_TILE_CAP;
 
 __global__ void k_check_ids(const uint32_t* __restrict__ a, uint64_t m, uint32_t n,
                             uint32_t* __restrict__ bad) {

@@ -680,7 +680,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   // fit in L2 together (the value array of the whole graph may not)
   uint32_t band = P;
   if (strat == NX_SPU && !streaming) {
-    const uint64_t kBandBytes = 48ull << 20;
+    const uint64_t kBandBytes = 128ull << 20;  // about the L2; smaller bands measured slower
     if (p.band_intervals) band = std::min<uint32_t>(p.band_intervals, P);
     else if ((uint64_t)n * 4 > kBandBytes)
       band = (uint32_t)std::max<uint64_t>(1, kBandBytes / ((uint64_t)L * 4));
