@@ -423,10 +423,9 @@ nx_status ppr_batch_impl(nx_graph* g, const float* tele_in, uint32_t B, uint32_t
     else
       NX_CUDA(cudaFuncSetAttribute(k_ppr_batch<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
-  cudaEvent_t e0, e1;
-  NX_CUDA(cudaEventCreate(&e0));
-  NX_CUDA(cudaEventCreate(&e1));
-  NX_CUDA(cudaEventRecord(e0, s));
+  EventPair ev;
+  NX_TRY(ev.create());
+  NX_CUDA(cudaEventRecord(ev.e0, s));
   int cur = 0;
   for (uint32_t itn = 0; itn < iters; ++itn) {
     const bool last = itn + 1 == iters;
@@ -446,12 +445,9 @@ nx_status ppr_batch_impl(nx_graph* g, const float* tele_in, uint32_t B, uint32_t
     NX_LAUNCH_CHECK();
     cur = 1 - cur;
   }
-  NX_CUDA(cudaEventRecord(e1, s));
-  NX_CUDA(cudaEventSynchronize(e1));
+  NX_CUDA(cudaEventRecord(ev.e1, s));
   float ms = 0.f;
-  NX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  NX_TRY(ev.elapsed(&ms));
   // output [n][B]
   if (dev_ptrs) {
     k_ppr_out<<<grid_of((uint64_t)n * B), 256, 0, s>>>(rv.as<float>(), B, BP, n, ranks);

@@ -314,10 +314,9 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   const bool on_dev = flags & NX_DEV_PTRS;
   const bool want_t = flags & NX_WITH_TRANSPOSE;
   const bool want_w = flags & NX_WITH_WEIGHTS;
-  cudaEvent_t e0, e1;
-  NX_CUDA(cudaEventCreate(&e0));
-  NX_CUDA(cudaEventCreate(&e1));
-  NX_CUDA(cudaEventRecord(e0, stream()));
+  EventPair ev;
+  NX_TRY(ev.create());
+  NX_CUDA(cudaEventRecord(ev.e0, stream()));
   // device copies of the inputs
   DevBuf ds, dd, dw;
   const uint32_t *s = src, *d = dst;
@@ -405,11 +404,8 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
       NX_CUDA(cudaMemcpyAsync(g->orig_dst.p, d, m * 4, cudaMemcpyDeviceToDevice, stream()));
     }
   }
-  NX_CUDA(cudaEventRecord(e1, stream()));
-  NX_CUDA(cudaEventSynchronize(e1));
-  NX_CUDA(cudaEventElapsedTime(&g->build_ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  NX_CUDA(cudaEventRecord(ev.e1, stream()));
+  NX_TRY(ev.elapsed(&g->build_ms));
   return NX_OK;
 }
 

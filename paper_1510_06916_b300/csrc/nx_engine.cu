@@ -812,14 +812,13 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       }
   }
 
-  cudaEvent_t e0, e1;
-  NX_CUDA(cudaEventCreate(&e0));
-  NX_CUDA(cudaEventCreate(&e1));
+  EventPair ev;
+  NX_TRY(ev.create());
   Scal sc = scal_of(g);
   uint64_t swept = 0;
   uint32_t done = 0;
   std::vector<uint32_t> act_h(P + 1, 1);
-  NX_CUDA(cudaEventRecord(e0, stream()));
+  NX_CUDA(cudaEventRecord(ev.e0, stream()));
   for (uint32_t it = 0; it < iters; ++it) {
     if (is_min(prog)) {
       NX_CUDA(cudaMemcpyAsync(act_h.data(), g->act[g->cur].p, (size_t)P * 4,
@@ -851,12 +850,9 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       if (cnt == 0) break;
     }
   }
-  NX_CUDA(cudaEventRecord(e1, stream()));
-  NX_CUDA(cudaEventSynchronize(e1));
+  NX_CUDA(cudaEventRecord(ev.e1, stream()));
   float ms = 0.f;
-  NX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  NX_TRY(ev.elapsed(&ms));
   if (staged && S.nh) {  // results of the host-side intervals back into the value arrays
     const int cc = g->cur;
     const bool has_c = (prog == NX_PR || prog == NX_PPR);
@@ -963,10 +959,9 @@ nx_status adjoint_impl(nx_graph* g, const float* grad_r, uint32_t K, float* grad
   a.split = g->split_buf.p;
   a.tele = g->tele.as<float>();
   a.alpha = g->wpr_alpha;
-  cudaEvent_t e0, e1;
-  NX_CUDA(cudaEventCreate(&e0));
-  NX_CUDA(cudaEventCreate(&e1));
-  NX_CUDA(cudaEventRecord(e0, s));
+  EventPair ev;
+  NX_TRY(ev.create());
+  NX_CUDA(cudaEventRecord(ev.e0, s));
   int cur = 0;
   uint32_t launches = 0;
   for (uint32_t k = 1; k < K; ++k) {  // lambda^{k} = M^T lambda^{k-1} + g
@@ -1002,7 +997,7 @@ nx_status adjoint_impl(nx_graph* g, const float* grad_r, uint32_t K, float* grad
     NX_LAUNCH_CHECK();
     ++launches;
   }
-  NX_CUDA(cudaEventRecord(e1, s));
+  NX_CUDA(cudaEventRecord(ev.e1, s));
   if (!dev && m) NX_CUDA(cudaMemcpyAsync(grad_w, dwp, m * 4, cudaMemcpyDeviceToHost, s));
   if (grad_t) {
     DevBuf dt_dev;
@@ -1016,11 +1011,8 @@ nx_status adjoint_impl(nx_graph* g, const float* grad_r, uint32_t K, float* grad
     if (!dev) NX_CUDA(cudaMemcpyAsync(grad_t, dtp, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
     NX_CUDA(cudaStreamSynchronize(s));
   }
-  NX_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;
-  NX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  NX_TRY(ev.elapsed(&ms));
   NX_CUDA(cudaStreamSynchronize(s));
   if (st) {
     memset(st, 0, sizeof *st);
@@ -1134,18 +1126,17 @@ nx_status multi_impl(nx_graph** gs, uint32_t count, nx_program prog, float alpha
   }
   float ms = 0.f;
   if (rc == NX_OK) {
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
-    cudaError_t e = cudaGraphLaunch(exec, s);
-    cudaEventRecord(e1, s);
-    cudaError_t e3 = cudaEventSynchronize(e1);
-    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__);
-    else if (e3 != cudaSuccess) rc = cuda_fail(e3, "multi-graph kernel", __FILE__, __LINE__);
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    EventPair ev;
+    rc = ev.create();
+    if (rc == NX_OK) {
+      cudaEventRecord(ev.e0, s);
+      cudaError_t e = cudaGraphLaunch(exec, s);
+      cudaEventRecord(ev.e1, s);
+      cudaError_t e3 = cudaEventSynchronize(ev.e1);
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__);
+      else if (e3 != cudaSuccess) rc = cuda_fail(e3, "multi-graph kernel", __FILE__, __LINE__);
+      else cudaEventElapsedTime(&ms, ev.e0, ev.e1);
+    }
   }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);

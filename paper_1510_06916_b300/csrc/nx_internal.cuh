@@ -70,6 +70,20 @@ struct PinnedBuf {
   template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Two timing events, destroyed on every exit path.
+struct EventPair {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  EventPair() = default;
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+  ~EventPair() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+  nx_status create();
+  nx_status elapsed(float* ms);  // waits for e1
+};
+
 inline uint32_t bits_for(uint64_t x) {  // bits to hold values in [0, x)
   uint32_t b = 0;
   while (b < 64 && (x - 1) >> b) ++b;

@@ -87,6 +87,17 @@ nx_status PinnedBuf::alloc(size_t n) {
   return NX_OK;
 }
 
+nx_status EventPair::create() {
+  NX_CUDA(cudaEventCreate(&e0));
+  NX_CUDA(cudaEventCreate(&e1));
+  return NX_OK;
+}
+nx_status EventPair::elapsed(float* ms) {
+  NX_CUDA(cudaEventSynchronize(e1));
+  NX_CUDA(cudaEventElapsedTime(ms, e0, e1));
+  return NX_OK;
+}
+
 // ---------------------------------------------------------------- scan
 namespace {
 constexpr int SC_THREADS = 256;
@@ -174,6 +185,7 @@ nx_status exclusive_scan(const T* in, T* out, uint64_t n, T* total) {
   NX_TRY(exclusive_scan<T>(part.as<T>(), part.as<T>(), nb, nullptr));
   scan_tiles<T><<<(unsigned)nb, SC_THREADS, 0, stream()>>>(in, out, n, part.as<T>(), total);
   NX_LAUNCH_CHECK();
+  NX_CUDA(cudaStreamSynchronize(stream()));  // `part` is freed on return
   return NX_OK;
 }
 }  // namespace

@@ -770,8 +770,12 @@ nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaS
   const bool sums = (kind == PK_PR || kind == PK_WPR || kind == PK_PRD || kind == PK_ADJ);
   const size_t smem = (size_t)a.tile_max * (sums ? 8 : 4) + flat_table_bytes(a);
   if (smem > 40 * 1024) {  // dynamic + static shared memory above the 48 KB default
-    static bool raised[8] = {};
-    if (!raised[kind]) {
+    // the opt-in shared-memory limit is a per-device function attribute
+    static bool raised[64][8] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!raised[dev][kind]) {
       cudaError_t e = cudaSuccess;
       switch (kind) {
         case PK_PR: e = cudaFuncSetAttribute(k_sweep<PK_PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
@@ -782,7 +786,7 @@ nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaS
         case PK_ADJ: e = cudaFuncSetAttribute(k_sweep<PK_ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
       }
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
-      raised[kind] = true;
+      raised[dev][kind] = true;
     }
   }
   switch (kind) {
