@@ -296,6 +296,51 @@ def measure_strategies(nx, inputs, torch, scale=22, seed=2, P=16):
             if strat == "mpu":
                 out["mpu_Q"] = st["Q"]
     out["dpu_over_spu_pr"] = out["dpu_pr_ms"] / out["spu_pr_ms"]
+    # Exp 1 / Table IV: the same sub-shards sorted by source, atomic pushes
+    for strat in ("src_coarse", "src_fine"):
+        g.run("pr", 20, strat)
+        st = g.run("pr", 20, strat)
+        out[f"{strat}_pr_ms"] = st["ms"]
+        out[f"{strat}_over_spu_pr"] = st["ms"] / out["spu_pr_ms"]
+    g.free()
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_budget_sweep(nx, inputs, torch, scale=22, seed=2, P=16, iters=10):
+    """Exp 4: PageRank x10 on the scale-22 graph as the device budget shrinks.
+
+    Budgets are fractions of the all-resident footprint F = 2 n B_a + m B_e
+    (above 2 n B_a: SPU with shards streamed from pinned host memory; below:
+    MPU with Q = floor(B_M P / (2 n B_a)) resident intervals). Each point lists
+    the host-link bytes moved per iteration beside the Table II model's.
+    """
+    n, m = 1 << scale, 16 << scale
+    src, dst, _ = inputs.rmat_edges_device(scale, m, seed)
+    g = nx.Graph(src, dst, n, P)
+    del src, dst
+    D = g.info()["D"]
+    vert = 2 * n * 4
+    full = vert + 4 * m
+    points = [("all", 0)]
+    points += [(f"{f:g}F", int(f * full)) for f in (0.75, 0.5, 0.25)]
+    points += [("2nBa", vert + 1)]
+    points += [(f"Q={q}", q * vert // P + 1) for q in (P * 3 // 4, P // 2, P // 4, 1)]
+    out = {"workload": f"R-MAT scale {scale} ef 16 seed {seed}, P={P}, PageRank x{iters}",
+           "F_bytes": full, "points": []}
+    for label, budget in points:
+        g.run("pr", iters, "auto", budget=budget)
+        st = g.run("pr", iters, "auto", budget=budget)
+        strat = ["spu", "dpu", "mpu"][st["strategy"]]
+        Q, rd, wr = nx.io_model(strat, n, m, P, budget if budget else full, d=m / max(D, 1))
+        # Table II counts the edges read from disk every iteration; below 2 n B_a
+        # they stay in device memory here, so only the interval/hub part moves
+        model_link = rd + wr - (4 * m if strat != "spu" else 0)
+        out["points"].append({
+            "budget": label, "bytes": budget, "strategy": strat.upper(),
+            "Q": st["Q"], "streamed_cols": st["streamed_cols"], "ms_per_iter": st["ms"] / iters,
+            "link_bytes_per_iter": (st["h2d_bytes"] + st["d2h_bytes"]) / iters,
+            "model_bytes_per_iter": rd + wr, "model_link_bytes_per_iter": model_link, "model_Q": Q})
     g.free()
     torch.cuda.empty_cache()
     return out
@@ -324,7 +369,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-PPR, adjoint and multi-graph measurements")
     ap.add_argument("--extras-only", default=None,
-                    choices=["ppr_batch", "adjoint", "multi_graph", "autotune", "strategies"],
+                    choices=["ppr_batch", "adjoint", "multi_graph", "autotune", "strategies",
+                             "budget_sweep"],
                     help="diagnostic: run one extra measurement and print it (for profiling)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -339,7 +385,7 @@ def main():
 
     extra_fns = {"ppr_batch": measure_ppr_batch, "adjoint": measure_adjoint,
                  "multi_graph": measure_multi, "autotune": measure_autotune,
-                 "strategies": measure_strategies}
+                 "strategies": measure_strategies, "budget_sweep": measure_budget_sweep}
     if args.extras_only:
         nx.set_stream(torch.cuda.current_stream())
         out = extra_fns[args.extras_only](nx, inputs, torch)

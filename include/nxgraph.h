@@ -60,7 +60,12 @@ typedef enum {
                   combines them per destination interval                           */
   NX_MPU = 2,  /* Algorithm 7: Q intervals resident from the budget; the (P-Q)^2
                   sub-shards among the others go through hubs                      */
-  NX_AUTO = 3  /* SPU when the budget holds all intervals, else MPU               */
+  NX_AUTO = 3, /* SPU when the budget holds all intervals, else MPU              */
+  /* Exp 1 / Table IV ablation (PR and PPR only; needs NX_WITH_TRANSPOSE; budget
+     0): the same sub-shards read in source order from the transpose DSSS, each
+     edge pushing its contribution to the destination with an atomic add.      */
+  NX_SRC_COARSE = 4, /* one thread block per sub-shard (coarse-grained model)  */
+  NX_SRC_FINE = 5    /* edge-balanced chunks of the source-sorted order         */
 } nx_strategy;
 
 /* nx_build_dsss flags. */
@@ -159,9 +164,9 @@ nx_status nx_dsss_export(const nx_graph* g, int32_t transpose, uint32_t* src, ui
  * The run starts from the program's Initialize (Algorithm 2 for BFS) unless
  * nx_set_values was called since the last run of the same program, in which
  * case it continues from those values.
- * Errors: INVALID_ARG (program needs a structure the graph lacks, root >= n),
- * BUDGET_TOO_SMALL (SPU without room for 2 n B_a; MPU/DPU below one interval
- * pair), OOM, CUDA.
+ * Errors: INVALID_ARG (program needs a structure the graph lacks, root >= n,
+ * an NX_SRC_* strategy with another program or a budget), BUDGET_TOO_SMALL
+ * (SPU without room for 2 n B_a; MPU/DPU below one interval pair), OOM, CUDA.
  */
 nx_status nx_run(nx_graph* g, nx_program program, const nx_params* params, uint32_t iters,
                  nx_strategy strategy, uint64_t mem_budget_bytes, nx_run_stats* stats);

@@ -593,6 +593,12 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     return invalid("nx_run: WCC needs the transpose DSSS (build with NX_WITH_TRANSPOSE)");
   if (prog == NX_WPR && !g->has_w) return invalid("nx_run: WPR needs NX_WITH_WEIGHTS");
   if (prog == NX_BFS && p.root >= n) return invalid("nx_run: BFS root >= n");
+  const bool push = (strategy == NX_SRC_COARSE || strategy == NX_SRC_FINE);
+  if (push && prog != NX_PR && prog != NX_PPR)
+    return invalid("nx_run: the source-sorted ablation runs PR and PPR only");
+  if (push && !g->has_tr)
+    return invalid("nx_run: the source-sorted ablation reads the transpose DSSS (NX_WITH_TRANSPOSE)");
+  if (push && budget) return invalid("nx_run: the source-sorted ablation takes no budget");
   // strategy from the budget (Section III-B3: Q <= B_M P / (2 n B_a))
   const double Ba = 4.0;
   uint32_t Qb = P;
@@ -645,6 +651,29 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   g->values_set_for = -1;
   g->last_prog = (int)prog;
   if (prog == NX_WPR) g->wpr_alpha = p.alpha;
+  if (push) {
+    PushRun r;
+    r.coarse = (strategy == NX_SRC_COARSE);
+    r.iters = iters;
+    r.alpha = p.alpha;
+    r.tele = tele;
+    r.dang_by_tele = (prog == NX_PPR) ? 1 : 0;
+    r.dm = scal_of(g).dm;
+    uint32_t launches = 0;
+    float ms = 0.f;
+    NX_TRY(push_run(g, r, &launches, &ms));
+    if (st) {
+      memset(st, 0, sizeof *st);
+      st->iters_done = iters;
+      st->Q = P;
+      st->strategy = (uint32_t)strategy;
+      st->ms = ms;
+      st->edges_swept = g->m * iters;
+      st->bytes_model = bytes_per_sweep(g, prog, g->m) * iters;
+      st->launches = launches;
+    }
+    return NX_OK;
+  }
 
   RunCtx c;
   c.g = g;
@@ -1190,7 +1219,7 @@ extern "C" nx_status nx_run(nx_graph* g, nx_program program, const nx_params* pa
                             nx_run_stats* stats) {
   if (!g) return nx::invalid("nx_run: graph is NULL");
   if ((int)program < 0 || (int)program > 4) return nx::invalid("nx_run: unknown program");
-  if ((int)strategy < 0 || (int)strategy > 3) return nx::invalid("nx_run: unknown strategy");
+  if ((int)strategy < 0 || (int)strategy > 5) return nx::invalid("nx_run: unknown strategy");
   nx_params p{};
   p.alpha = 0.85f;
   if (params) p = *params;

@@ -200,3 +200,18 @@ struct nx_graph {
   uint32_t gexec_iters = 0;
   uint64_t device_bytes() const;
 };
+
+namespace nx {
+// Table IV ablation run (nx_push.cu): source-sorted sub-shards with atomic
+// pushes; values start from g->val/aux[g->cur] and dm[g->cur].
+struct PushRun {
+  bool coarse;         // one block per sub-shard (else edge-balanced chunks)
+  uint32_t iters;
+  float alpha;
+  const float* tele;   // nullable: uniform 1/n
+  int dang_by_tele;    // PPR: dangling mass spread by the teleport
+  double* dm;          // [2] dangling mass ping-pong
+};
+nx_status push_run(nx_graph* g, const PushRun& r, uint32_t* launches, float* ms);
+}  // namespace nx
+

@@ -17,12 +17,13 @@ LIB_PATH = os.path.join(_HERE, "csrc", "libnxgraph.so")
 
 NX_OK, NX_ERR_INVALID_ARG, NX_ERR_OOM, NX_ERR_BUDGET_TOO_SMALL, NX_ERR_CUDA, NX_ERR_TIMEOUT = range(6)
 PR, PPR, WPR, BFS, WCC = range(5)
-SPU, DPU, MPU, AUTO = range(4)
+SPU, DPU, MPU, AUTO, SRC_COARSE, SRC_FINE = range(6)
 HOST_PTRS, DEV_PTRS, WITH_TRANSPOSE, WITH_WEIGHTS = 0, 1, 2, 4
 INF = 0xFFFFFFFF
 
 PROGRAMS = {"pr": PR, "ppr": PPR, "wpr": WPR, "bfs": BFS, "wcc": WCC}
-STRATEGIES = {"spu": SPU, "dpu": DPU, "mpu": MPU, "auto": AUTO}
+STRATEGIES = {"spu": SPU, "dpu": DPU, "mpu": MPU, "auto": AUTO,
+              "src_coarse": SRC_COARSE, "src_fine": SRC_FINE}
 
 EXPORTS = [
     "nx_set_stream", "nx_last_error", "nx_build_dsss", "nx_graph_get_info", "nx_run",

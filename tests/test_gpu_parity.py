@@ -448,3 +448,59 @@ def test_autotune_picks_a_candidate_and_caches(tmp_path):
     assert P == (2, 4, 8)[int(np.argmin(ms))]
     P2, ms2 = nx.autotune(s, d, n, candidates=(2, 4, 8), iters=5, cache=cache)
     assert P2 == P and all(x == -1 for x in ms2)  # served from the cache file
+
+
+# ------------------------------------------------- Table IV ablation (Exp 1)
+
+@pytest.mark.parametrize("strategy", ["src_coarse", "src_fine"])
+@pytest.mark.parametrize("P", [1, 3, 16])
+def test_source_sorted_push_matches_oracle(strategy, P):
+    # the source-sorted, atomic-push sweep computes the same PageRank (ragged n)
+    n = 5000
+    s, d, _ = inputs.rmat_edges(13, 60000, 17)
+    keep = (s < n) & (d < n)
+    s, d = s[keep], d[keep]
+    g = nx.Graph(s, d, n, P, transpose=True)
+    st = g.run("pr", 20, strategy)
+    assert st["iters_done"] == 20 and st["launches"] >= 40
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"{strategy} P={P}")
+
+
+@pytest.mark.parametrize("strategy", ["src_coarse", "src_fine"])
+def test_source_sorted_push_hub_and_ppr(strategy):
+    k = 300_000  # in-star: 300k atomic adds into one destination
+    n = k + 1
+    s = np.concatenate([np.arange(1, n, dtype=np.uint32), np.array([0, 5], np.uint32)])
+    d = np.concatenate([np.zeros(k, np.uint32), np.array([7, 0], np.uint32)])
+    g = nx.Graph(s, d, n, 4, transpose=True)
+    g.run("pr", 20, strategy)
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"{strategy} hub")
+    n2 = 1 << 14
+    s2, d2, _ = rmat(14, 16, 3)
+    t = inputs.ppr_teleports(n2, 1, 33)[:, 0].copy()
+    g2 = nx.Graph(s2, d2, n2, 8, transpose=True)
+    g2.run("ppr", 30, strategy, teleport=t)
+    ref = oracle.personalized_pagerank(n2, s2, d2, t, 0.85, 30)
+    assert_pr_close(g2.values(), ref, f"{strategy} PPR")
+    # then the DSSS sweep continues from the pushed values (same state layout)
+    g2.set_values("ppr", g2.values())
+    g2.run("ppr", 5, "spu", teleport=t)
+    ref35 = oracle.personalized_pagerank(n2, s2, d2, t, 0.85, 35)
+    assert_pr_close(g2.values(), ref35, f"{strategy} then SPU")
+
+
+def test_source_sorted_push_rejects():
+    n = 64
+    s = np.arange(n, dtype=np.uint32)
+    d = ((np.arange(n) + 1) % n).astype(np.uint32)
+    g = nx.Graph(s, d, n, 2)
+    with pytest.raises(nx.NxError):  # no transpose DSSS
+        g.run("pr", 2, "src_fine")
+    gt = nx.Graph(s, d, n, 2, transpose=True)
+    for prog in ("bfs", "wcc"):
+        with pytest.raises(nx.NxError):
+            gt.run(prog, 2, "src_coarse")
+    with pytest.raises(nx.NxError):
+        gt.run("pr", 2, "src_coarse", budget=1 << 20)
+    gt.run("pr", 2, "src_coarse")
+    assert np.allclose(gt.values(), 1.0 / n, rtol=1e-6)
