@@ -346,6 +346,24 @@ def measure_budget_sweep(nx, inputs, torch, scale=22, seed=2, P=16, iters=10):
     return out
 
 
+def measure_relabel(nx, inputs, torch, scale=22, seed=2, P=16, iters=20):
+    """Degree-ordered ids (NX_RELABEL) vs the generator's ids: PageRank x20 under SPU."""
+    n, m = 1 << scale, 16 << scale
+    src, dst, _ = inputs.rmat_edges_device(scale, m, seed)
+    out = {"workload": f"R-MAT scale {scale} ef 16 seed {seed}, P={P}, PageRank x{iters}"}
+    for name, rl in (("ids", False), ("relabel", True)):
+        g = nx.Graph(src, dst, n, P, relabel=rl)
+        g.run("pr", iters)
+        st = g.run("pr", iters)
+        out[f"{name}_ms_per_iter"] = st["ms"] / iters
+        out[f"{name}_build_ms"] = g.info()["build_ms"]
+        g.free()
+    out["relabel_over_ids"] = out["relabel_ms_per_iter"] / out["ids_ms_per_iter"]
+    del src, dst
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_autotune(nx, inputs, torch, scale=22, seed=2):
     """P autotuned over {8, 16, 32, 64} for PageRank on the scale-22 graph."""
     n, m = 1 << scale, 16 << scale
@@ -370,7 +388,7 @@ def main():
                     help="skip the batched-PPR, adjoint and multi-graph measurements")
     ap.add_argument("--extras-only", default=None,
                     choices=["ppr_batch", "adjoint", "multi_graph", "autotune", "strategies",
-                             "budget_sweep"],
+                             "budget_sweep", "relabel"],
                     help="diagnostic: run one extra measurement and print it (for profiling)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -385,7 +403,8 @@ def main():
 
     extra_fns = {"ppr_batch": measure_ppr_batch, "adjoint": measure_adjoint,
                  "multi_graph": measure_multi, "autotune": measure_autotune,
-                 "strategies": measure_strategies, "budget_sweep": measure_budget_sweep}
+                 "strategies": measure_strategies, "budget_sweep": measure_budget_sweep,
+                 "relabel": measure_relabel}
     if args.extras_only:
         nx.set_stream(torch.cuda.current_stream())
         out = extra_fns[args.extras_only](nx, inputs, torch)

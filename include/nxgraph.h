@@ -73,6 +73,8 @@ typedef enum {
 #define NX_DEV_PTRS 1u           /* src/dst/w are device pointers                   */
 #define NX_WITH_TRANSPOSE 2u     /* also build the source-sorted (transpose) DSSS  */
 #define NX_WITH_WEIGHTS 4u       /* w (float, > 0) is given: weighted PageRank     */
+#define NX_RELABEL 8u            /* degree-ordered internal ids (Section III-A
+                                    "degreeing"): see nx_get_relabel              */
 
 typedef struct nx_graph nx_graph; /* opaque; owns all its device and pinned memory */
 
@@ -131,6 +133,15 @@ void nx_last_error(char* buf, size_t len);
  *   w        : edge weights [m] (> 0) when NX_WITH_WEIGHTS, else ignored
  *   out      : receives the new graph (caller frees with nx_graph_free)
  * Input arrays are copied; the caller keeps ownership.
+ * NX_RELABEL renames the vertices before sharding: internal id k is the
+ * caller vertex with the k-th largest out-degree (ties by caller id), so
+ * heavily read source values cluster. No vertex is dropped and n is kept.
+ * Every vertex-indexed argument and result of nx_run, nx_get_values,
+ * nx_set_values, nx_run_ppr_batch and nx_adjoint_wpr stays in caller ids
+ * (BFS root, teleports, ranks, depths, WCC labels = smallest caller id of the
+ * component, gradients; edge gradients stay in caller edge order). Only
+ * nx_dsss_export reports internal ids. nx_run_multi and
+ * nx_pagerank_step_noalloc reject relabeled graphs.
  * Errors: INVALID_ARG (an id >= n, P out of range, m >= 2^32, n > 2^30,
  * missing w), OOM, CUDA.
  */
@@ -140,12 +151,22 @@ nx_status nx_build_dsss(const uint32_t* src, const uint32_t* dst, uint64_t m, ui
 nx_status nx_graph_get_info(const nx_graph* g, nx_graph_info* info);
 
 /*
+ * The vertex order of a graph built with NX_RELABEL: old_of_new[k] is the
+ * caller id of internal vertex k (a permutation of [0, n)).
+ *   old_of_new : [count] uint32, device if out_is_device else host
+ * Errors: INVALID_ARG (NULL, count != n, graph built without NX_RELABEL), CUDA.
+ */
+nx_status nx_get_relabel(const nx_graph* g, uint32_t* old_of_new, uint64_t count,
+                         int32_t out_is_device);
+
+/*
  * Exports a DSSS in its storage order (Section II-A): edge k of the output is
  * the k-th stored edge, sub-shard by sub-shard (shard j = destination
  * interval outer, source interval i inner), each sorted by destination then
  * source. sub_off[j*P + i] is where SS_ij starts (P*P + 1 entries).
  *   transpose : 0 = forward DSSS, 1 = the transpose DSSS (its "destination"
  *               is the original source; the output gives original src/dst)
+ * Ids are the internal ones (after NX_RELABEL, map them with nx_get_relabel).
  *   src, dst  : host uint32 [m]; sub_off: host uint64 [P*P + 1] (nullable)
  * Errors: INVALID_ARG (transpose not built), CUDA.
  */
@@ -218,7 +239,8 @@ nx_status nx_adjoint_wpr(nx_graph* g, const float* grad_r, uint32_t adj_terms, f
  * Runs `program` on `count` independent graphs in one persistent kernel per
  * call, the whole iteration loop captured in a CUDA graph. Each graph keeps
  * its own values (read them with nx_get_values). BFS uses root 0.
- * Errors: INVALID_ARG (WCC on a graph without transpose, ...), TIMEOUT (a
+ * Errors: INVALID_ARG (WCC on a graph without transpose, a graph built with
+ * NX_RELABEL, ...), TIMEOUT (a
  * bounded grid barrier gave up; the values are then undefined), OOM, CUDA.
  */
 nx_status nx_run_multi(nx_graph** graphs, uint32_t count, nx_program program, float alpha,
@@ -249,7 +271,7 @@ void nx_graph_free(nx_graph* g);
  * it and must be serialised by the caller. Runs on the stream of
  * nx_set_stream and returns when the step is complete.
  * Errors: INVALID_ARG (NULL pointers, r_in == r_out, alpha outside [0, 1),
- * too many tiles), CUDA.
+ * too many tiles, a graph built with NX_RELABEL), CUDA.
  */
 nx_status nx_pagerank_step_noalloc(const nx_graph* g, float alpha, const float* r_in,
                                    float* r_out);

@@ -246,10 +246,12 @@ __global__ void k_subtile_cost(const uint32_t* __restrict__ ew, const uint64_t* 
   }
 }
 
-// Nonzero teleport entries (vertex, column, value), appended in any order.
+// Nonzero teleport entries (vertex, column, value), appended in any order;
+// rows are in caller order, vertices stored as internal ids (map nullable).
 __global__ void k_seed_list(const float* __restrict__ t_in, uint32_t B, uint32_t n,
-                            uint32_t* __restrict__ cnt, uint32_t cap, uint32_t* __restrict__ sv,
-                            uint32_t* __restrict__ sb, float* __restrict__ st) {
+                            const uint32_t* __restrict__ map, uint32_t* __restrict__ cnt,
+                            uint32_t cap, uint32_t* __restrict__ sv, uint32_t* __restrict__ sb,
+                            float* __restrict__ st) {
   const uint64_t total = (uint64_t)n * B;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
@@ -257,7 +259,8 @@ __global__ void k_seed_list(const float* __restrict__ t_in, uint32_t B, uint32_t
     if (tv != 0.f) {
       const uint32_t k = atomicAdd(cnt, 1u);
       if (k < cap) {
-        sv[k] = (uint32_t)(x / B);
+        const uint32_t v = (uint32_t)(x / B);
+        sv[k] = map ? map[v] : v;
         sb[k] = (uint32_t)(x % B);
         st[k] = tv;
       }
@@ -286,12 +289,15 @@ __global__ void k_seed_apply(uint32_t nnz, const uint32_t* __restrict__ sv,
   }
 }
 
+// [n][B] output rows in caller order (map: caller -> internal id, nullable).
 __global__ void k_ppr_out(const float* __restrict__ r, uint32_t B, uint32_t BP, uint32_t n,
-                          float* __restrict__ out) {
+                          const uint32_t* __restrict__ map, float* __restrict__ out) {
   const uint64_t total = (uint64_t)n * B;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride)
-    out[x] = r[(x / B) * BP + (x % B)];
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
+    const uint32_t v = (uint32_t)(x / B);
+    out[x] = r[(size_t)(map ? map[v] : v) * BP + (x % B)];
+  }
 }
 
 unsigned grid_of(uint64_t work) {
@@ -379,8 +385,9 @@ nx_status ppr_batch_impl(nx_graph* g, const float* tele_in, uint32_t B, uint32_t
   }
   NX_TRY(cnt.alloc(4));
   NX_CUDA(cudaMemsetAsync(cnt.p, 0, 4, s));
-  k_seed_list<<<grid_of((uint64_t)n * B), 256, 0, s>>>(t_dev, B, n, cnt.as<uint32_t>(), 0, nullptr,
-                                                       nullptr, nullptr);
+  const uint32_t* map = g->relabeled ? g->new_of_old.as<uint32_t>() : nullptr;
+  k_seed_list<<<grid_of((uint64_t)n * B), 256, 0, s>>>(t_dev, B, n, map, cnt.as<uint32_t>(), 0,
+                                                       nullptr, nullptr, nullptr);
   NX_LAUNCH_CHECK();
   uint32_t nnz = 0;
   NX_CUDA(cudaMemcpyAsync(&nnz, cnt.p, 4, cudaMemcpyDeviceToHost, s));
@@ -389,7 +396,7 @@ nx_status ppr_batch_impl(nx_graph* g, const float* tele_in, uint32_t B, uint32_t
   NX_TRY(sb.alloc(std::max<size_t>(nnz, 1) * 4));
   NX_TRY(sval.alloc(std::max<size_t>(nnz, 1) * 4));
   NX_CUDA(cudaMemsetAsync(cnt.p, 0, 4, s));
-  k_seed_list<<<grid_of((uint64_t)n * B), 256, 0, s>>>(t_dev, B, n, cnt.as<uint32_t>(), nnz,
+  k_seed_list<<<grid_of((uint64_t)n * B), 256, 0, s>>>(t_dev, B, n, map, cnt.as<uint32_t>(), nnz,
                                                        sv.as<uint32_t>(), sb.as<uint32_t>(),
                                                        sval.as<float>());
   NX_LAUNCH_CHECK();
@@ -450,12 +457,13 @@ nx_status ppr_batch_impl(nx_graph* g, const float* tele_in, uint32_t B, uint32_t
   NX_TRY(ev.elapsed(&ms));
   // output [n][B]
   if (dev_ptrs) {
-    k_ppr_out<<<grid_of((uint64_t)n * B), 256, 0, s>>>(rv.as<float>(), B, BP, n, ranks);
+    k_ppr_out<<<grid_of((uint64_t)n * B), 256, 0, s>>>(rv.as<float>(), B, BP, n, map, ranks);
     NX_LAUNCH_CHECK();
   } else {
     DevBuf o;
     NX_TRY(o.alloc((size_t)n * B * 4));
-    k_ppr_out<<<grid_of((uint64_t)n * B), 256, 0, s>>>(rv.as<float>(), B, BP, n, o.as<float>());
+    k_ppr_out<<<grid_of((uint64_t)n * B), 256, 0, s>>>(rv.as<float>(), B, BP, n, map,
+                                                       o.as<float>());
     NX_LAUNCH_CHECK();
     NX_CUDA(cudaMemcpyAsync(ranks, o.p, (size_t)n * B * 4, cudaMemcpyDeviceToHost, s));
   }

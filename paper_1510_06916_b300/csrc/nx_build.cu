@@ -353,6 +353,20 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   g->m = m;
   Geometry& geo = g->geo;
   geo.n = n;
+  DevBuf rs, rd;
+  if (flags & NX_RELABEL) {  // degree-ordered ids; host inputs are renamed in their device copies
+    uint32_t* so = ds.as<uint32_t>();
+    uint32_t* dout = dd.as<uint32_t>();
+    if (on_dev) {
+      NX_TRY(rs.alloc(std::max<uint64_t>(m, 1) * 4));
+      NX_TRY(rd.alloc(std::max<uint64_t>(m, 1) * 4));
+      so = rs.as<uint32_t>();
+      dout = rd.as<uint32_t>();
+    }
+    NX_TRY(relabel_edges(g, s, d, m, so, dout));
+    s = so;
+    d = dout;
+  }
   geo.P = P;
   geo.L = (uint32_t)ceil_div(n, P);
   geo.lb = bits_for(geo.L);

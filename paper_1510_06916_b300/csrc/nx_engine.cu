@@ -52,10 +52,12 @@ __global__ void k_sum_parts(const double* __restrict__ part, uint32_t k, double*
   if (threadIdx.x == 0) *out = red[0];
 }
 
-__global__ void k_init_min(uint32_t n, int bfs, uint32_t root, uint32_t* __restrict__ v) {
+// WCC labels start as the caller's ids (ids: internal -> caller, nullable).
+__global__ void k_init_min(uint32_t n, int bfs, uint32_t root, const uint32_t* __restrict__ ids,
+                           uint32_t* __restrict__ v) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
-    v[x] = bfs ? (x == root ? 0u : kInf) : (uint32_t)x;
+    v[x] = bfs ? (x == root ? 0u : kInf) : (ids ? ids[x] : (uint32_t)x);
 }
 
 unsigned grid_for(uint64_t work) {
@@ -244,8 +246,9 @@ nx_status initialize(nx_graph* g, nx_program prog, const nx_params& p, const flo
                               stream()));
       std::fill(a0.begin(), a0.begin() + P, 1u);
     } else {
-      k_init_min<<<grid_for(n), 256, 0, stream()>>>(n, prog == NX_BFS, p.root,
-                                                     g->val[0].as<uint32_t>());
+      k_init_min<<<grid_for(n), 256, 0, stream()>>>(
+          n, prog == NX_BFS, p.root, g->relabeled ? g->old_of_new.as<uint32_t>() : nullptr,
+          g->val[0].as<uint32_t>());
       NX_LAUNCH_CHECK();
       if (prog == NX_BFS) a0[p.root / g->geo.L] = 1u;
       else std::fill(a0.begin(), a0.begin() + P, 1u);
@@ -621,12 +624,25 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   // teleport
   const float* tele = nullptr;
   if ((prog == NX_PPR || prog == NX_WPR) && p.teleport) {
-    if (p.teleport_is_device) {
+    if (p.teleport_is_device && !g->relabeled) {
       tele = p.teleport;
     } else {
       NX_TRY(ensure(g->tele, (size_t)n * 4));
-      NX_CUDA(cudaMemcpyAsync(g->tele.p, p.teleport, (size_t)n * 4, cudaMemcpyHostToDevice,
-                              stream()));
+      if (g->relabeled) {  // caller order -> internal order
+        DevBuf tmp;
+        const void* in = p.teleport;
+        if (!p.teleport_is_device) {
+          NX_TRY(tmp.alloc((size_t)n * 4));
+          NX_CUDA(cudaMemcpyAsync(tmp.p, p.teleport, (size_t)n * 4, cudaMemcpyHostToDevice,
+                                  stream()));
+          in = tmp.p;
+        }
+        NX_TRY(vertex_to_internal(g, in, g->tele.p));
+        NX_CUDA(cudaStreamSynchronize(stream()));  // tmp is freed on leaving
+      } else {
+        NX_CUDA(cudaMemcpyAsync(g->tele.p, p.teleport, (size_t)n * 4, cudaMemcpyHostToDevice,
+                                stream()));
+      }
       tele = g->tele.as<float>();
     }
   }
@@ -956,8 +972,14 @@ nx_status adjoint_impl(nx_graph* g, const float* grad_r, uint32_t K, float* grad
   for (int k = 0; k < 2; ++k) NX_TRY(ensure(g->lam[k], (size_t)n * 4));
   NX_TRY(ensure(g->ybuf, (size_t)n * 4));
   NX_TRY(ensure(g->tele, (size_t)n * 4));  // holds g = dL/dr
-  NX_CUDA(cudaMemcpyAsync(g->tele.p, grad_r, (size_t)n * 4,
-                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (g->relabeled) {  // caller order -> internal order
+    NX_CUDA(cudaMemcpyAsync(g->lam[1].p, grad_r, (size_t)n * 4,
+                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    NX_TRY(vertex_to_internal(g, g->lam[1].p, g->tele.p));
+  } else {
+    NX_CUDA(cudaMemcpyAsync(g->tele.p, grad_r, (size_t)n * 4,
+                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  }
   NX_CUDA(cudaMemcpyAsync(g->lam[0].p, g->tele.p, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
   // S0 = sum of lambda^0
   Scal sc = scal_of(g);
@@ -1035,8 +1057,15 @@ nx_status adjoint_impl(nx_graph* g, const float* grad_r, uint32_t K, float* grad
       NX_TRY(dt_dev.alloc((size_t)n * 4));
       dtp = dt_dev.as<float>();
     }
-    k_scale<<<grid_for(n), 256, 0, s>>>(g->lam[cur].as<float>(), n, 1.0f - g->wpr_alpha, dtp);
-    NX_LAUNCH_CHECK();
+    if (g->relabeled) {  // internal order -> caller order (lam[1-cur] is free now)
+      k_scale<<<grid_for(n), 256, 0, s>>>(g->lam[cur].as<float>(), n, 1.0f - g->wpr_alpha,
+                                          g->lam[1 - cur].as<float>());
+      NX_LAUNCH_CHECK();
+      NX_TRY(vertex_to_caller(g, g->lam[1 - cur].p, dtp));
+    } else {
+      k_scale<<<grid_for(n), 256, 0, s>>>(g->lam[cur].as<float>(), n, 1.0f - g->wpr_alpha, dtp);
+      NX_LAUNCH_CHECK();
+    }
     if (!dev) NX_CUDA(cudaMemcpyAsync(grad_t, dtp, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
     NX_CUDA(cudaStreamSynchronize(s));
   }
@@ -1224,6 +1253,11 @@ extern "C" nx_status nx_run(nx_graph* g, nx_program program, const nx_params* pa
   p.alpha = 0.85f;
   if (params) p = *params;
   if (!(p.alpha >= 0.f && p.alpha < 1.f)) return nx::invalid("nx_run: alpha must be in [0, 1)");
+  if (program == NX_BFS && g->relabeled && p.root < g->geo.n) {  // caller id -> internal id
+    NX_CUDA(cudaMemcpyAsync(&p.root, g->new_of_old.as<uint32_t>() + p.root, 4,
+                            cudaMemcpyDeviceToHost, nx::stream()));
+    NX_CUDA(cudaStreamSynchronize(nx::stream()));
+  }
   return nx::run_impl(g, program, p, iters, strategy, mem_budget_bytes, stats);
 }
 
@@ -1252,6 +1286,7 @@ extern "C" nx_status nx_run_multi(nx_graph** graphs, uint32_t count, nx_program 
       if (graphs[r] == g) return nx::invalid("nx_run_multi: a graph appears twice");
     if (program == NX_WCC && !g->has_tr) return nx::invalid("nx_run_multi: WCC needs the transpose");
     if (program == NX_WPR && !g->has_w) return nx::invalid("nx_run_multi: WPR needs weights");
+    if (g->relabeled) return nx::invalid("nx_run_multi: a graph was built with NX_RELABEL");
   }
   return nx::multi_impl(graphs, count, program, alpha, iters, stats);
 }
@@ -1261,6 +1296,19 @@ extern "C" nx_status nx_get_values(const nx_graph* g, void* out, uint64_t count,
   if (!g || !out) return nx::invalid("nx_get_values: NULL argument");
   if (count != g->geo.n) return nx::invalid("nx_get_values: count must equal n");
   if (g->last_prog < 0 && g->values_set_for < 0) return nx::invalid("nx_get_values: nothing run yet");
+  if (g->relabeled) {  // internal order -> caller order
+    nx::DevBuf tmp;
+    void* dst = out;
+    if (!out_is_device) {
+      NX_TRY(tmp.alloc(count * 4));
+      dst = tmp.p;
+    }
+    NX_TRY(nx::vertex_to_caller(g, g->val[g->cur].p, dst));
+    if (!out_is_device)
+      NX_CUDA(cudaMemcpyAsync(out, tmp.p, count * 4, cudaMemcpyDeviceToHost, nx::stream()));
+    NX_CUDA(cudaStreamSynchronize(nx::stream()));
+    return NX_OK;
+  }
   NX_CUDA(cudaMemcpyAsync(out, g->val[g->cur].p, count * 4,
                           out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                           nx::stream()));
@@ -1274,9 +1322,20 @@ extern "C" nx_status nx_set_values(nx_graph* g, nx_program program, const void* 
   if (count != g->geo.n) return nx::invalid("nx_set_values: count must equal n");
   if ((int)program < 0 || (int)program > 4) return nx::invalid("nx_set_values: unknown program");
   NX_TRY(nx::prepare(g));
-  NX_CUDA(cudaMemcpyAsync(g->val[g->cur].p, in, count * 4,
-                          in_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                          nx::stream()));
+  if (g->relabeled) {  // caller order -> internal order
+    nx::DevBuf tmp;
+    const void* src = in;
+    if (!in_is_device) {
+      NX_TRY(tmp.alloc(count * 4));
+      NX_CUDA(cudaMemcpyAsync(tmp.p, in, count * 4, cudaMemcpyHostToDevice, nx::stream()));
+      src = tmp.p;
+    }
+    NX_TRY(nx::vertex_to_internal(g, src, g->val[g->cur].p));
+  } else {
+    NX_CUDA(cudaMemcpyAsync(g->val[g->cur].p, in, count * 4,
+                            in_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            nx::stream()));
+  }
   NX_CUDA(cudaStreamSynchronize(nx::stream()));
   g->values_set_for = (int)program;
   g->last_prog = (int)program;

@@ -163,6 +163,10 @@ struct nx_graph {
   nx::DevBuf outdeg;   // uint32 [n]
   nx::DevBuf wsum;     // float [n]  W_u (weighted)
   nx::DevBuf orig_src, orig_dst;  // uint32 [m] caller order (weighted: edge grads)
+  // Degree-ordered ids (NX_RELABEL): internal id k holds caller vertex
+  // old_of_new[k]; every vertex-indexed input and output is mapped at the ABI.
+  bool relabeled = false;
+  nx::DevBuf old_of_new, new_of_old;  // uint32 [n]
   float build_ms = 0.f;
   // values
   int last_prog = -1;
@@ -213,5 +217,17 @@ struct PushRun {
   double* dm;          // [2] dangling mass ping-pong
 };
 nx_status push_run(nx_graph* g, const PushRun& r, uint32_t* launches, float* ms);
+
+// Relabel (nx_relabel.cu). relabel_edges computes the vertex order (out-degree
+// descending, ties by caller id) into g and writes the renamed endpoints
+// (s_out / d_out may alias s / d). gather_u32: out[k] = in[idx[k]] for k < n.
+nx_status relabel_edges(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64_t m,
+                        uint32_t* s_out, uint32_t* d_out);
+nx_status gather_u32(const uint32_t* idx, const void* in, void* out, uint64_t n);
+// Vertex arrays across the ABI: caller order -> internal order (to_internal)
+// or back; a plain copy for graphs that were not relabeled. `in` and `out`
+// are device pointers and must not alias.
+nx_status vertex_to_internal(const nx_graph* g, const void* in, void* out);
+nx_status vertex_to_caller(const nx_graph* g, const void* in, void* out);
 }  // namespace nx
 

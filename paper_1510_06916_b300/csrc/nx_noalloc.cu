@@ -85,6 +85,8 @@ extern "C" nx_status nx_pagerank_step_noalloc(const nx_graph* g, float alpha, co
   if (r_in == r_out) return nx::invalid("nx_pagerank_step_noalloc: r_in and r_out must differ");
   if (!(alpha >= 0.f && alpha < 1.f))
     return nx::invalid("nx_pagerank_step_noalloc: alpha must be in [0, 1)");
+  if (g->relabeled)  // mapping caller order would need scratch of n entries
+    return nx::invalid("nx_pagerank_step_noalloc: the graph was built with NX_RELABEL");
   const uint32_t ntiles = g->geo.ntiles, n = g->geo.n;
   if (ntiles > nx::kMaxTiles)
     return nx::invalid("nx_pagerank_step_noalloc: the graph has more destination tiles than the "

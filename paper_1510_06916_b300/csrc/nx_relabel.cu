@@ -1,0 +1,131 @@
+// Degree-ordered vertex ids (the "degreeing" step of Section III-A maps the
+// input's vertex indices to the ids the sharder uses). Here the map is a
+// permutation of [0, n): internal id k is the caller vertex with the k-th
+// largest out-degree (ties by caller id), so the most-read source values share
+// cache lines. No vertex is dropped, so n and every result are unchanged; the
+// ABI maps vertex-indexed inputs and outputs between the two numberings.
+#include <algorithm>
+
+#include "nx_internal.cuh"
+
+namespace nx {
+namespace {
+
+__global__ void k_outdeg(const uint32_t* __restrict__ s, uint64_t m, uint32_t* __restrict__ od) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+    atomicAdd(&od[s[e]], 1u);
+}
+
+// key = (m - outdeg) << vb | v: ascending keys = descending degree, then id.
+__global__ void k_order_keys(const uint32_t* __restrict__ od, uint32_t n, uint64_t m, uint32_t vb,
+                             uint64_t* __restrict__ keys) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    keys[v] = ((m - od[v]) << vb) | v;
+}
+
+__global__ void k_order_perm(const uint64_t* __restrict__ keys, uint32_t n, uint32_t vb,
+                             uint32_t* __restrict__ old_of_new, uint32_t* __restrict__ new_of_old) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t mask = (1ull << vb) - 1;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    const uint32_t old = (uint32_t)(keys[k] & mask);
+    old_of_new[k] = old;
+    new_of_old[old] = (uint32_t)k;
+  }
+}
+
+__global__ void k_rename(const uint32_t* __restrict__ map, const uint32_t* s, const uint32_t* d,
+                         uint64_t m, uint32_t* s_out, uint32_t* d_out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const uint32_t a = s[e], b = d[e];
+    s_out[e] = map[a];
+    d_out[e] = map[b];
+  }
+}
+
+__global__ void k_gather(const uint32_t* __restrict__ idx, const uint32_t* __restrict__ in,
+                         uint64_t n, uint32_t* __restrict__ out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
+    out[k] = in[idx[k]];
+}
+
+unsigned grid_of(uint64_t work) {
+  return (unsigned)std::min<uint64_t>(ceil_div(work ? work : 1, 256), (uint64_t)num_sms() * 8);
+}
+
+}  // namespace
+
+nx_status relabel_edges(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64_t m,
+                        uint32_t* s_out, uint32_t* d_out) {
+  const uint32_t n = g->geo.n;
+  const uint32_t vb = std::max<uint32_t>(1, bits_for(n));
+  const uint32_t db = bits_for(m + 1);
+  DevBuf od, keys;
+  NX_TRY(od.alloc((uint64_t)n * 4));
+  NX_TRY(keys.alloc((uint64_t)n * 8));
+  NX_CUDA(cudaMemsetAsync(od.p, 0, (uint64_t)n * 4, stream()));
+  if (m) {
+    k_outdeg<<<grid_of(m), 256, 0, stream()>>>(s, m, od.as<uint32_t>());
+    NX_LAUNCH_CHECK();
+  }
+  k_order_keys<<<grid_of(n), 256, 0, stream()>>>(od.as<uint32_t>(), n, m, vb, keys.as<uint64_t>());
+  NX_LAUNCH_CHECK();
+  NX_TRY(radix_sort_u64(keys.as<uint64_t>(), nullptr, n, vb + db));
+  NX_TRY(g->old_of_new.alloc((uint64_t)n * 4));
+  NX_TRY(g->new_of_old.alloc((uint64_t)n * 4));
+  k_order_perm<<<grid_of(n), 256, 0, stream()>>>(keys.as<uint64_t>(), n, vb,
+                                                 g->old_of_new.as<uint32_t>(),
+                                                 g->new_of_old.as<uint32_t>());
+  NX_LAUNCH_CHECK();
+  if (m) {
+    k_rename<<<grid_of(m), 256, 0, stream()>>>(g->new_of_old.as<uint32_t>(), s, d, m, s_out, d_out);
+    NX_LAUNCH_CHECK();
+  }
+  NX_CUDA(cudaStreamSynchronize(stream()));  // od and keys are freed on return
+  g->relabeled = true;
+  return NX_OK;
+}
+
+nx_status gather_u32(const uint32_t* idx, const void* in, void* out, uint64_t n) {
+  if (!n) return NX_OK;
+  k_gather<<<grid_of(n), 256, 0, stream()>>>(idx, static_cast<const uint32_t*>(in), n,
+                                             static_cast<uint32_t*>(out));
+  NX_LAUNCH_CHECK();
+  return NX_OK;
+}
+
+nx_status vertex_to_internal(const nx_graph* g, const void* in, void* out) {
+  const uint64_t n = g->geo.n;
+  if (!g->relabeled) {
+    NX_CUDA(cudaMemcpyAsync(out, in, n * 4, cudaMemcpyDeviceToDevice, stream()));
+    return NX_OK;
+  }
+  return gather_u32(g->old_of_new.as<uint32_t>(), in, out, n);
+}
+
+nx_status vertex_to_caller(const nx_graph* g, const void* in, void* out) {
+  const uint64_t n = g->geo.n;
+  if (!g->relabeled) {
+    NX_CUDA(cudaMemcpyAsync(out, in, n * 4, cudaMemcpyDeviceToDevice, stream()));
+    return NX_OK;
+  }
+  return gather_u32(g->new_of_old.as<uint32_t>(), in, out, n);
+}
+
+}  // namespace nx
+
+extern "C" nx_status nx_get_relabel(const nx_graph* g, uint32_t* old_of_new, uint64_t count,
+                                    int32_t out_is_device) {
+  if (!g || !old_of_new) return nx::invalid("nx_get_relabel: NULL argument");
+  if (!g->relabeled) return nx::invalid("nx_get_relabel: the graph was built without NX_RELABEL");
+  if (count != g->geo.n) return nx::invalid("nx_get_relabel: count must equal n");
+  NX_CUDA(cudaMemcpyAsync(old_of_new, g->old_of_new.p, count * 4,
+                          out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          nx::stream()));
+  NX_CUDA(cudaStreamSynchronize(nx::stream()));
+  return NX_OK;
+}

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "csrc", "libnxgraph.so")
 NX_OK, NX_ERR_INVALID_ARG, NX_ERR_OOM, NX_ERR_BUDGET_TOO_SMALL, NX_ERR_CUDA, NX_ERR_TIMEOUT = range(6)
 PR, PPR, WPR, BFS, WCC = range(5)
 SPU, DPU, MPU, AUTO, SRC_COARSE, SRC_FINE = range(6)
-HOST_PTRS, DEV_PTRS, WITH_TRANSPOSE, WITH_WEIGHTS = 0, 1, 2, 4
+HOST_PTRS, DEV_PTRS, WITH_TRANSPOSE, WITH_WEIGHTS, RELABEL = 0, 1, 2, 4, 8
 INF = 0xFFFFFFFF
 
 PROGRAMS = {"pr": PR, "ppr": PPR, "wpr": WPR, "bfs": BFS, "wcc": WCC}
@@ -29,7 +29,7 @@ EXPORTS = [
     "nx_set_stream", "nx_last_error", "nx_build_dsss", "nx_graph_get_info", "nx_run",
     "nx_get_values", "nx_set_values", "nx_run_ppr_batch", "nx_adjoint_wpr", "nx_run_multi",
     "nx_graph_free", "nx_io_model", "nx_dsss_export", "nx_pagerank_step_noalloc",
-    "nx_autotune",
+    "nx_autotune", "nx_get_relabel",
 ]
 
 
@@ -91,6 +91,7 @@ def lib():
         L.nx_run_multi.argtypes = [ctypes.POINTER(vp), u32, i32, f32, u32,
                                    ctypes.POINTER(NxRunStats)]
         L.nx_dsss_export.argtypes = [vp, i32, vp, vp, vp]
+        L.nx_get_relabel.argtypes = [vp, vp, u64, i32]
         L.nx_pagerank_step_noalloc.argtypes = [vp, f32, vp, vp]
         L.nx_autotune.argtypes = [vp, vp, u64, u32, u32, vp, i32, vp, u32, u32,
                                   ctypes.POINTER(u32), vp, ctypes.c_char_p]
@@ -159,7 +160,8 @@ def io_model(strategy, n, m, P, B_M, B_a=4.0, B_v=4.0, B_e=4.0, d=15.0):
 class Graph:
     """A DSSS built on the current device (owns it; free() or context exit)."""
 
-    def __init__(self, src, dst, n: int, P: int, transpose: bool = False, weights=None):
+    def __init__(self, src, dst, n: int, P: int, transpose: bool = False, weights=None,
+                 relabel: bool = False):
         if isinstance(src, np.ndarray):
             src = np.ascontiguousarray(src, dtype=np.uint32)
         if isinstance(dst, np.ndarray):
@@ -180,6 +182,8 @@ class Graph:
         flags = DEV_PTRS if sd else HOST_PTRS
         if transpose:
             flags |= WITH_TRANSPOSE
+        if relabel:
+            flags |= RELABEL
         wp = None
         if weights is not None:
             wp, wd = _ptr(weights)
@@ -194,6 +198,12 @@ class Graph:
     @property
     def handle(self):
         return self._h
+
+    def relabel_map(self) -> np.ndarray:
+        """old_of_new[k] = caller id of internal vertex k (graphs built with relabel=True)."""
+        out = np.empty(self.n, dtype=np.uint32)
+        check(lib().nx_get_relabel(self._h, out.ctypes.data, self.n, 0))
+        return out
 
     def free(self):
         if self._h:

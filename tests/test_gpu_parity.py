@@ -504,3 +504,110 @@ def test_source_sorted_push_rejects():
         gt.run("pr", 2, "src_coarse", budget=1 << 20)
     gt.run("pr", 2, "src_coarse")
     assert np.allclose(gt.values(), 1.0 / n, rtol=1e-6)
+
+
+# ------------------------------------------- degree-ordered ids (NX_RELABEL)
+
+def _ragged_graph():
+    n = 5000
+    s, d, _ = inputs.rmat_edges(13, 60000, 17)
+    keep = (s < n) & (d < n)
+    return n, s[keep], d[keep]
+
+
+@pytest.mark.parametrize("P", [1, 4, 7])
+def test_relabel_order_and_layout(P):
+    n, s, d = _ragged_graph()
+    g = nx.Graph(s, d, n, P, transpose=True, relabel=True)
+    old_of_new = g.relabel_map()
+    assert (np.sort(old_of_new) == np.arange(n)).all()  # a permutation
+    od = np.bincount(s, minlength=n)[old_of_new]
+    assert (np.diff(od) <= 0).all()  # out-degree non-increasing
+    tie = np.diff(od) == 0
+    assert (np.diff(old_of_new.astype(np.int64))[tie] > 0).all()  # ties by caller id
+    new_of_old = np.empty(n, np.uint32)
+    new_of_old[old_of_new] = np.arange(n, dtype=np.uint32)
+    ns, nd = new_of_old[s], new_of_old[d]
+    order, off = oracle.dsss_order(n, P, ns, nd)  # the DSSS of the renamed graph
+    gs, gd, goff = g.export()
+    assert (goff == off).all()
+    assert (gs == ns[order]).all() and (gd == nd[order]).all()
+    order_t, _ = oracle.dsss_order(n, P, nd, ns)
+    ts, td, _ = g.export(transpose=True)
+    assert (ts == ns[order_t]).all() and (td == nd[order_t]).all()
+
+
+@pytest.mark.parametrize("P", [3, 16])
+def test_relabel_programs_in_caller_ids(P):
+    n, s, d = _ragged_graph()
+    g = nx.Graph(s, d, n, P, transpose=True, relabel=True)
+    g.run("pr", 20)
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"relabel P={P} PR")
+    for strat in ("dpu", "src_fine"):
+        g.run("pr", 20, strat)
+        assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"relabel {strat}")
+    g.run("pr", 20, "mpu", budget=2 * n * 4 // 2 + 1)
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), "relabel MPU")
+    t = inputs.ppr_teleports(n, 1, 5)[:, 0].copy()
+    g.run("ppr", 30, teleport=t)
+    assert_pr_close(g.values(), oracle.personalized_pagerank(n, s, d, t, 0.85, 30), "relabel PPR")
+    for root in (1, 4999):
+        g.run("bfs", 1000, root=root)
+        assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, root)).all()
+    g.run("wcc", 1000)
+    assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+    g.run("wcc", 1000, "dpu")
+    assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+    # resume: values set in caller order continue in caller order
+    g.run("pr", 10)
+    mid = g.values().copy()
+    g.set_values("pr", mid)
+    g.run("pr", 10)
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), "relabel resume")
+
+
+def test_relabel_device_pointers_batch_and_adjoint():
+    import torch
+
+    n = 1 << 12
+    s, d, w = rmat(12, 16, 4, weights=True)
+    g = nx.Graph(torch.from_numpy(s.view(np.int32)).cuda(), torch.from_numpy(d.view(np.int32)).cuda(),
+                 n, 4, transpose=True, weights=torch.from_numpy(w).cuda(), relabel=True)
+    T = inputs.ppr_teleports(n, 8, 21)
+    R, _ = g.ppr_batch(torch.from_numpy(T).cuda(), iters=30)
+    R = R.cpu().numpy()
+    for b in (0, 5):
+        ref = oracle.personalized_pagerank(n, s, d, T[:, b].astype(np.float64), 0.85, 30)
+        assert_pr_close(R[:, b], ref, f"relabel batch col {b}")
+    tv = torch.from_numpy(T[:, 3].copy()).cuda()
+    g.run("ppr", 30, teleport=tv)  # device teleport
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    g.values(out)
+    ref = oracle.personalized_pagerank(n, s, d, T[:, 3].astype(np.float64), 0.85, 30)
+    assert_pr_close(out.cpu().numpy(), ref, "relabel device PPR")
+    gv = np.zeros(n, np.float32)
+    gv[inputs.targets(n, 64, 4)] = 1.0
+    g.run("wpr", 20)
+    dw = np.empty(len(s), np.float32)
+    dt = np.empty(n, np.float32)
+    g.adjoint_wpr(gv, 20, dw, dt)
+    ref = oracle.wpr_adjoint(n, s, d, w.astype(np.float64), gv.astype(np.float64), 0.85, 20, 20)
+    assert_pr_close(g.values(), ref["r"], "relabel WPR")
+    for got, want, what in ((dt, ref["dt"], "dL/dt"), (dw, ref["dw"], "dL/dw")):
+        _grad_close(got, want, f"relabel {what}")
+
+
+def test_relabel_rejected_where_unsupported():
+    import torch
+
+    n, s, d = _ragged_graph()
+    g = nx.Graph(s, d, n, 4, relabel=True)
+    with pytest.raises(nx.NxError):
+        nx.run_multi([g], "pr", 2)
+    r_in = torch.full((n,), 1.0 / n, dtype=torch.float32, device="cuda")
+    r_out = torch.empty_like(r_in)
+    rc = nx.lib().nx_pagerank_step_noalloc(g.handle, 0.85, r_in.data_ptr(), r_out.data_ptr())
+    assert rc == nx.NX_ERR_INVALID_ARG
+    plain = nx.Graph(s, d, n, 4)
+    with pytest.raises(nx.NxError):
+        plain.relabel_map()
