@@ -411,13 +411,16 @@ struct RunCtx {
   nx_program prog;
   std::vector<const Dsss*> ds;
   uint32_t P, Q, Jc;
+  uint64_t keep[2] = {0, 0};  // leading words of shard Jc (per DSSS) cached in device memory
   const float* tele;
   uint64_t h2d = 0, d2h = 0;
   uint32_t launches = 0;
 };
 
 // SPU iteration with columns [Jc, P) streamed from pinned host memory on a
-// side stream (double-buffered); columns [0, Jc) are read in place.
+// side stream (double-buffered); columns [0, Jc) are read in place. The
+// leading c.keep[s] words of column Jc are cached in device memory, so only
+// the rest of that column crosses the host link.
 nx_status spu_stream_iteration(RunCtx& c, SweepArgs& a, const std::vector<uint32_t>& col_off,
                                Streamer& sm) {
   nx_graph* g = c.g;
@@ -442,9 +445,14 @@ nx_status spu_stream_iteration(RunCtx& c, SweepArgs& a, const std::vector<uint32
       const uint64_t words = e1 - e0;
       // stage[b] holds one shard per DSSS of the sweep (second half: transpose)
       uint32_t* dst = g->stage[b].as<uint32_t>() + (s ? (g->stage[b].bytes / 8) : 0);
-      NX_CUDA(cudaMemcpyAsync(dst, d.h_ew.as<uint32_t>() + (e0 - d.h_ew_first), words * 4,
-                              cudaMemcpyHostToDevice, sm.side));
-      c.h2d += words * 4;
+      const uint64_t kw = (j == c.Jc) ? std::min(c.keep[s], words) : 0;
+      if (kw)
+        NX_CUDA(cudaMemcpyAsync(dst, d.ew.as<uint32_t>() + e0, kw * 4, cudaMemcpyDeviceToDevice,
+                                sm.side));
+      if (words > kw)
+        NX_CUDA(cudaMemcpyAsync(dst + kw, d.h_ew.as<uint32_t>() + (e0 + kw - d.h_ew_first),
+                                (words - kw) * 4, cudaMemcpyHostToDevice, sm.side));
+      c.h2d += (words - kw) * 4;
       sa.src[s].ew = dst;
       sa.ew_lo[s] = e0;
     }
@@ -715,6 +723,15 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       left -= bytes;
     }
     c.Jc = j;
+    if (c.Jc < P) {  // the rest of the budget caches the head of shard Jc
+      for (size_t s = 0; s < c.ds.size(); ++s) {
+        const Dsss* d = c.ds[s];
+        const uint64_t w = d->h_piece_off[(uint64_t)P * tb[j + 1]] - d->h_piece_off[(uint64_t)P * tb[j]];
+        const uint64_t kw = std::min<uint64_t>(w, left / 4) & ~(kEdgeAlign - 1);
+        c.keep[s] = kw;
+        left -= kw * 4;
+      }
+    }
     if (c.Jc < P && prog == NX_WPR) {
       set_error("nx_run: weighted PageRank needs its edges on the device (budget too small)");
       return NX_ERR_BUDGET_TOO_SMALL;

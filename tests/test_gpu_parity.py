@@ -303,6 +303,10 @@ def test_spu_streams_shards_from_host(frac):
     st = g.run("pr", 20, "spu", budget=budget)
     assert st["streamed_cols"] > 0 and st["h2d_bytes"] > 0
     assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"streamed PR {frac}")
+    # byte-granular caching: each iteration moves m B_e + 2 n B_a - B_M (Section III-B1),
+    # up to the 16-word alignment of each streamed shard
+    want = 4 * m + 2 * n * 4 - budget
+    assert abs(st["h2d_bytes"] / 20 - want) <= 8 * 3 * 16 * 4 + 64, (st["h2d_bytes"] / 20, want)
     g.run("bfs", 1000, "spu", budget=budget, root=0)
     assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 0)).all()
     st = g.run("wcc", 1000, "spu", budget=budget + int(frac * 4 * m))
