@@ -85,9 +85,10 @@ typedef struct {
   int32_t teleport_is_device;
   int32_t use_graph;      /* reserved, set to 0                                  */
   uint32_t band_intervals;/* SPU: source intervals per launch (0 = automatic: one
-                             launch when the gathered value array fits the L2,
-                             else bands whose values do); accumulators carry
-                             between bands in device memory                      */
+                             launch, or, when the gathered value array exceeds
+                             128 MB and P >= 32, bands whose values fit in 128
+                             MB); accumulators carry between bands in device
+                             memory                                              */
 } nx_params;
 
 typedef struct {

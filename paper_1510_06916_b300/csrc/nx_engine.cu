@@ -742,9 +742,11 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   // fit in L2 together (the value array of the whole graph may not)
   uint32_t band = P;
   if (strat == NX_SPU && !streaming) {
-    const uint64_t kBandBytes = 128ull << 20;  // about the L2; smaller bands measured slower
+    // Measured at R-MAT scale 26 (268 MB of values): two bands gain 2-3% at P = 32 and 64
+    // (short pieces), and lose 2-10% at P = 16 and 8; smaller bands lose at every P.
+    const uint64_t kBandBytes = 128ull << 20;  // about the L2
     if (p.band_intervals) band = std::min<uint32_t>(p.band_intervals, P);
-    else if ((uint64_t)n * 4 > kBandBytes)
+    else if ((uint64_t)n * 4 > kBandBytes && P >= 32)
       band = (uint32_t)std::max<uint64_t>(1, kBandBytes / ((uint64_t)L * 4));
   }
   const uint32_t nbands = (uint32_t)ceil_div(P, band);
