@@ -227,16 +227,29 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint64_t* __restrict
   }
 }
 
+// Stable scatter of one 8-bit digit. Keys are ranked per warp (lane order
+// within a round, rounds in order, warps in order = input order), placed in
+// shared memory in digit order, and written out from there so that
+// consecutive threads store consecutive addresses of one digit's run.
+// Dynamic shared memory: RS_TILE keys (+ RS_TILE values when vin != nullptr).
 __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
     uint32_t* __restrict__ vout, uint64_t n, uint32_t shift, const uint32_t* __restrict__ offs,
     uint32_t nb) {
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  uint64_t* sk = reinterpret_cast<uint64_t*>(rs_smem);       // [RS_TILE]
+  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + RS_TILE);  // [RS_TILE] (values)
   __shared__ uint32_t wc[RS_WARPS][257];
+  __shared__ uint32_t dstart[256];  // first local slot of each digit
+  __shared__ uint32_t gbase[256];   // first global slot of this block's run of each digit
+  __shared__ uint32_t wsum[RS_WARPS];
   for (int k = threadIdx.x; k < RS_WARPS * 257; k += RS_THREADS) (&wc[0][0])[k] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const uint64_t base = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)w * RS_WARP_KEYS + lane;
+  const uint64_t tile0 = (uint64_t)blockIdx.x * RS_TILE;
+  const uint64_t base = tile0 + (uint64_t)w * RS_WARP_KEYS + lane;
+  const uint32_t cnt = (uint32_t)((n - tile0) < (uint64_t)RS_TILE ? (n - tile0) : (uint64_t)RS_TILE);
   uint64_t key[RS_ROUNDS];
   uint32_t rank[RS_ROUNDS];
 #pragma unroll
@@ -253,13 +266,34 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
     rank[r] = before + __popc(peers & lt_mask);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
-    uint32_t s = offs[(uint64_t)d * nb + blockIdx.x];
+  // per digit: block total, then per-warp starts inside the digit's local run
+  uint32_t tot = 0;
+  if (threadIdx.x < 256) {
+    const int d = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < RS_WARPS; ++q) tot += wc[q][d];
+    gbase[d] = offs[(uint64_t)d * nb + blockIdx.x];
+  }
+  // exclusive scan of the 256 digit totals (one per thread)
+  uint32_t x = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  uint32_t pre = 0;
+  for (int q = 0; q < w; ++q) pre += wsum[q];
+  if (threadIdx.x < 256) {
+    const int d = threadIdx.x;
+    uint32_t st = pre + x - tot;
+    dstart[d] = st;
 #pragma unroll
     for (int q = 0; q < RS_WARPS; ++q) {
-      uint32_t t = wc[q][d];
-      wc[q][d] = s;
-      s += t;
+      const uint32_t t = wc[q][d];
+      wc[q][d] = st;
+      st += t;
     }
   }
   __syncthreads();
@@ -267,11 +301,19 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
   for (int r = 0; r < RS_ROUNDS; ++r) {
     uint64_t idx = base + (uint64_t)r * 32;
     if (idx < n) {
-      uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
-      uint32_t pos = wc[w][d] + rank[r];
-      kout[pos] = key[r];
-      if (vin) vout[pos] = vin[idx];
+      const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+      const uint32_t lp = wc[w][d] + rank[r];
+      sk[lp] = key[r];
+      if (vin) sv[lp] = vin[idx];
     }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < cnt; i += RS_THREADS) {
+    const uint64_t k = sk[i];
+    const uint32_t d = (uint32_t)(k >> shift) & 255u;
+    const uint32_t pos = gbase[d] + (i - dstart[d]);
+    kout[pos] = k;
+    if (vin) vout[pos] = sv[i];
   }
 }
 }  // namespace
@@ -288,14 +330,17 @@ nx_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t n, uint32_t ke
   uint64_t* kb = k2.as<uint64_t>();
   uint32_t* va = vals;
   uint32_t* vb = vals ? v2.as<uint32_t>() : nullptr;
+  const size_t smem = (size_t)RS_TILE * (sizeof(uint64_t) + (vals ? sizeof(uint32_t) : 0));
+  // dynamic + static shared memory exceed 48 KB: opt in (per device, so every call)
+  NX_CUDA(cudaFuncSetAttribute(rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int passes = 0;
   for (uint32_t shift = 0; shift < key_bits; shift += 8, ++passes) {
     rs_hist<<<nb, RS_THREADS, 0, stream()>>>(ka, n, shift, counts.as<uint32_t>(), nb);
     NX_LAUNCH_CHECK();
     NX_TRY(exclusive_scan_u32(counts.as<uint32_t>(), counts.as<uint32_t>(), (uint64_t)nb * 256,
                               nullptr));
-    rs_scatter<<<nb, RS_THREADS, 0, stream()>>>(ka, va, kb, vb, n, shift, counts.as<uint32_t>(),
-                                                nb);
+    rs_scatter<<<nb, RS_THREADS, smem, stream()>>>(ka, va, kb, vb, n, shift,
+                                                   counts.as<uint32_t>(), nb);
     NX_LAUNCH_CHECK();
     std::swap(ka, kb);
     std::swap(va, vb);
