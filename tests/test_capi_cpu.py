@@ -72,3 +72,26 @@ def test_io_model_mpu_interpolates(frac):
     q0, rd0, wr0 = nx.io_model("mpu", n, m, P, 0.0, Ba, Bv, Be, d)
     qd, rdd, wrd = nx.io_model("dpu", n, m, P, 0.0, Ba, Bv, Be, d)
     assert q0 == 0 and rd0 == pytest.approx(rdd) and wr0 == pytest.approx(wrd)
+
+
+def test_null_handles_rejected_without_a_device():
+    L = nx.lib()
+    buf = np.zeros(4, np.uint32)
+    # NULL graph / output pointers are refused before any CUDA call
+    assert L.nx_get_relabel(None, buf.ctypes.data, 4, 0) == nx.NX_ERR_INVALID_ARG
+    assert L.nx_get_values(None, buf.ctypes.data, 4, 0) == nx.NX_ERR_INVALID_ARG
+    assert L.nx_run(None, nx.PR, None, 1, nx.SPU, 0, None) == nx.NX_ERR_INVALID_ARG
+    assert L.nx_run_multi(None, 0, nx.PR, 0.85, 1, None) == nx.NX_ERR_INVALID_ARG
+    assert L.nx_pagerank_step_noalloc(None, 0.85, None, None) == nx.NX_ERR_INVALID_ARG
+    msg = nx.last_error()
+    assert "NULL" in msg
+
+
+def test_strategy_names_cover_the_ablation():
+    # the Table IV ablation strategies follow AUTO in the C enum
+    assert (nx.SRC_COARSE, nx.SRC_FINE) == (nx.AUTO + 1, nx.AUTO + 2)
+    assert nx.STRATEGIES["src_coarse"] == nx.SRC_COARSE
+    assert nx.STRATEGIES["src_fine"] == nx.SRC_FINE
+    hdr = open(HDR).read()
+    assert re.search(r"NX_SRC_COARSE\s*=\s*4", hdr) and re.search(r"NX_SRC_FINE\s*=\s*5", hdr)
+    assert re.search(r"#define NX_RELABEL 8u", hdr) and nx.RELABEL == 8
