@@ -881,15 +881,19 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   Scal sc = scal_of(g);
   uint64_t swept = 0;
   uint32_t done = 0;
-  std::vector<uint32_t> act_h(P + 1, 1);
+  // activity: [0] = active-interval count, [1 + i] = flag of interval i (pinned)
+  if (g->hact.bytes < ((size_t)P + 1) * 4) NX_TRY(g->hact.alloc(((size_t)P + 1) * 4));
+  uint32_t* hact = g->hact.as<uint32_t>();
+  const uint32_t* act_h = hact + 1;
+  std::fill(hact, hact + P + 1, 1u);
+  if (is_min(prog)) {  // the flags Initialize left (later ones arrive with each count)
+    NX_CUDA(cudaMemcpyAsync(hact + 1, g->act[g->cur].p, (size_t)P * 4, cudaMemcpyDeviceToHost,
+                            stream()));
+    NX_CUDA(cudaStreamSynchronize(stream()));
+    c.d2h += (uint64_t)P * 4;
+  }
   NX_CUDA(cudaEventRecord(ev.e0, stream()));
   for (uint32_t it = 0; it < iters; ++it) {
-    if (is_min(prog)) {
-      NX_CUDA(cudaMemcpyAsync(act_h.data(), g->act[g->cur].p, (size_t)P * 4,
-                              cudaMemcpyDeviceToHost, stream()));
-      NX_CUDA(cudaStreamSynchronize(stream()));
-      c.d2h += (uint64_t)P * 4;
-    }
     for (uint32_t i = 0; i < P; ++i)
       if (act_h[i]) swept += row_edges[i];
     if (strat == NX_SPU && !streaming && nbands == 1) {
@@ -906,12 +910,13 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       NX_TRY(mpu_iteration(c, a, S));
     }
     ++done;
-    if (is_min(prog)) {
-      uint32_t cnt = 0;
-      NX_CUDA(cudaMemcpyAsync(&cnt, sc.act_count, 4, cudaMemcpyDeviceToHost, stream()));
+    if (is_min(prog)) {  // Algorithm 1: stop when no interval is active; one round trip
+      NX_CUDA(cudaMemcpyAsync(hact, sc.act_count, 4, cudaMemcpyDeviceToHost, stream()));
+      NX_CUDA(cudaMemcpyAsync(hact + 1, g->act[g->cur].p, (size_t)P * 4, cudaMemcpyDeviceToHost,
+                              stream()));
       NX_CUDA(cudaStreamSynchronize(stream()));
-      c.d2h += 4;
-      if (cnt == 0) break;
+      c.d2h += 4 + (uint64_t)P * 4;
+      if (hact[0] == 0) break;
     }
   }
   NX_CUDA(cudaEventRecord(ev.e1, stream()));

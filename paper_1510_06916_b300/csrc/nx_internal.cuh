@@ -198,6 +198,7 @@ struct nx_graph {
   nx::DevBuf stage[2];      // staging for streamed shards
   nx::DevBuf vstage[4];     // staging for non-resident intervals (MPU)
   nx::PinnedBuf hval[2];    // pinned host values of non-resident intervals
+  nx::PinnedBuf hact;       // pinned host copy of the activity count + flags [P + 1]
   nx::DevBuf accres;        // MPU resident-column accumulators
   cudaGraphExec_t gexec = nullptr;
   int gexec_key = -1;
