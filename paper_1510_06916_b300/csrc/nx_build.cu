@@ -433,7 +433,8 @@ uint64_t nx_graph::device_bytes() const {
                               &val[0], &val[1], &aux[0], &aux[1], &act[0], &act[1], &scal,
                               &tile_part, &split_buf, &tile_ticket, &hubs, &hubs_t, &tele,
                               &lam[0], &lam[1], &ybuf, &stage[0], &stage[1], &vstage[0],
-                              &vstage[1], &vstage[2], &vstage[3], &accres, &init_part};
+                              &vstage[1], &vstage[2], &vstage[3], &vstage[4], &vstage[5],
+                              &vstage[6], &vstage[7], &accres, &init_part};
   uint64_t s = 0;
   for (auto* b : bufs) s += b->bytes;
   for (const auto& kv : plans) s += kv.second->items.bytes;

@@ -412,6 +412,7 @@ struct RunCtx {
   std::vector<const Dsss*> ds;
   uint32_t P, Q, Jc;
   uint64_t keep[2] = {0, 0};  // leading words of shard Jc (per DSSS) cached in device memory
+  const uint32_t* act_host = nullptr;  // BFS / WCC: this iteration's interval flags (host)
   const float* tele;
   uint64_t h2d = 0, d2h = 0;
   uint32_t launches = 0;
@@ -491,9 +492,39 @@ nx_status spu_band_iteration(RunCtx& c, SweepArgs& a, const std::vector<uint32_t
 }
 
 // MPU iteration (Algorithm 7) with intervals [Q, P) in pinned host memory.
+// Their transfers run on a side stream, double-buffered against the sweeps:
+// vstage[0..1] source rows (lines 7-16), vstage[2..3] / [4..5] new values /
+// contributions of a staged column, vstage[6..7] its previous values (BFS,
+// WCC; lines 17-26).
 struct Staged {
   uint32_t n_res = 0, nh = 0;
   std::vector<uint32_t> off;  // launch boundaries in the item array
+  cudaStream_t side = nullptr;
+  // row_in/row_used: source row copied / its sweep done; col_in: previous
+  // values copied; col_done: column swept; col_out: its results copied out
+  cudaEvent_t row_in[2] = {}, row_used[2] = {}, col_in[2] = {}, col_done[2] = {}, col_out[2] = {};
+  uint32_t nrow = 0, ncol = 0;  // buffers handed out so far (parity picks the buffer)
+  ~Staged() {
+    for (cudaEvent_t* e : {row_in, row_used, col_in, col_done, col_out})
+      for (int k = 0; k < 2; ++k)
+        if (e[k]) cudaEventDestroy(e[k]);
+    if (side) cudaStreamDestroy(side);
+  }
+  nx_status init() {
+    NX_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {row_in, row_used, col_in, col_done, col_out})
+      for (int k = 0; k < 2; ++k) {
+        NX_CUDA(cudaEventCreateWithFlags(&e[k], cudaEventDisableTiming));
+        NX_CUDA(cudaEventRecord(e[k], stream()));
+      }
+    return NX_OK;
+  }
+  // the main stream waits for everything queued on the side stream
+  nx_status join() {
+    NX_CUDA(cudaEventRecord(col_out[0], side));
+    NX_CUDA(cudaStreamWaitEvent(stream(), col_out[0], 0));
+    return NX_OK;
+  }
 };
 
 nx_status mpu_iteration(RunCtx& c, SweepArgs& a, Staged& S) {
@@ -525,29 +556,30 @@ nx_status mpu_iteration(RunCtx& c, SweepArgs& a, Staged& S) {
     NX_TRY(launch_sweep(K, m2, k, stream()));
     ++c.launches;
   }
-  // 2. rows i >= Q: load I_i, update resident columns in place, ToHub the rest (lines 7-16)
-  std::vector<uint32_t> act_h(P, 1);
-  if (!pr) {
-    NX_CUDA(cudaMemcpyAsync(act_h.data(), a.act_in, P * 4, cudaMemcpyDeviceToHost, stream()));
-    NX_CUDA(cudaStreamSynchronize(stream()));
-  }
+  // 2. rows i >= Q: load I_i, update resident columns in place, ToHub the rest (lines 7-16).
+  // BFS / WCC skip inactive rows (the run's host copy of this iteration's flags).
   for (uint32_t i = Q; i < P; ++i) {
     auto [it, k] = items_of(li++);
-    if (!act_h[i] || k == 0) continue;
+    if ((!pr && !c.act_host[i]) || k == 0) continue;
     const uint32_t v0 = i * L, v1 = std::min<uint32_t>(n, v0 + L);
     if (v1 <= v0) continue;
     const float* src_host = (has_c ? hc_old : hv_old) + (v0 - S.n_res);
-    NX_CUDA(cudaMemcpyAsync(g->vstage[0].p, src_host, (size_t)(v1 - v0) * 4,
-                            cudaMemcpyHostToDevice, stream()));
+    const int b = (int)(S.nrow++ & 1);
+    NX_CUDA(cudaStreamWaitEvent(S.side, S.row_used[b], 0));  // the sweep two rows back is done
+    NX_CUDA(cudaMemcpyAsync(g->vstage[b].p, src_host, (size_t)(v1 - v0) * 4,
+                            cudaMemcpyHostToDevice, S.side));
+    NX_CUDA(cudaEventRecord(S.row_in[b], S.side));
     c.h2d += (uint64_t)(v1 - v0) * 4;
     SweepArgs m1 = a;
     m1.mode = 1;
     m1.items = it;
     m1.q_res = Q;
     m1.accres = g->accres.p;
-    m1.gstage = g->vstage[0].p;
+    m1.gstage = g->vstage[b].p;
     m1.stage_i = i;
+    NX_CUDA(cudaStreamWaitEvent(stream(), S.row_in[b], 0));
     NX_TRY(launch_sweep(K, m1, k, stream()));
+    NX_CUDA(cudaEventRecord(S.row_used[b], stream()));
     ++c.launches;
   }
   // 3. epilogue of the resident columns from their accumulators
@@ -566,6 +598,7 @@ nx_status mpu_iteration(RunCtx& c, SweepArgs& a, Staged& S) {
     const uint32_t v0 = j * L, v1 = std::min<uint32_t>(n, v0 + L);
     if (v1 <= v0) continue;
     const size_t bytes = (size_t)(v1 - v0) * 4;
+    const int b = (int)(S.ncol++ & 1);
     SweepArgs m0 = a;
     m0.mode = 0;
     m0.items = it;
@@ -574,24 +607,31 @@ nx_status mpu_iteration(RunCtx& c, SweepArgs& a, Staged& S) {
     m0.hub_lo = Q;
     m0.hub_hi = P;
     m0.out_base = v0;
-    m0.vnew = g->vstage[1].p;
-    m0.cnew = has_c ? g->vstage[2].as<float>() : nullptr;
-    if (!pr) {
-      NX_CUDA(cudaMemcpyAsync(g->vstage[3].p, hv_old + (v0 - S.n_res), bytes,
-                              cudaMemcpyHostToDevice, stream()));
+    m0.vnew = g->vstage[2 + b].p;
+    m0.cnew = has_c ? g->vstage[4 + b].as<float>() : nullptr;
+    if (!pr) {  // previous values: the sweep two columns back is done with the buffer
+      NX_CUDA(cudaStreamWaitEvent(S.side, S.col_done[b], 0));
+      NX_CUDA(cudaMemcpyAsync(g->vstage[6 + b].p, hv_old + (v0 - S.n_res), bytes,
+                              cudaMemcpyHostToDevice, S.side));
+      NX_CUDA(cudaEventRecord(S.col_in[b], S.side));
+      NX_CUDA(cudaStreamWaitEvent(stream(), S.col_in[b], 0));
       c.h2d += bytes;
-      m0.vold = g->vstage[3].p;
+      m0.vold = g->vstage[6 + b].p;
     }
+    NX_CUDA(cudaStreamWaitEvent(stream(), S.col_out[b], 0));  // outputs two columns back copied out
     NX_TRY(launch_sweep(K, m0, k, stream()));
+    NX_CUDA(cudaEventRecord(S.col_done[b], stream()));
     ++c.launches;
-    NX_CUDA(cudaMemcpyAsync(hv_new + (v0 - S.n_res), g->vstage[1].p, bytes, cudaMemcpyDeviceToHost,
-                            stream()));
+    NX_CUDA(cudaStreamWaitEvent(S.side, S.col_done[b], 0));
+    NX_CUDA(cudaMemcpyAsync(hv_new + (v0 - S.n_res), g->vstage[2 + b].p, bytes,
+                            cudaMemcpyDeviceToHost, S.side));
     c.d2h += bytes;
     if (has_c) {
-      NX_CUDA(cudaMemcpyAsync(hc_new + (v0 - S.n_res), g->vstage[2].p, bytes,
-                              cudaMemcpyDeviceToHost, stream()));
+      NX_CUDA(cudaMemcpyAsync(hc_new + (v0 - S.n_res), g->vstage[4 + b].p, bytes,
+                              cudaMemcpyDeviceToHost, S.side));
       c.d2h += bytes;
     }
+    NX_CUDA(cudaEventRecord(S.col_out[b], S.side));
   }
   g->cur ^= 1;
   return NX_OK;
@@ -846,7 +886,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     S.nh = n - S.n_res;
     S.off = pl.off;
     NX_TRY(ensure(g->accres, std::max<size_t>(S.n_res, 1) * 4));
-    for (int b = 0; b < 4; ++b) NX_TRY(ensure(g->vstage[b], (size_t)L * 4));
+    for (int b = 0; b < 8; ++b) NX_TRY(ensure(g->vstage[b], (size_t)L * 4));
     const bool has_c = (prog == NX_PR || prog == NX_PPR);
     const size_t hbytes = (size_t)S.nh * 4 * (has_c ? 2 : 1);
     for (int b = 0; b < 2; ++b)
@@ -861,6 +901,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
                                 (size_t)S.nh * 4, cudaMemcpyDeviceToHost, stream()));
     }
     NX_CUDA(cudaStreamSynchronize(stream()));
+    NX_TRY(S.init());
   }
 
   // per-interval edge counts (edges streamed by a sweep of active sources)
@@ -885,6 +926,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   if (g->hact.bytes < ((size_t)P + 1) * 4) NX_TRY(g->hact.alloc(((size_t)P + 1) * 4));
   uint32_t* hact = g->hact.as<uint32_t>();
   const uint32_t* act_h = hact + 1;
+  c.act_host = act_h;
   std::fill(hact, hact + P + 1, 1u);
   if (is_min(prog)) {  // the flags Initialize left (later ones arrive with each count)
     NX_CUDA(cudaMemcpyAsync(hact + 1, g->act[g->cur].p, (size_t)P * 4, cudaMemcpyDeviceToHost,
@@ -919,6 +961,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       if (hact[0] == 0) break;
     }
   }
+  if (staged) NX_TRY(S.join());  // the last results reach the host inside the timed region
   NX_CUDA(cudaEventRecord(ev.e1, stream()));
   float ms = 0.f;
   NX_TRY(ev.elapsed(&ms));

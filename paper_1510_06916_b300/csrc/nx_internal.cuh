@@ -196,7 +196,7 @@ struct nx_graph {
   nx::DevBuf lam[2], ybuf;  // adjoint scratch
   float wpr_alpha = 0.85f;  // damping of the last weighted PageRank run
   nx::DevBuf stage[2];      // staging for streamed shards
-  nx::DevBuf vstage[4];     // staging for non-resident intervals (MPU)
+  nx::DevBuf vstage[8];     // staging for non-resident intervals (MPU), double-buffered
   nx::PinnedBuf hval[2];    // pinned host values of non-resident intervals
   nx::PinnedBuf hact;       // pinned host copy of the activity count + flags [P + 1]
   nx::DevBuf accres;        // MPU resident-column accumulators
