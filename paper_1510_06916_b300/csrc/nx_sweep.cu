@@ -15,6 +15,10 @@
 // accumulator to a private slot and the last block to finish (a completion
 // counter) combines the slots in a fixed order, so results do not depend on
 // block scheduling except for the order of shared-memory atomics inside a block.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "nx_sweep.cuh"
 
 namespace nx {
@@ -765,30 +769,67 @@ size_t flat_table_bytes(const SweepArgs& a) {
   return a.flat_cap ? (size_t)(a.flat_cap + 1) * sizeof(FlatEnt) : 0;
 }
 
+const void* sweep_fn(ProgKind kind) {
+  switch (kind) {
+    case PK_PR: return reinterpret_cast<const void*>(k_sweep<PK_PR>);
+    case PK_WPR: return reinterpret_cast<const void*>(k_sweep<PK_WPR>);
+    case PK_BFS: return reinterpret_cast<const void*>(k_sweep<PK_BFS>);
+    case PK_WCC: return reinterpret_cast<const void*>(k_sweep<PK_WCC>);
+    case PK_PRD: return reinterpret_cast<const void*>(k_sweep<PK_PRD>);
+    case PK_ADJ: return reinterpret_cast<const void*>(k_sweep<PK_ADJ>);
+  }
+  return nullptr;
+}
+
+// Function attributes of a sweep kernel for `smem` bytes of dynamic shared
+// memory: the opt-in limit when dynamic + static shared memory pass the 48 KB
+// default, and the smallest shared-memory carveout that still holds the blocks
+// an SM can run (registers limit them to four), so the rest of the unified L1
+// caches the random source gathers. The driver's own choice reserved more:
+// PageRank ran 0-6% slower with it (R-MAT scales 22-26, P = 8-64). The
+// carveout is computed once per (device, kernel, size) and re-applied when the
+// size in use changes (another graph's tiles).
+nx_status configure_sweep(ProgKind kind, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, size_t>, int> pct_of;  // carveout per size
+  static std::map<std::pair<int, int>, int> applied;         // carveout now set
+  int dev = 0;
+  NX_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  const void* fn = sweep_fn(kind);
+  const auto key = std::make_tuple(dev, (int)kind, smem);
+  auto hit = pct_of.find(key);
+  if (hit == pct_of.end()) {
+    if (smem > 40 * 1024)  // the opt-in limit is a per-device function attribute
+      NX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    // occupancy with all of the unified memory available to shared memory
+    NX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    applied[std::make_pair(dev, (int)kind)] = 100;
+    int nb = 0, per_sm = 0;
+    cudaFuncAttributes fa;
+    NX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem));
+    NX_CUDA(cudaFuncGetAttributes(&fa, fn));
+    NX_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    int pct = 100;
+    if (nb > 0 && per_sm > 0) {
+      const uint64_t need = (uint64_t)nb * (smem + fa.sharedSizeBytes + 1024);  // 1 KB reserved per block
+      pct = (int)std::min<uint64_t>(100, ceil_div(100 * need, (uint64_t)per_sm));
+    }
+    hit = pct_of.emplace(key, pct).first;
+  }
+  int& cur = applied[std::make_pair(dev, (int)kind)];
+  if (cur != hit->second) {
+    NX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, hit->second));
+    cur = hit->second;
+  }
+  return NX_OK;
+}
+
 nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaStream_t s) {
   if (nitems == 0) return NX_OK;
   const bool sums = (kind == PK_PR || kind == PK_WPR || kind == PK_PRD || kind == PK_ADJ);
   const size_t smem = (size_t)a.tile_max * (sums ? 8 : 4) + flat_table_bytes(a);
-  if (smem > 40 * 1024) {  // dynamic + static shared memory above the 48 KB default
-    // the opt-in shared-memory limit is a per-device function attribute
-    static bool raised[64][8] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) dev = 0;
-    if (!raised[dev][kind]) {
-      cudaError_t e = cudaSuccess;
-      switch (kind) {
-        case PK_PR: e = cudaFuncSetAttribute(k_sweep<PK_PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
-        case PK_WPR: e = cudaFuncSetAttribute(k_sweep<PK_WPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
-        case PK_BFS: e = cudaFuncSetAttribute(k_sweep<PK_BFS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
-        case PK_WCC: e = cudaFuncSetAttribute(k_sweep<PK_WCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
-        case PK_PRD: e = cudaFuncSetAttribute(k_sweep<PK_PRD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
-        case PK_ADJ: e = cudaFuncSetAttribute(k_sweep<PK_ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); break;
-      }
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
-      raised[dev][kind] = true;
-    }
-  }
+  NX_TRY(configure_sweep(kind, smem));
   switch (kind) {
     case PK_PR: k_sweep<PK_PR><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_WPR: k_sweep<PK_WPR><<<nitems, kThreads, smem, s>>>(a); break;
