@@ -430,6 +430,9 @@ nx_status ppr_batch_impl(nx_graph* g, const float* tele_in, uint32_t B, uint32_t
     else
       NX_CUDA(cudaFuncSetAttribute(k_ppr_batch<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
+  NX_TRY(prefer_l1(BP == 32 ? reinterpret_cast<const void*>(k_ppr_batch<32>)
+                             : reinterpret_cast<const void*>(k_ppr_batch<64>),
+                   kBT, smem));
   EventPair ev;
   NX_TRY(ev.create());
   NX_CUDA(cudaEventRecord(ev.e0, s));

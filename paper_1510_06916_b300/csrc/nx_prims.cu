@@ -197,6 +197,44 @@ nx_status exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint
   return exclusive_scan<uint64_t>(in, out, n, total);
 }
 
+// ---------------------------------------------------------------- L1 carveout
+// Smallest shared-memory carveout that still holds the blocks of `fn` an SM
+// can run with `smem` bytes of dynamic shared memory, so the rest of the
+// unified L1 caches global loads. Computed once per (device, kernel, size)
+// with the whole unified memory offered to shared memory, and re-applied
+// whenever the size in use for the kernel changes.
+nx_status prefer_l1(const void* fn, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, size_t>, int> pct_of;
+  static std::map<std::pair<int, const void*>, int> applied;
+  int dev = 0;
+  NX_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_tuple(dev, fn, smem);
+  auto hit = pct_of.find(key);
+  if (hit == pct_of.end()) {
+    NX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    applied[std::make_pair(dev, fn)] = 100;
+    int nb = 0, per_sm = 0;
+    cudaFuncAttributes fa;
+    NX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem));
+    NX_CUDA(cudaFuncGetAttributes(&fa, fn));
+    NX_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    int pct = 100;
+    if (nb > 0 && per_sm > 0) {
+      const uint64_t need = (uint64_t)nb * (smem + fa.sharedSizeBytes + 1024);  // 1 KB reserved per block
+      pct = (int)std::min<uint64_t>(100, ceil_div(100 * need, (uint64_t)per_sm));
+    }
+    hit = pct_of.emplace(key, pct).first;
+  }
+  int& cur = applied[std::make_pair(dev, fn)];
+  if (cur != hit->second) {
+    NX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, hit->second));
+    cur = hit->second;
+  }
+  return NX_OK;
+}
+
 // ---------------------------------------------------------------- radix sort
 namespace {
 constexpr int RS_THREADS = 256;

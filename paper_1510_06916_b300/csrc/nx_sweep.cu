@@ -15,9 +15,9 @@
 // accumulator to a private slot and the last block to finish (a completion
 // counter) combines the slots in a fixed order, so results do not depend on
 // block scheduling except for the order of shared-memory atomics inside a block.
-#include <map>
 #include <mutex>
-#include <tuple>
+#include <set>
+#include <utility>
 
 #include "nx_sweep.cuh"
 
@@ -783,46 +783,23 @@ const void* sweep_fn(ProgKind kind) {
 
 // Function attributes of a sweep kernel for `smem` bytes of dynamic shared
 // memory: the opt-in limit when dynamic + static shared memory pass the 48 KB
-// default, and the smallest shared-memory carveout that still holds the blocks
-// an SM can run (registers limit them to four), so the rest of the unified L1
-// caches the random source gathers. The driver's own choice reserved more:
-// PageRank ran 0-6% slower with it (R-MAT scales 22-26, P = 8-64). The
-// carveout is computed once per (device, kernel, size) and re-applied when the
-// size in use changes (another graph's tiles).
+// default (per device), and the smallest shared-memory carveout that still
+// holds the blocks an SM can run (registers limit them to four), so the rest
+// of the unified L1 caches the random source gathers. The driver's own choice
+// reserved more: PageRank ran 0-6% slower with it (R-MAT scales 22-26,
+// P = 8-64).
 nx_status configure_sweep(ProgKind kind, size_t smem) {
-  static std::mutex mu;
-  static std::map<std::tuple<int, int, size_t>, int> pct_of;  // carveout per size
-  static std::map<std::pair<int, int>, int> applied;         // carveout now set
-  int dev = 0;
-  NX_CUDA(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lock(mu);
   const void* fn = sweep_fn(kind);
-  const auto key = std::make_tuple(dev, (int)kind, smem);
-  auto hit = pct_of.find(key);
-  if (hit == pct_of.end()) {
-    if (smem > 40 * 1024)  // the opt-in limit is a per-device function attribute
+  if (smem > 40 * 1024) {
+    static std::mutex mu;
+    static std::set<std::pair<int, int>> raised;
+    int dev = 0;
+    NX_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (raised.insert(std::make_pair(dev, (int)kind)).second)
       NX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    // occupancy with all of the unified memory available to shared memory
-    NX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    applied[std::make_pair(dev, (int)kind)] = 100;
-    int nb = 0, per_sm = 0;
-    cudaFuncAttributes fa;
-    NX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem));
-    NX_CUDA(cudaFuncGetAttributes(&fa, fn));
-    NX_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    int pct = 100;
-    if (nb > 0 && per_sm > 0) {
-      const uint64_t need = (uint64_t)nb * (smem + fa.sharedSizeBytes + 1024);  // 1 KB reserved per block
-      pct = (int)std::min<uint64_t>(100, ceil_div(100 * need, (uint64_t)per_sm));
-    }
-    hit = pct_of.emplace(key, pct).first;
   }
-  int& cur = applied[std::make_pair(dev, (int)kind)];
-  if (cur != hit->second) {
-    NX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, hit->second));
-    cur = hit->second;
-  }
-  return NX_OK;
+  return prefer_l1(fn, kThreads, smem);
 }
 
 nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaStream_t s) {
