@@ -41,15 +41,33 @@ nx_status invalid(const std::string& msg);
 cudaStream_t stream();
 
 // ---------------------------------------------------------------- device buffers
+// Device memory from the library's stream-ordered pool (one per device):
+// allocated and freed in the order of the stream that was current at
+// allocation, so buffers of one graph are reused without device-wide
+// synchronisation. A buffer released while another stream is current first
+// waits for the whole device (the older stream may still use it).
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  cudaStream_t owner = nullptr;  // stream current at allocation
+  bool pooled = false;           // false: plain cudaMalloc (no pool on this device)
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), owner(o.owner), pooled(o.pooled) {
+    o.p = nullptr;
+    o.bytes = 0;
+  }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    if (this != &o) {
+      release();
+      p = o.p;
+      bytes = o.bytes;
+      owner = o.owner;
+      pooled = o.pooled;
+      o.p = nullptr;
+      o.bytes = 0;
+    }
     return *this;
   }
   ~DevBuf() { release(); }

@@ -44,15 +44,62 @@ int num_sms() {
 }
 
 // ---------------------------------------------------------------- buffers
+// The pool keeps up to kPoolKeep bytes of freed memory for reuse (graphs built
+// and run one after another reuse it); memory above that goes back to the
+// driver at the next synchronisation.
+static constexpr uint64_t kPoolKeep = 4ull << 30;
+
+static cudaError_t pool_of_current_device(cudaMemPool_t* out) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    e = cudaMemPoolCreate(&pools[dev], &props);
+    if (e != cudaSuccess) {
+      pools[dev] = nullptr;
+      return e;
+    }
+    uint64_t keep = kPoolKeep;
+    e = cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) return e;
+  }
+  *out = pools[dev];
+  return cudaSuccess;
+}
+
 void DevBuf::release() {
-  if (p) cudaFree(p);
+  if (p) {
+    if (!pooled) {
+      cudaFree(p);
+    } else {
+      if (owner != stream()) cudaDeviceSynchronize();  // the allocating stream may still use it
+      cudaFreeAsync(p, stream());
+    }
+  }
   p = nullptr;
   bytes = 0;
 }
 nx_status DevBuf::alloc(size_t n) {
   release();
   if (n == 0) return NX_OK;
-  cudaError_t e = cudaMalloc(&p, n);
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = pool_of_current_device(&pool);
+  pooled = (e == cudaSuccess);
+  if (pooled) {
+    e = cudaMallocFromPoolAsync(&p, n, pool, stream());
+  } else {
+    cudaGetLastError();
+    e = cudaMalloc(&p, n);
+  }
+  owner = stream();
   if (e != cudaSuccess) {
     p = nullptr;
     cudaGetLastError();
