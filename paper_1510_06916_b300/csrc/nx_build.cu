@@ -309,6 +309,26 @@ nx_status build_geometry(nx_graph* g, const uint32_t* deg_a, const uint32_t* deg
   return NX_OK;
 }
 
+// Side stream and events of a chunked host-to-device upload.
+struct Upload {
+  cudaStream_t side = nullptr;
+  cudaEvent_t ready = nullptr;
+  std::vector<cudaEvent_t> copied;
+  ~Upload() {
+    for (cudaEvent_t e : copied)
+      if (e) cudaEventDestroy(e);
+    if (ready) cudaEventDestroy(ready);
+    if (side) cudaStreamDestroy(side);
+  }
+  nx_status init(int chunks) {
+    NX_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    NX_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    copied.assign(chunks, nullptr);
+    for (auto& e : copied) NX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return NX_OK;
+  }
+};
+
 nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t P,
                      uint32_t flags, const float* w, nx_graph* g) {
   const bool on_dev = flags & NX_DEV_PTRS;
@@ -317,34 +337,64 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   EventPair ev;
   NX_TRY(ev.create());
   NX_CUDA(cudaEventRecord(ev.e0, stream()));
-  // device copies of the inputs
+  // Degrees of the input ids can be counted as the edges arrive unless the
+  // ids are renamed first (NX_RELABEL counts them after renaming).
+  const bool early_deg = !(flags & NX_RELABEL);
+  DevBuf indeg, bad;
+  NX_TRY(g->outdeg.alloc((uint64_t)n * 4));
+  NX_TRY(indeg.alloc((uint64_t)n * 4));
+  NX_TRY(bad.alloc(4));
+  NX_CUDA(cudaMemsetAsync(g->outdeg.p, 0, (uint64_t)n * 4, stream()));
+  NX_CUDA(cudaMemsetAsync(indeg.p, 0, (uint64_t)n * 4, stream()));
+  NX_CUDA(cudaMemsetAsync(bad.p, 0, 4, stream()));
+  // per range of edges: ids < n, and the degree histograms
+  auto scan_edges = [&](const uint32_t* s0, const uint32_t* d0, uint64_t len) -> nx_status {
+    k_check_ids<<<grid_for(len), 256, 0, stream()>>>(s0, len, n, bad.as<uint32_t>());
+    k_check_ids<<<grid_for(len), 256, 0, stream()>>>(d0, len, n, bad.as<uint32_t>());
+    if (early_deg) {
+      k_histogram<<<grid_for(len), 256, 0, stream()>>>(s0, len, g->outdeg.as<uint32_t>());
+      k_histogram<<<grid_for(len), 256, 0, stream()>>>(d0, len, indeg.as<uint32_t>());
+    }
+    NX_LAUNCH_CHECK();
+    return NX_OK;
+  };
+  // device copies of host inputs, uploaded in chunks on a side stream so the
+  // checks and histograms of one chunk overlap the copy of the next
   DevBuf ds, dd, dw;
   const uint32_t *s = src, *d = dst;
   const float* wp = w;
   if (!on_dev) {
     NX_TRY(ds.alloc(std::max<uint64_t>(m, 1) * 4));
     NX_TRY(dd.alloc(std::max<uint64_t>(m, 1) * 4));
-    if (m) {
-      NX_CUDA(cudaMemcpyAsync(ds.p, src, m * 4, cudaMemcpyHostToDevice, stream()));
-      NX_CUDA(cudaMemcpyAsync(dd.p, dst, m * 4, cudaMemcpyHostToDevice, stream()));
-    }
+    if (want_w) NX_TRY(dw.alloc(std::max<uint64_t>(m, 1) * 4));
     s = ds.as<uint32_t>();
     d = dd.as<uint32_t>();
-    if (want_w) {
-      NX_TRY(dw.alloc(std::max<uint64_t>(m, 1) * 4));
-      if (m) NX_CUDA(cudaMemcpyAsync(dw.p, w, m * 4, cudaMemcpyHostToDevice, stream()));
-      wp = dw.as<float>();
+    if (want_w) wp = dw.as<float>();
+    if (m) {
+      constexpr int kChunks = 8;
+      Upload up;
+      NX_TRY(up.init(kChunks));
+      NX_CUDA(cudaEventRecord(up.ready, stream()));  // the buffers exist in stream order
+      NX_CUDA(cudaStreamWaitEvent(up.side, up.ready, 0));
+      const uint64_t chunk = round_up(ceil_div(m, kChunks), 1024);
+      for (int c = 0; c < kChunks && (uint64_t)c * chunk < m; ++c) {
+        const uint64_t e0 = (uint64_t)c * chunk, len = std::min<uint64_t>(chunk, m - e0);
+        NX_CUDA(cudaMemcpyAsync(ds.as<uint32_t>() + e0, src + e0, len * 4, cudaMemcpyHostToDevice, up.side));
+        NX_CUDA(cudaMemcpyAsync(dd.as<uint32_t>() + e0, dst + e0, len * 4, cudaMemcpyHostToDevice, up.side));
+        NX_CUDA(cudaEventRecord(up.copied[c], up.side));
+        NX_CUDA(cudaStreamWaitEvent(stream(), up.copied[c], 0));
+        NX_TRY(scan_edges(s + e0, d + e0, len));
+      }
+      if (want_w) {
+        NX_CUDA(cudaMemcpyAsync(dw.p, w, m * 4, cudaMemcpyHostToDevice, up.side));
+        NX_CUDA(cudaEventRecord(up.ready, up.side));
+        NX_CUDA(cudaStreamWaitEvent(stream(), up.ready, 0));
+      }
     }
+  } else if (m) {
+    NX_TRY(scan_edges(s, d, m));
   }
   {  // ids < n
-    DevBuf bad;
-    NX_TRY(bad.alloc(4));
-    NX_CUDA(cudaMemsetAsync(bad.p, 0, 4, stream()));
-    if (m) {
-      k_check_ids<<<grid_for(m), 256, 0, stream()>>>(s, m, n, bad.as<uint32_t>());
-      k_check_ids<<<grid_for(m), 256, 0, stream()>>>(d, m, n, bad.as<uint32_t>());
-      NX_LAUNCH_CHECK();
-    }
     uint32_t hb = 0;
     NX_CUDA(cudaMemcpyAsync(&hb, bad.p, 4, cudaMemcpyDeviceToHost, stream()));
     NX_CUDA(cudaStreamSynchronize(stream()));
@@ -366,22 +416,16 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
     NX_TRY(relabel_edges(g, s, d, m, so, dout));
     s = so;
     d = dout;
+    if (m) {  // degrees of the renamed ids
+      k_histogram<<<grid_for(m), 256, 0, stream()>>>(s, m, g->outdeg.as<uint32_t>());
+      k_histogram<<<grid_for(m), 256, 0, stream()>>>(d, m, indeg.as<uint32_t>());
+      NX_LAUNCH_CHECK();
+    }
   }
   geo.P = P;
   geo.L = (uint32_t)ceil_div(n, P);
   geo.lb = bits_for(geo.L);
   geo.tile_max = (uint32_t)std::min<uint64_t>(kTileMaxCap, 1ull << (32 - geo.lb));
-  // degrees
-  DevBuf indeg;
-  NX_TRY(g->outdeg.alloc((uint64_t)n * 4));
-  NX_TRY(indeg.alloc((uint64_t)n * 4));
-  NX_CUDA(cudaMemsetAsync(g->outdeg.p, 0, (uint64_t)n * 4, stream()));
-  NX_CUDA(cudaMemsetAsync(indeg.p, 0, (uint64_t)n * 4, stream()));
-  if (m) {
-    k_histogram<<<grid_for(m), 256, 0, stream()>>>(s, m, g->outdeg.as<uint32_t>());
-    k_histogram<<<grid_for(m), 256, 0, stream()>>>(d, m, indeg.as<uint32_t>());
-    NX_LAUNCH_CHECK();
-  }
   DevBuf tile_of;
   NX_TRY(build_geometry(g, indeg.as<uint32_t>(), want_t ? g->outdeg.as<uint32_t>() : nullptr,
                         want_t ? 2 * m : m, tile_of));
