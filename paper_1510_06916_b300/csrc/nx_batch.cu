@@ -8,9 +8,11 @@
 // binary-searches the sub-tile's range inside piece (i, t) (edges are sorted
 // by destination inside a piece) and its warps walk those edges 32 at a time:
 // lane l loads edge word l, then the warp broadcasts each edge and gathers the
-// source row cooperatively (lane l holds columns [l*Bp/32, (l+1)*Bp/32)). Runs
-// of equal destination accumulate in registers (compensated) and are flushed
-// to the shared-memory row of that destination with one atomic per column.
+// source row with 16-byte loads by Bp/4 lanes, so one warp instruction serves
+// 2 (Bp = 64) or 4 (Bp = 32) edges. Runs of equal destination accumulate in
+// registers (at most the edges of one lane group in a 32-edge chunk) and are
+// flushed to the shared-memory row of that destination with one atomic per
+// column.
 //
 //   r'[v][b] = (1-a) t[v][b] + a (sum_{u->v} c[u][b] + Dm[b] t[v][b]),
 //   c'[v][b] = r'[v][b] / outdeg(v) (0 if dangling), Dm[b] = sum_{dangling} r[v][b].
@@ -72,9 +74,23 @@ __device__ __forceinline__ uint64_t lower_key(const uint32_t* __restrict__ ew, u
   return p0;
 }
 
+// Lanes per edge: a BP-float row is read with 16-byte loads by LPE = BP / 4
+// lanes, so a warp works on 32 / LPE edges at once. In shared memory, column b
+// of a destination row is stored at (b % 4) * LPE + b / 4: the q-th component
+// of the float4 of lane gl goes to q * LPE + gl, so the lanes of one group add
+// into consecutive words.
+template <int BP>
+__device__ __forceinline__ uint32_t acc_pos(uint32_t b) {
+  return (b % 4) * (BP / 4) + b / 4;
+}
+
 template <int BP>
 __global__ void __launch_bounds__(kBT) k_ppr_batch(const BArgs a) {
-  constexpr int C = BP / 32;  // columns per lane
+  constexpr int C = BP / 32;   // columns per lane in the epilogue
+  constexpr int LPE = BP / 4;  // lanes per edge in the sweep
+  constexpr int NG = 32 / LPE; // edge groups per warp
+  constexpr int EPG = 32 / NG; // chunk edges per group
+  static_assert(EPG % kRows == 0, "kRows must divide the edges of a group");
   extern __shared__ __align__(16) unsigned char smem[];
   float* acc = reinterpret_cast<float*>(smem);                          // [kSub][BP]
   uint64_t* rlo = reinterpret_cast<uint64_t*>(acc + kSub * BP);          // [P]
@@ -89,6 +105,13 @@ __global__ void __launch_bounds__(kBT) k_ppr_batch(const BArgs a) {
   const uint32_t k1 = min(k0 + kSub, te - ts);
   const uint32_t nrows = k1 - k0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPE, gl = lane % LPE;
+  auto flush = [&](float* arow, const float4 v) {
+    atomicAdd(arow + gl, v.x);
+    atomicAdd(arow + LPE + gl, v.y);
+    atomicAdd(arow + 2 * LPE + gl, v.z);
+    atomicAdd(arow + 3 * LPE + gl, v.w);
+  };
   for (uint32_t q = threadIdx.x; q < kSub * BP; q += kBT) acc[q] = 0.f;
   // sub-tile range inside every piece (i, t)
   for (uint32_t i = threadIdx.x; i < a.P; i += kBT) {
@@ -128,49 +151,40 @@ __global__ void __launch_bounds__(kBT) k_ppr_batch(const BArgs a) {
       const uint32_t w = e < e1 ? __ldcs(a.ew + e) : 0xFFFFFFFFu;
       const uint64_t left = e1 - (e0 + (uint64_t)ch * 32);
       const uint32_t cnt = left < 32 ? (uint32_t)left : 32u;
-      float s[C], cmp[C];
+      // group grp takes the chunk's edges [grp * EPG, (grp + 1) * EPG); a run in
+      // registers spans at most those edges: plain sums
+      float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
       uint32_t curk = 0xFFFFFFFFu;
-#pragma unroll
-      for (int q = 0; q < C; ++q) s[q] = cmp[q] = 0.f;
-      for (uint32_t x = 0; x < cnt; x += kRows) {
-        float row[kRows][C];
+      const uint32_t g0 = (uint32_t)grp * EPG;
+      for (uint32_t x = 0; x < (uint32_t)EPG; x += kRows) {
+        float4 row[kRows];
         uint32_t key[kRows];
 #pragma unroll
-        for (int y = 0; y < kRows; ++y) {  // kRows rows in flight
-          const uint32_t wy = __shfl_sync(0xffffffffu, w, (x + y) & 31);
-          const bool ok = x + y < cnt;
+        for (int y = 0; y < kRows; ++y) {  // kRows rows in flight per group
+          const uint32_t ce = g0 + x + y;
+          const uint32_t wy = __shfl_sync(0xffffffffu, w, ce);
+          const bool ok = ce < cnt;
           key[y] = ok ? (wy >> a.lb) - k0 : 0xFFFFFFFFu;
-          const float* src = a.c_in + (size_t)(sbase + (wy & smask)) * BP + lane * C;
-#pragma unroll
-          for (int q = 0; q < C; ++q) row[y][q] = ok ? __ldg(src + q) : 0.f;
+          const float4* src = reinterpret_cast<const float4*>(
+              a.c_in + (size_t)(sbase + (wy & smask)) * BP + gl * 4);
+          row[y] = ok ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int y = 0; y < kRows; ++y) {
           if (key[y] == 0xFFFFFFFFu) continue;
           if (key[y] != curk) {
-            if (curk != 0xFFFFFFFFu)
-#pragma unroll
-              for (int q = 0; q < C; ++q) atomicAdd(acc + curk * BP + lane * C + q, s[q] + cmp[q]);
+            if (curk != 0xFFFFFFFFu) flush(acc + curk * BP, sum);
             curk = key[y];
-#pragma unroll
-            for (int q = 0; q < C; ++q) {
-              s[q] = row[y][q];
-              cmp[q] = 0.f;
-            }
+            sum = row[y];
           } else {
-#pragma unroll
-            for (int q = 0; q < C; ++q) {  // Kahan-Babuska (Neumaier) step
-              const float tq = s[q] + row[y][q];
-              cmp[q] += fabsf(s[q]) >= fabsf(row[y][q]) ? (s[q] - tq) + row[y][q]
-                                                         : (row[y][q] - tq) + s[q];
-              s[q] = tq;
-            }
+            sum.x += row[y].x;
+            sum.y += row[y].y;
+            sum.z += row[y].z;
+            sum.w += row[y].w;
           }
         }
       }
-      if (curk != 0xFFFFFFFFu)
-#pragma unroll
-        for (int q = 0; q < C; ++q) atomicAdd(acc + curk * BP + lane * C + q, s[q] + cmp[q]);
+      if (curk != 0xFFFFFFFFu) flush(acc + curk * BP, sum);
     }
   }
   __syncthreads();
@@ -204,7 +218,7 @@ __global__ void __launch_bounds__(kBT) k_ppr_batch(const BArgs a) {
     for (int q = 0; q < C; ++q) {
       const size_t o = (size_t)v * BP + lane * C + q;
       // the teleport terms are added afterwards at the seed entries
-      const float r = al * acc[rr * BP + lane * C + q];
+      const float r = al * acc[rr * BP + acc_pos<BP>(lane * C + q)];
       if (a.write_r) a.r_out[o] = r;
       a.c_out[o] = od ? r / (float)od : 0.0f;
       if (od == 0) dang[q] += (double)r;
