@@ -390,6 +390,8 @@ def main():
                     choices=["ppr_batch", "adjoint", "multi_graph", "autotune", "strategies",
                              "budget_sweep", "relabel"],
                     help="diagnostic: run one extra measurement and print it (for profiling)")
+    ap.add_argument("--batch-scale", type=int, default=24,
+                    help="R-MAT scale of the batched-PPR measurement (profiling uses 22)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -407,7 +409,11 @@ def main():
                  "relabel": measure_relabel}
     if args.extras_only:
         nx.set_stream(torch.cuda.current_stream())
-        out = extra_fns[args.extras_only](nx, inputs, torch)
+        fn = extra_fns[args.extras_only]
+        if args.extras_only == "ppr_batch":
+            out = fn(nx, inputs, torch, scale=args.batch_scale)
+        else:
+            out = fn(nx, inputs, torch)
         if rank == 0:
             print(json.dumps({"extras_only": args.extras_only, "result": out}), flush=True)
         return 0
