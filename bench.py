@@ -458,11 +458,15 @@ def main():
     ms_per_step = ms_max / args.steps
     value = aggregate_gteps(m, iters, args.steps, world, ms_max)
 
-    # roofline of the sweep kernel: algorithmic bytes per launch / launch time
-    bytes_per_launch = 4 * m + 16 * n
-    t_launch = kern_ms / 1e3 / launches
+    # roofline of the sweep kernel: algorithmic bytes of one sweep (one PageRank
+    # iteration) / the sweep's kernel time. A sweep is one launch, or one launch
+    # per band of source intervals when the value array exceeds 128 MB and
+    # P >= 32 (the bands share the sweep's bytes).
+    sweeps = args.steps * iters
+    bytes_per_sweep = 4 * m + 16 * n
+    t_sweep = kern_ms / 1e3 / sweeps
     peak, peak_kind = load_peaks()
-    achieved = bytes_per_launch / t_launch / 1e9
+    achieved = bytes_per_sweep / t_sweep / 1e9
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):  # only while the profiled kernel source is unchanged
@@ -498,14 +502,17 @@ def main():
         dt = barrier_max(dt, world)
         e2e = {"value": m * iters * world / dt / 1e9, "unit": "GTEPS",
                "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 4 * n,
-               "ms_per_step": dt * 1e3, "includes": "DSSS build from host edges + 20 iterations + values to host"}
+               "ms_per_step": dt * 1e3,
+               "includes": f"DSSS build from host edges + {iters} iterations + values to host"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            v, cores, dt = cpu_oracle_sample(w, 2)
+            # about 3 s at scale 22; one iteration (plus its CSR build) above 2^30 edges
+            n_it = 1 if m > (1 << 30) else 2
+            v, cores, dt = cpu_oracle_sample(w, n_it)
             cpu = {"value": v, "unit": "GTEPS", "cores": cores, "kind": "oracle",
-                   "sample": f"2 PageRank iterations (incl. CSR build) of the full graph, {dt:.1f} s"}
+                   "sample": f"{n_it} PageRank iteration(s) (incl. CSR build) of the full graph, {dt:.1f} s"}
         except Exception as e:  # pragma: no cover
             cpu = {"value": None, "unit": "GTEPS", "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
 
@@ -532,8 +539,10 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "kernel": "k_sweep<PR> (SPU sweep + fused epilogue)",
-                         "algorithmic_bytes_per_launch": bytes_per_launch,
-                         "launch_ms": t_launch * 1e3},
+                         "algorithmic_bytes_per_launch": bytes_per_sweep * sweeps // launches,
+                         "launches_per_sweep": launches / sweeps,
+                         "launch_ms": kern_ms / launches,
+                         "sweep_ms": t_sweep * 1e3},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
