@@ -474,12 +474,13 @@ def main():
     achieved = bytes_per_sweep / t_sweep / 1e9
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):  # only while the profiled kernel source is unchanged
+    if os.path.exists(prof):  # only while the kernel and its launch code are unchanged
         try:
             import hashlib
             ent = json.load(open(prof)).get(args.workload)
-            src = open(os.path.join(ROOT, ent["source"]), "rb").read()
-            if hashlib.sha256(src).hexdigest() == ent["source_sha256"]:
+            same = all(hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() == h
+                       for f, h in ent["sources_sha256"].items())
+            if same and ent["sources_sha256"]:
                 traffic = ent["bytes_per_launch"]
         except Exception:
             traffic = None

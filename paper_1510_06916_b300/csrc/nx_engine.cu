@@ -302,10 +302,12 @@ SweepArgs base_args(nx_graph* g, nx_program prog, const nx_params& p, const floa
     a.hub_dst[1] = g->tr.hub_dst.as<uint16_t>();
     a.hubs[1] = g->hubs_t.p;
   }
-  // Flattened step schedule: measured faster for BFS / WCC (short, activity-
-  // filtered pieces), slightly slower for the PageRank family on one graph.
+  // Flattened step schedule (a tile's pieces as one sequence of warp steps):
+  // measured faster for every program once the shared-memory carveout leaves
+  // L1 to the gathers -- PageRank at R-MAT scale 26 by 3% (P = 16) to 16%
+  // (P = 64), where pieces are short; BFS / WCC skip inactive pieces in it.
   const uint32_t npieces = (uint32_t)a.nsrc * g->geo.P;
-  a.flat_cap = (is_min(prog) && npieces <= 256) ? npieces : 0;
+  a.flat_cap = npieces <= 256 ? npieces : 0;
   return a;
 }
 
