@@ -299,7 +299,10 @@ nx_status nx_autotune(const uint32_t* src, const uint32_t* dst, uint64_t m, uint
 /* Planner model of Section III-B (Table II): bytes read / written per
  * iteration for strategy s with n vertices, m edges, P intervals, budget B_M,
  * attribute/id/edge sizes B_a, B_v, B_e and average hub in-degree d.
- * Q (resident intervals) = min(P, floor(B_M * P / (2 n B_a))) for MPU. */
+ * Q (resident intervals) = min(P, floor(B_M * P / (2 n B_a))) for MPU.
+ * Host arithmetic only (no device is touched).
+ * Errors: INVALID_ARG (n, P, B_a or d not positive; a strategy other than
+ * SPU, DPU, MPU or AUTO, which the paper's model does not cover). */
 nx_status nx_io_model(nx_strategy s, double n, double m, double P, double B_M, double B_a,
                       double B_v, double B_e, double d, double* Q, double* bytes_read,
                       double* bytes_write);

@@ -196,7 +196,7 @@ nx_status prepare(nx_graph* g) {
   return NX_OK;
 }
 
-nx_status upload_items(nx_graph* g, const PlanOut& plan, nx_graph::Plan& dst) {
+nx_status upload_items(nx_graph*, const PlanOut& plan, nx_graph::Plan& dst) {
   NX_TRY(dst.items.alloc(std::max<size_t>(plan.items.size(), 1) * sizeof(Item)));
   if (!plan.items.empty())
     NX_CUDA(cudaMemcpyAsync(dst.items.p, plan.items.data(), plan.items.size() * sizeof(Item),
@@ -1444,6 +1444,8 @@ extern "C" nx_status nx_io_model(nx_strategy s, double n, double m, double P, do
       wr = f * f * m * (B_a + B_v) / d + f * n * B_a;
       break;
     }
+    default:  // the Table IV ablation strategies have no I/O model in the paper
+      return nx::invalid("nx_io_model: the model covers SPU, DPU, MPU and AUTO only");
   }
   if (Q) *Q = q;
   if (bytes_read) *bytes_read = rd;

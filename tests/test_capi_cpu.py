@@ -95,3 +95,11 @@ def test_strategy_names_cover_the_ablation():
     hdr = open(HDR).read()
     assert re.search(r"NX_SRC_COARSE\s*=\s*4", hdr) and re.search(r"NX_SRC_FINE\s*=\s*5", hdr)
     assert re.search(r"#define NX_RELABEL 8u", hdr) and nx.RELABEL == 8
+
+
+def test_io_model_rejects_strategies_it_does_not_model():
+    # Table II covers SPU, DPU and MPU; the ablation strategies and junk values are refused
+    for s in (nx.SRC_COARSE, nx.SRC_FINE, 99):
+        with pytest.raises(nx.NxError) as e:
+            nx.io_model(s, 1e6, 1e7, 16, 1e8)
+        assert e.value.code == nx.NX_ERR_INVALID_ARG
