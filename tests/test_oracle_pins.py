@@ -124,6 +124,31 @@ def test_ppr_uniform_teleport_equals_pagerank():
                   - oracle.pagerank(n, s, d, ALPHA, 30)).max() < 1e-15
 
 
+@pytest.mark.parametrize("iters", [1, 7, 30])
+def test_ppr_is_linear_in_the_teleport_without_dangling_vertices(iters):
+    # With every vertex holding an out-edge there is no dangling mass, so each
+    # step r' = (1-a) t + a Pt r (from r0 = t) is linear in t: the result for a
+    # mix of two teleports is the same mix of their results. (With dangling
+    # vertices the term Dm(r) t is bilinear and this does not hold.)
+    n = 500
+    s, d = _rand_graph(n, 3000, 11)
+    ring_s = np.arange(n, dtype=np.uint32)
+    ring_d = ((np.arange(n) + 1) % n).astype(np.uint32)
+    s, d = np.concatenate([s, ring_s]), np.concatenate([d, ring_d])
+    rng = np.random.default_rng(5)
+    t1 = np.zeros(n)
+    t1[rng.choice(n, 3, replace=False)] = 1.0 / 3
+    t2 = rng.random(n)
+    t2 /= t2.sum()
+    # weights that do not sum to one, so a constant term (an affine map) fails too
+    beta, gamma = 0.3, 1.1
+    mix = oracle.personalized_pagerank(n, s, d, beta * t1 + gamma * t2, ALPHA, iters)
+    r1 = oracle.personalized_pagerank(n, s, d, t1, ALPHA, iters)
+    r2 = oracle.personalized_pagerank(n, s, d, t2, ALPHA, iters)
+    assert np.abs(mix - (beta * r1 + gamma * r2)).max() < 1e-15
+    assert abs(mix.sum() - (beta + gamma)) < 1e-12  # no dangling vertex: mass is kept
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_ppr_fixed_point_dense(seed):
     # With dangling mass spread by t the fixed point is x / sum(x),
