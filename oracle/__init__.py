@@ -12,6 +12,11 @@ Functions and the passage each follows:
 * ``bfs`` — Algorithms 2-4 (root depth 0, others infinity, min depth+1).
 * ``wcc`` — weakly connected components, min vertex id per component
   (Section IV-D names WCC; undirected = both directions, Section II-A).
+* ``scc`` — strongly connected components, min vertex id per component
+  (Section IV-D names SCC), by Tarjan's depth-first search.
+* ``bfs_max_depth`` — Algorithm 4's Output: the largest finite depth.
+* ``PreparedPageRank`` — the ``pagerank`` arithmetic with its CSR built once,
+  so that the iteration loop can be timed on its own.
 * ``wpr_adjoint`` — adjoint of weighted PageRank (an extension; the paper has
   no counterpart), the Neumann-series fixed-point formula in nx_oracle.c.
 * ``dsss_order`` — the Destination-Sorted Sub-Shard layout of Section II-A and
@@ -56,9 +61,15 @@ def _load():
         lib.orc_pagerank.argtypes = [u32, u64, vp, vp, vp, dbl, u32, vp, i32, vp, vp]
         lib.orc_bfs.argtypes = [u32, u64, vp, vp, u32, vp]
         lib.orc_wcc.argtypes = [u32, u64, vp, vp, vp]
+        lib.orc_scc.argtypes = [u32, u64, vp, vp, vp]
+        lib.orc_pr_prepare.argtypes = [u32, u64, vp, vp, vp, ctypes.POINTER(vp)]
+        lib.orc_pr_iterate.argtypes = [vp, dbl, u32, vp, i32, vp, vp]
+        lib.orc_pr_release.argtypes = [vp]
+        lib.orc_pr_release.restype = None
         lib.orc_wpr_adjoint.argtypes = [u32, u64, vp, vp, vp, dbl, u32, u32, vp, vp, vp, vp,
                                         vp, vp]
-        for f in (lib.orc_pagerank, lib.orc_bfs, lib.orc_wcc, lib.orc_wpr_adjoint):
+        for f in (lib.orc_pagerank, lib.orc_bfs, lib.orc_wcc, lib.orc_scc, lib.orc_wpr_adjoint,
+                  lib.orc_pr_prepare, lib.orc_pr_iterate):
             f.restype = i32
         _lib = lib
     return _lib
@@ -114,6 +125,54 @@ def wcc(n, src, dst) -> np.ndarray:
     if _load().orc_wcc(n, len(src), _ptr(src), _ptr(dst), _ptr(out)):
         raise ValueError("orc_wcc: bad arguments")
     return out
+
+
+def scc(n, src, dst) -> np.ndarray:
+    src, dst = _u32(src), _u32(dst)
+    out = np.empty(n, dtype=np.uint32)
+    if _load().orc_scc(n, len(src), _ptr(src), _ptr(dst), _ptr(out)):
+        raise ValueError("orc_scc: bad arguments")
+    return out
+
+
+def bfs_max_depth(depth) -> int:
+    """Algorithm 4 (Output): the largest finite depth (-1 if none is finite)."""
+    depth = np.asarray(depth, dtype=np.uint32)
+    fin = depth[depth != INF]
+    return int(fin.max()) if len(fin) else -1
+
+
+class PreparedPageRank:
+    """PageRank-family problem with the oracle's CSR built once (same
+    arithmetic as :func:`pagerank`); ``iterate`` runs only the iteration loop."""
+
+    def __init__(self, n, src, dst, w=None):
+        src, dst = _u32(src), _u32(dst)
+        w = _f64(w)
+        self.n = n
+        self._h = ctypes.c_void_p()
+        if _load().orc_pr_prepare(n, len(src), _ptr(src), _ptr(dst), _ptr(w),
+                                  ctypes.byref(self._h)):
+            raise ValueError("orc_pr_prepare: bad arguments or out of memory")
+
+    def iterate(self, alpha=0.85, iters=20, tele=None, dangling_by_tele=False, r0=None):
+        tele, r0 = _f64(tele), _f64(r0)
+        out = np.empty(self.n, dtype=np.float64)
+        if _load().orc_pr_iterate(self._h, alpha, iters, _ptr(tele), int(dangling_by_tele),
+                                  _ptr(r0), _ptr(out)):
+            raise ValueError("orc_pr_iterate: bad arguments")
+        return out
+
+    def close(self):
+        if self._h:
+            _load().orc_pr_release(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def wpr_adjoint(n, src, dst, w, g, alpha=0.85, fwd_iters=50, adj_terms=50, tele=None):

@@ -23,6 +23,8 @@
  *     depth(v) = min over in-edges of depth(u) + 1 — here by a FIFO queue.
  *   WCC: label(v) = the smallest vertex id in v's weakly connected component
  *     (edges taken in both directions, Section II-A) — here by union-find.
+ *   SCC: label(v) = the smallest vertex id in v's strongly connected component
+ *     (Section IV-D) — here by Tarjan's depth-first search.
  *   Weighted-PageRank adjoint: lambda^0 = g, lambda' = M^T lambda + g with
  *     (M^T lambda)_u = alpha ( sum_v p_uv lambda_v + d_u (sum_v lambda_v)/n ),
  *     dL/dt = (1-alpha) lambda,
@@ -38,7 +40,8 @@
 #define ORC_INF 0xFFFFFFFFu
 
 /* In-edge CSR by destination: off[n+1], nbr[m] (sources), eid[m] (input edge
- * index), built by a counting sort that keeps input order within a vertex. */
+ * index, built only when asked for), by a counting sort that keeps input order
+ * within a vertex. */
 typedef struct {
   uint64_t* off;
   uint32_t* nbr;
@@ -56,12 +59,12 @@ static void csr_free(orc_csr* c) {
 
 /* key[e] picks the bucket (dst for in-CSR, src for out-CSR); val[e] is stored. */
 static int csr_build(uint32_t n, uint64_t m, const uint32_t* key, const uint32_t* val,
-                     orc_csr* c) {
+                     int with_eid, orc_csr* c) {
   c->off = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
   c->nbr = (uint32_t*)malloc((size_t)(m ? m : 1) * sizeof(uint32_t));
-  c->eid = (uint64_t*)malloc((size_t)(m ? m : 1) * sizeof(uint64_t));
+  c->eid = with_eid ? (uint64_t*)malloc((size_t)(m ? m : 1) * sizeof(uint64_t)) : NULL;
   uint64_t* fill = (uint64_t*)malloc(((size_t)n + 1) * sizeof(uint64_t));
-  if (!c->off || !c->nbr || !c->eid || !fill) {
+  if (!c->off || !c->nbr || (with_eid && !c->eid) || !fill) {
     free(fill);
     csr_free(c);
     return -1;
@@ -72,7 +75,7 @@ static int csr_build(uint32_t n, uint64_t m, const uint32_t* key, const uint32_t
   for (uint64_t e = 0; e < m; ++e) {
     uint64_t k = fill[key[e]]++;
     c->nbr[k] = val[e];
-    c->eid[k] = e;
+    if (c->eid) c->eid[k] = e;
   }
   free(fill);
   return 0;
@@ -114,6 +117,85 @@ static void pr_step(uint32_t n, const orc_csr* in, const double* w, const double
 }
 
 /*
+ * A prepared PageRank problem: the in-edge CSR and out-weights built once, so
+ * that a caller can time the iteration loop alone (the build is not part of
+ * an iteration). The arithmetic of each step is pr_step above.
+ */
+typedef struct {
+  uint32_t n;
+  uint64_t m;
+  orc_csr in;
+  double* w; /* copy of the weights (NULL: unweighted) */
+  double* W;
+} orc_pr_problem;
+
+void orc_pr_release(void* h) {
+  orc_pr_problem* p = (orc_pr_problem*)h;
+  if (!p) return;
+  csr_free(&p->in);
+  free(p->w);
+  free(p->W);
+  free(p);
+}
+
+/* Builds the problem for edges src/dst (and weights w, nullable); *out
+ * receives the handle (release with orc_pr_release). */
+int orc_pr_prepare(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                   const double* w, void** out) {
+  *out = NULL;
+  if (check_edges(n, m, src, dst)) return -1;
+  orc_pr_problem* p = (orc_pr_problem*)calloc(1, sizeof(orc_pr_problem));
+  if (!p) return -1;
+  p->n = n;
+  p->m = m;
+  if (csr_build(n, m, dst, src, w != NULL, &p->in)) {
+    free(p);
+    return -1;
+  }
+  if (w) {
+    p->w = (double*)malloc((size_t)(m ? m : 1) * sizeof(double));
+    if (!p->w) {
+      orc_pr_release(p);
+      return -1;
+    }
+    memcpy(p->w, w, (size_t)m * sizeof(double));
+  }
+  p->W = out_weight(n, m, src, w);
+  if (!p->W) {
+    orc_pr_release(p);
+    return -1;
+  }
+  *out = p;
+  return 0;
+}
+
+/* `iters` synchronous steps of a prepared problem from r0 (NULL: 1/n). */
+int orc_pr_iterate(void* h, double alpha, uint32_t iters, const double* tele,
+                   int dangling_by_tele, const double* r0, double* r_out) {
+  orc_pr_problem* p = (orc_pr_problem*)h;
+  if (!p) return -1;
+  const uint32_t n = p->n;
+  double* a = (double*)malloc((size_t)n * sizeof(double));
+  double* b = (double*)malloc((size_t)n * sizeof(double));
+  if (!a || !b) {
+    free(a);
+    free(b);
+    return -1;
+  }
+  for (uint32_t v = 0; v < n; ++v) a[v] = r0 ? r0[v] : 1.0 / (double)n;
+  for (uint32_t it = 0; it < iters; ++it) {
+    pr_step(n, &p->in, p->w, p->W, alpha, tele, dangling_by_tele, a, b);
+    double* t = a;
+    a = b;
+    b = t;
+  }
+  memcpy(r_out, a, (size_t)n * sizeof(double));
+  free(a);
+  free(b);
+  return 0;
+}
+
+/*
  * PageRank / personalized PageRank / weighted PageRank, `iters` synchronous
  * steps from r0 (NULL: uniform 1/n). w may be NULL (unweighted); tele may be
  * NULL (uniform teleport 1/n). Result in r_out[n].
@@ -121,32 +203,11 @@ static void pr_step(uint32_t n, const orc_csr* in, const double* w, const double
 int orc_pagerank(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
                  const double* w, double alpha, uint32_t iters, const double* tele,
                  int dangling_by_tele, const double* r0, double* r_out) {
-  if (check_edges(n, m, src, dst)) return -1;
-  orc_csr in;
-  if (csr_build(n, m, dst, src, &in)) return -1;
-  double* W = out_weight(n, m, src, w);
-  double* a = (double*)malloc((size_t)n * sizeof(double));
-  double* b = (double*)malloc((size_t)n * sizeof(double));
-  if (!W || !a || !b) {
-    free(W);
-    free(a);
-    free(b);
-    csr_free(&in);
-    return -1;
-  }
-  for (uint32_t v = 0; v < n; ++v) a[v] = r0 ? r0[v] : 1.0 / (double)n;
-  for (uint32_t it = 0; it < iters; ++it) {
-    pr_step(n, &in, w, W, alpha, tele, dangling_by_tele, a, b);
-    double* t = a;
-    a = b;
-    b = t;
-  }
-  memcpy(r_out, a, (size_t)n * sizeof(double));
-  free(W);
-  free(a);
-  free(b);
-  csr_free(&in);
-  return 0;
+  void* h = NULL;
+  if (orc_pr_prepare(n, m, src, dst, w, &h)) return -1;
+  int rc = orc_pr_iterate(h, alpha, iters, tele, dangling_by_tele, r0, r_out);
+  orc_pr_release(h);
+  return rc;
 }
 
 /* BFS depths from `root` over directed edges (Algorithms 2-4). */
@@ -154,7 +215,7 @@ int orc_bfs(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst, ui
             uint32_t* depth) {
   if (check_edges(n, m, src, dst) || root >= n) return -1;
   orc_csr out;
-  if (csr_build(n, m, src, dst, &out)) return -1;
+  if (csr_build(n, m, src, dst, 0, &out)) return -1;
   uint32_t* queue = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
   if (!queue) {
     csr_free(&out);
@@ -208,6 +269,94 @@ int orc_wcc(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst, ui
 }
 
 /*
+ * SCC labels (Section IV-D names strongly connected components among its
+ * tasks without giving an algorithm): label(v) = the smallest vertex id of the
+ * strongly connected component holding v, u and v sharing a component when
+ * each reaches the other along directed edges. Computed by Tarjan's algorithm
+ * (Tarjan 1972, "Depth-first search and linear graph algorithms"), written
+ * with an explicit stack instead of recursion: a vertex is the root of a
+ * component when no vertex reached from it in the depth-first search leads
+ * back to a vertex discovered before it; the component is then popped from
+ * the stack of visited, unassigned vertices.
+ */
+int orc_scc(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst, uint32_t* label) {
+  if (check_edges(n, m, src, dst)) return -1;
+  orc_csr out;
+  if (csr_build(n, m, src, dst, 0, &out)) return -1;
+  uint32_t* index = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t* low = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t* stk = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));    /* visited, unassigned */
+  uint32_t* cs_v = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));   /* DFS path: vertex    */
+  uint64_t* cs_e = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));   /* next out-edge       */
+  unsigned char* on = (unsigned char*)calloc(n, 1);
+  if (!index || !low || !stk || !cs_v || !cs_e || !on) {
+    free(index);
+    free(low);
+    free(stk);
+    free(cs_v);
+    free(cs_e);
+    free(on);
+    csr_free(&out);
+    return -1;
+  }
+  for (uint32_t v = 0; v < n; ++v) index[v] = ORC_INF;
+  uint32_t next = 0, sp = 0;
+  for (uint32_t r = 0; r < n; ++r) {
+    if (index[r] != ORC_INF) continue;
+    uint32_t depth = 0;
+    cs_v[0] = r;
+    cs_e[0] = out.off[r];
+    index[r] = low[r] = next++;
+    stk[sp++] = r;
+    on[r] = 1;
+    depth = 1;
+    while (depth) {
+      const uint32_t u = cs_v[depth - 1];
+      if (cs_e[depth - 1] < out.off[u + 1]) {
+        const uint32_t v = out.nbr[cs_e[depth - 1]++];
+        if (index[v] == ORC_INF) { /* descend */
+          index[v] = low[v] = next++;
+          stk[sp++] = v;
+          on[v] = 1;
+          cs_v[depth] = v;
+          cs_e[depth] = out.off[v];
+          ++depth;
+        } else if (on[v] && index[v] < low[u]) {
+          low[u] = index[v];
+        }
+        continue;
+      }
+      /* all out-edges of u done */
+      if (low[u] == index[u]) { /* u roots a component: pop it, label = its min id */
+        uint32_t k = sp, mn = ORC_INF;
+        do {
+          --k;
+          if (stk[k] < mn) mn = stk[k];
+        } while (stk[k] != u);
+        for (uint32_t q = k; q < sp; ++q) {
+          label[stk[q]] = mn;
+          on[stk[q]] = 0;
+        }
+        sp = k;
+      }
+      --depth;
+      if (depth) {
+        const uint32_t p = cs_v[depth - 1];
+        if (low[u] < low[p]) low[p] = low[u];
+      }
+    }
+  }
+  free(index);
+  free(low);
+  free(stk);
+  free(cs_v);
+  free(cs_e);
+  free(on);
+  csr_free(&out);
+  return 0;
+}
+
+/*
  * Weighted-PageRank adjoint. Forward: `fwd_iters` steps from r0 = 1/n with
  * teleport `tele` (NULL: 1/n) and uniform dangling spread. Adjoint:
  * lambda^0 = g, then adj_terms-1 updates lambda' = M^T lambda + g, so lambda
@@ -226,7 +375,7 @@ int orc_wpr_adjoint(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t*
   double* y = (double*)malloc((size_t)n * sizeof(double));
   orc_csr out;
   int bad = !r || !W || !lam || !nl || !y;
-  if (!bad) bad = csr_build(n, m, src, dst, &out) != 0;
+  if (!bad) bad = csr_build(n, m, src, dst, 1, &out) != 0;
   if (bad) {
     free(r);
     free(W);

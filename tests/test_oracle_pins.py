@@ -105,6 +105,23 @@ def test_rank_mass_sums_to_one_with_dangling(iters):
     assert (r > 0).all()
 
 
+@pytest.mark.parametrize("weighted", [False, True])
+def test_prepared_problem_is_the_same_arithmetic(weighted):
+    # the prepared form (CSR built once, iterations timed alone) returns exactly
+    # the one-call result, and repeated iterate() calls do not interfere
+    s, d, w = inputs.rmat_edges(10, 8 << 10, 8, weights=weighted)
+    n = 1 << 10
+    w = None if w is None else w.astype(np.float64)
+    pp = oracle.PreparedPageRank(n, s, d, w)
+    for iters in (1, 7):
+        assert (pp.iterate(ALPHA, iters) == oracle.pagerank(n, s, d, ALPHA, iters, w=w)).all()
+    t = np.zeros(n)
+    t[[3, 9]] = 0.5
+    assert (pp.iterate(ALPHA, 4, tele=t, dangling_by_tele=True, r0=t)
+            == oracle.pagerank(n, s, d, ALPHA, 4, w=w, tele=t, dangling_by_tele=True, r0=t)).all()
+    pp.close()
+
+
 def test_pagerank_dangling_term_matters():
     # A plausible mistake (dropping the dangling mass) breaks the sum-to-one pin:
     # a 2-vertex path 0 -> 1 with 1 dangling.
@@ -208,6 +225,8 @@ def test_bfs_golden_fixture():
     assert depth.tolist() == want
     finite = depth[depth != oracle.INF]
     assert int(finite.max()) == int(fx["maxdepth"][0])  # Algorithm 4 output
+    assert oracle.bfs_max_depth(depth) == int(fx["maxdepth"][0])
+    assert oracle.bfs_max_depth(np.full(3, oracle.INF, np.uint32)) == -1
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -261,6 +280,75 @@ def test_wcc_matches_scipy_components():
     for c in range(k):
         members = np.flatnonzero(comp == c)
         assert (lab[members] == members.min()).all()
+
+
+# ---------------------------------------------------------------- SCC
+
+def _scc_brute(n, s, d):
+    """u and v share a component iff each reaches the other (reachability by
+    a breadth-first search from every vertex); label = smallest member."""
+    adj = [[] for _ in range(n)]
+    for u, v in zip(s, d):
+        adj[int(u)].append(int(v))
+    reach = np.zeros((n, n), dtype=bool)
+    for r in range(n):
+        reach[r, r] = True
+        q = deque([r])
+        while q:
+            u = q.popleft()
+            for v in adj[u]:
+                if not reach[r, v]:
+                    reach[r, v] = True
+                    q.append(v)
+    mutual = reach & reach.T
+    return np.array([int(np.flatnonzero(mutual[v]).min()) for v in range(n)], dtype=np.uint32)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_scc_matches_mutual_reachability(seed):
+    n = 3 + 6 * seed
+    s, d = _rand_graph(n, int(1.3 * n), seed)
+    assert (oracle.scc(n, s, d) == _scc_brute(n, s, d)).all()
+
+
+def test_scc_special_cases():
+    # a directed cycle is one component; a path (a DAG) is all singletons;
+    # a self-loop does not join anything; isolated vertices are their own
+    n = 10
+    cyc = np.arange(n, dtype=np.uint32)
+    assert (oracle.scc(n, cyc, (cyc + 1) % n) == 0).all()
+    assert (oracle.scc(n, cyc[:-1], cyc[1:]) == cyc).all()
+    assert (oracle.scc(n, [3, 3], [3, 4]) == cyc).all()
+    # two cycles joined one way stay apart: {0,1,2} -> {5,6}
+    s = np.array([0, 1, 2, 2, 5, 6], np.uint32)
+    d = np.array([1, 2, 0, 5, 6, 5], np.uint32)
+    lab = oracle.scc(7, s, d)
+    assert lab.tolist() == [0, 0, 0, 3, 4, 5, 5]
+
+
+def test_scc_matches_scipy_strong_components():
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    s, d, _ = inputs.rmat_edges(12, 4 << 12, 6)
+    n = 1 << 12
+    lab = oracle.scc(n, s, d)
+    A = sp.coo_matrix((np.ones(len(s)), (s, d)), shape=(n, n))
+    k, comp = connected_components(A, directed=True, connection="strong")
+    assert len(np.unique(lab)) == k
+    assert k < n - 100  # a non-trivial case: many vertices share components
+    for c in range(k):
+        members = np.flatnonzero(comp == c)
+        assert (lab[members] == members.min()).all()
+
+
+def test_scc_is_finer_than_wcc():
+    s, d, _ = inputs.rmat_edges(11, 8 << 11, 2)
+    n = 1 << 11
+    scc, wcc = oracle.scc(n, s, d), oracle.wcc(n, s, d)
+    # every strong component lies inside one weak component, and the labels are minima
+    assert (wcc[scc] == wcc).all()
+    assert (scc <= np.arange(n)).all() and (scc[scc] == scc).all()
 
 
 # ---------------------------------------------------------------- adjoint
@@ -337,6 +425,37 @@ def test_adjoint_central_differences_and_scale_invariance():
     per_u = np.zeros(n)
     np.add.at(per_u, s, w * out["dw"])
     assert np.abs(per_u).max() < 1e-14
+
+
+def test_adjoint_central_differences_on_100_edges():
+    # The differentiation workload checks 100 random edges against central
+    # differences; here at R-MAT scale 12 (edge factor 16, 64 targets), with
+    # 200 forward steps and 200 adjoint terms (a^200 ~ 8e-15 truncation).
+    # Central differences err by rounding, about eps |L| / h, and by h^2 times
+    # the third derivative / 6.
+    n = 1 << 12
+    s, d, w = inputs.rmat_edges(12, 16 << 12, 4, weights=True)
+    w = w.astype(np.float64)
+    T = inputs.targets(n, 64, 4)
+    g = np.zeros(n)
+    g[T] = 1.0
+    K = 200
+    out = oracle.wpr_adjoint(n, s, d, w, g, ALPHA, fwd_iters=K, adj_terms=K)
+    L0 = oracle.pagerank(n, s, d, ALPHA, K, w=w)[T].sum()
+    rng = np.random.default_rng(100)
+    worst = 0.0
+    for e in rng.choice(len(s), 100, replace=False):
+        h = 1e-5 * w[e]
+        wp, wm = w.copy(), w.copy()
+        wp[e] += h
+        wm[e] -= h
+        fd = (oracle.pagerank(n, s, d, ALPHA, K, w=wp)[T].sum()
+              - oracle.pagerank(n, s, d, ALPHA, K, w=wm)[T].sum()) / (2 * h)
+        err = abs(fd - out["dw"][e])
+        tol = 1e-6 * abs(fd) + 50 * np.finfo(float).eps * L0 / h
+        worst = max(worst, err / tol)
+        assert err <= tol, (e, fd, out["dw"][e])
+    print(f"100-edge central differences: worst error / tolerance = {worst:.3f}")
 
 
 # ---------------------------------------------------------------- DSSS layout
