@@ -98,7 +98,10 @@ typedef struct {
   uint32_t streamed_cols; /* shards streamed from pinned host per iteration     */
   float ms;               /* wall time of the iteration loop (CUDA events)      */
   uint64_t edges_swept;   /* edges read by all sweeps (inactive sources skipped) */
-  uint64_t bytes_model;   /* algorithmic device bytes of the loop (see DESIGN)  */
+  uint64_t bytes_model;   /* algorithmic device bytes of the loop: per sweep 4 B
+                             per edge read (8 B weighted) + 16 n (PageRank family:
+                             gather, outdeg, new values, contributions) or 12 n
+                             (BFS / WCC); DPU adds 12 B per hub entry          */
   uint64_t h2d_bytes;     /* host->device bytes of the loop (streaming)         */
   uint64_t d2h_bytes;     /* device->host bytes of the loop                     */
   uint32_t launches;      /* kernels launched by the loop                       */
@@ -178,14 +181,13 @@ nx_status nx_dsss_export(const nx_graph* g, int32_t transpose, uint32_t* src, ui
  * Runs `iters` synchronous iterations of `program` (BFS/WCC: at most `iters`,
  * stopping when no interval is active — Algorithm 1) under `strategy` with a
  * device-memory budget of mem_budget_bytes for intervals and sub-shards
- * (0 = unlimited). Values persist in the graph: a later nx_run of the same
- * program with params->use_graph unchanged continues from them when
- * `resume` is set in the params-independent sense below.
+ * (0 = unlimited, or the graph's budget from nx_graph_set_budget).
  *   params : nullable (alpha 0.85, root 0, uniform teleport)
  *   stats  : nullable; filled on success
- * The run starts from the program's Initialize (Algorithm 2 for BFS) unless
- * nx_set_values was called since the last run of the same program, in which
- * case it continues from those values.
+ * Every run starts from the program's Initialize (Algorithm 2 for BFS), with
+ * one exception that serves resuming: when nx_set_values was called for this
+ * program since the graph's last run, the run continues from those values.
+ * The values a run leaves stay in the graph for nx_get_values.
  * Errors: INVALID_ARG (program needs a structure the graph lacks, root >= n,
  * an NX_SRC_* strategy with another program or a budget), BUDGET_TOO_SMALL
  * (SPU without room for 2 n B_a; MPU/DPU below one interval pair), OOM, CUDA.
@@ -213,9 +215,9 @@ nx_status nx_set_values(nx_graph* g, nx_program program, const void* in, uint64_
  * sweep per iteration over the DSSS with B values per vertex.
  *   teleport : [n][B] row-major float (vertex-major), host or device
  *   ranks    : output [n][B] float, host or device (same flag)
- * r0 = t and dangling mass spread by each column's t; alpha from params.
- * Errors: INVALID_ARG (B not in {1..64} or not a multiple of 4 unless B < 4... see
- * DESIGN: B in [1, 64]), OOM, CUDA.
+ * r0 = t and dangling mass spread by each column's t; damping `alpha`.
+ * Errors: INVALID_ARG (NULL pointers, B not in [1, 64], iters == 0, alpha
+ * outside [0, 1)), OOM, CUDA.
  */
 nx_status nx_run_ppr_batch(nx_graph* g, const float* teleport, uint32_t B, uint32_t iters,
                            float alpha, float* ranks, int32_t ptrs_are_device,
@@ -238,14 +240,41 @@ nx_status nx_adjoint_wpr(nx_graph* g, const float* grad_r, uint32_t adj_terms, f
 
 /*
  * Runs `program` on `count` independent graphs in one persistent kernel per
- * call, the whole iteration loop captured in a CUDA graph. Each graph keeps
- * its own values (read them with nx_get_values). BFS uses root 0.
- * Errors: INVALID_ARG (WCC on a graph without transpose, a graph built with
- * NX_RELABEL, ...), TIMEOUT (a
- * bounded grid barrier gave up; the values are then undefined), OOM, CUDA.
+ * call (blocks pull (graph, tile) work items from a counter and meet at a
+ * grid barrier after every iteration), the whole iteration loop captured in a
+ * CUDA graph. The executable graph is kept (a few per process) and replayed
+ * by a later call with the same graphs, program, iteration count, damping and
+ * barrier limit whose graphs have not reallocated any buffer since
+ * (stats->Q is then 1, else 0); nx_graph_free of a member drops it. Each
+ * graph keeps its own values (read them with nx_get_values). BFS uses root 0.
+ * Errors: INVALID_ARG (NULL or repeated graphs, PPR, WCC on a graph without
+ * transpose, WPR without weights, a graph built with NX_RELABEL), TIMEOUT (a
+ * grid barrier waited longer than its limit, see nx_set_barrier_limit; the
+ * kernel then ends without touching memory beyond its graphs, the values are
+ * undefined and the graphs' completion counters are reset for later runs),
+ * OOM, CUDA.
  */
 nx_status nx_run_multi(nx_graph** graphs, uint32_t count, nx_program program, float alpha,
                        uint32_t iters, nx_run_stats* stats);
+
+/*
+ * Output of BFS (Algorithm 4): the largest finite depth among the graph's
+ * current BFS values (the number of levels below the root), or -1 if none is
+ * finite.
+ *   max_depth : host int64
+ * Errors: INVALID_ARG (NULL, the graph's last run was not NX_BFS), CUDA.
+ */
+nx_status nx_bfs_max_depth(const nx_graph* g, int64_t* max_depth);
+
+/*
+ * How long a thread block of nx_run_multi's persistent kernel waits at a grid
+ * barrier before it gives up, in GPU clock cycles (0 = the default, 4e9
+ * cycles: about two seconds at 2 GHz). Applies to later calls in the whole
+ * process. A short limit makes the barrier give up on purpose, which is how
+ * the TIMEOUT path is tested (no block ever waits without a limit).
+ * Errors: INVALID_ARG (cycles > 2^62).
+ */
+nx_status nx_set_barrier_limit(uint64_t cycles);
 
 void nx_graph_free(nx_graph* g);
 

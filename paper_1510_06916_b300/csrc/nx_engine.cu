@@ -2,7 +2,9 @@
 // SPU / DPU / MPU (Algorithms 5-7), activity-driven termination (Algorithm 1),
 // value access, and the I/O model of Table II.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -1155,6 +1157,46 @@ nx_status adjoint_impl(nx_graph* g, const float* grad_r, uint32_t K, float* grad
 }
 
 // ---------------------------------------------------------------- many graphs
+// The executable CUDA graph of a multi-graph run (counter resets + the
+// persistent kernel) and the device copies of its arguments. A later call on
+// the same graphs with the same program, iteration count, damping and barrier
+// limit, whose per-graph arguments are byte-identical (no buffer of any graph
+// was reallocated), replays it without capturing again.
+struct MultiExec {
+  int device = -1;
+  std::vector<nx_graph*> graphs;
+  int prog = -1;
+  float alpha = 0.f;
+  uint32_t iters = 0;
+  long long limit = 0;
+  std::vector<unsigned char> args_img, items_img;
+  DevBuf d_args, d_items, d_ctr, d_sync;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~MultiExec() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+constexpr size_t kMultiCacheSize = 4;
+std::mutex g_multi_mu;
+// most recent last; never destroyed (at process exit the CUDA context and the
+// caller's streams may already be gone)
+std::vector<std::unique_ptr<MultiExec>>& g_multi_cache = *new std::vector<std::unique_ptr<MultiExec>>();
+std::atomic<long long> g_barrier_limit{0};
+
+// Drops the cached executable graphs that sweep `g` (it is being freed).
+void multi_cache_drop(const nx_graph* g) {
+  std::lock_guard<std::mutex> lock(g_multi_mu);
+  auto& c = g_multi_cache;
+  for (size_t q = 0; q < c.size();) {
+    if (std::find(c[q]->graphs.begin(), c[q]->graphs.end(), g) != c[q]->graphs.end())
+      c.erase(c.begin() + q);
+    else
+      ++q;
+  }
+}
+
 nx_status multi_impl(nx_graph** gs, uint32_t count, nx_program prog, float alpha, uint32_t iters,
                      nx_run_stats* st) {
   nx_params p{};
@@ -1214,64 +1256,96 @@ nx_status multi_impl(nx_graph** gs, uint32_t count, nx_program prog, float alpha
                    [&](uint32_t x, uint32_t y) { return costs[x] > costs[y]; });
   std::vector<MItem> sorted(items.size());
   for (size_t q = 0; q < order.size(); ++q) sorted[q] = items[order[q]];
-  DevBuf d_args, d_items, d_ctr, d_sync;
-  NX_TRY(d_args.alloc(args.size() * sizeof(SweepArgs)));
-  NX_TRY(d_items.alloc(std::max<size_t>(sorted.size(), 1) * sizeof(MItem)));
-  NX_TRY(d_ctr.alloc(std::max<size_t>(iters, 1) * 4));
-  NX_TRY(d_sync.alloc(sizeof(MultiSync)));
+  const long long limit = barrier_limit();
+  int device = 0;
+  NX_CUDA(cudaGetDevice(&device));
+  const unsigned char* ab = reinterpret_cast<const unsigned char*>(args.data());
+  const unsigned char* ib = reinterpret_cast<const unsigned char*>(sorted.data());
+  std::vector<unsigned char> args_img(ab, ab + args.size() * sizeof(SweepArgs));
+  std::vector<unsigned char> items_img(ib, ib + sorted.size() * sizeof(MItem));
   cudaStream_t s = stream();
-  NX_CUDA(cudaMemcpyAsync(d_args.p, args.data(), args.size() * sizeof(SweepArgs),
-                          cudaMemcpyHostToDevice, s));
-  if (!sorted.empty())
-    NX_CUDA(cudaMemcpyAsync(d_items.p, sorted.data(), sorted.size() * sizeof(MItem),
+
+  std::lock_guard<std::mutex> lock(g_multi_mu);
+  MultiExec* ex = nullptr;
+  for (size_t q = 0; q < g_multi_cache.size(); ++q) {
+    MultiExec* c = g_multi_cache[q].get();
+    if (c->device == device && c->prog == (int)prog && c->alpha == alpha && c->iters == iters &&
+        c->limit == limit && c->graphs == std::vector<nx_graph*>(gs, gs + count) &&
+        c->args_img == args_img && c->items_img == items_img) {
+      std::unique_ptr<MultiExec> keep = std::move(g_multi_cache[q]);  // most recent last
+      g_multi_cache.erase(g_multi_cache.begin() + q);
+      g_multi_cache.push_back(std::move(keep));
+      ex = g_multi_cache.back().get();
+      break;
+    }
+  }
+  const bool hit = ex != nullptr;
+  if (!hit) {
+    std::unique_ptr<MultiExec> c(new MultiExec());
+    c->device = device;
+    c->graphs.assign(gs, gs + count);
+    c->prog = (int)prog;
+    c->alpha = alpha;
+    c->iters = iters;
+    c->limit = limit;
+    NX_TRY(c->d_args.alloc(args.size() * sizeof(SweepArgs)));
+    NX_TRY(c->d_items.alloc(std::max<size_t>(sorted.size(), 1) * sizeof(MItem)));
+    NX_TRY(c->d_ctr.alloc(std::max<size_t>(iters, 1) * 4));
+    NX_TRY(c->d_sync.alloc(sizeof(MultiSync)));
+    NX_CUDA(cudaMemcpyAsync(c->d_args.p, args.data(), args.size() * sizeof(SweepArgs),
                             cudaMemcpyHostToDevice, s));
-  NX_CUDA(cudaStreamSynchronize(s));
-  uint32_t nblocks = 0;
-  NX_TRY(multi_blocks(K, tile_max, &nblocks));
-  // the whole iteration loop as one CUDA graph: counters reset, then the kernel
-  cudaStream_t cs = nullptr;
-  NX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  nx_status rc = NX_OK;
-  {
+    if (!sorted.empty())
+      NX_CUDA(cudaMemcpyAsync(c->d_items.p, sorted.data(), sorted.size() * sizeof(MItem),
+                              cudaMemcpyHostToDevice, s));
+    NX_CUDA(cudaStreamSynchronize(s));
+    uint32_t nblocks = 0;
+    NX_TRY(multi_blocks(K, tile_max, &nblocks));
+    // the whole iteration loop as one CUDA graph: counters reset, then the kernel
+    cudaStream_t cs = nullptr;
+    NX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    nx_status rc = NX_OK;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaMemsetAsync(d_ctr.p, 0, std::max<size_t>(iters, 1) * 4, cs);
-      cudaMemsetAsync(d_sync.p, 0, sizeof(MultiSync), cs);
-      rc = launch_multi(K, d_args.as<SweepArgs>(), d_items.as<MItem>(), (uint32_t)sorted.size(),
-                        iters, d_ctr.as<uint32_t>(), d_sync.as<MultiSync>(), tile_max, nblocks, cs);
-      cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+      cudaMemsetAsync(c->d_ctr.p, 0, std::max<size_t>(iters, 1) * 4, cs);
+      cudaMemsetAsync(c->d_sync.p, 0, sizeof(MultiSync), cs);
+      rc = launch_multi(K, c->d_args.as<SweepArgs>(), c->d_items.as<MItem>(),
+                        (uint32_t)sorted.size(), iters, c->d_ctr.as<uint32_t>(),
+                        c->d_sync.as<MultiSync>(), tile_max, nblocks, limit, cs);
+      cudaError_t e2 = cudaStreamEndCapture(cs, &c->graph);
       if (rc == NX_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture", __FILE__, __LINE__);
     } else {
       rc = cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
     }
-  }
-  if (rc == NX_OK) {
-    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    cudaStreamDestroy(cs);
+    NX_TRY(rc);
+    NX_CUDA(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    c->args_img.swap(args_img);
+    c->items_img.swap(items_img);
+    if (g_multi_cache.size() >= kMultiCacheSize) g_multi_cache.erase(g_multi_cache.begin());
+    g_multi_cache.push_back(std::move(c));
+    ex = g_multi_cache.back().get();
   }
   float ms = 0.f;
-  if (rc == NX_OK) {
+  {
     EventPair ev;
-    rc = ev.create();
-    if (rc == NX_OK) {
-      cudaEventRecord(ev.e0, s);
-      cudaError_t e = cudaGraphLaunch(exec, s);
-      cudaEventRecord(ev.e1, s);
-      cudaError_t e3 = cudaEventSynchronize(ev.e1);
-      if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__);
-      else if (e3 != cudaSuccess) rc = cuda_fail(e3, "multi-graph kernel", __FILE__, __LINE__);
-      else cudaEventElapsedTime(&ms, ev.e0, ev.e1);
-    }
+    NX_TRY(ev.create());
+    NX_CUDA(cudaEventRecord(ev.e0, s));
+    NX_CUDA(cudaGraphLaunch(ex->exec, s));
+    NX_CUDA(cudaEventRecord(ev.e1, s));
+    NX_TRY(ev.elapsed(&ms));
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  cudaStreamDestroy(cs);
-  NX_TRY(rc);
   MultiSync hs{};
-  NX_CUDA(cudaMemcpy(&hs, d_sync.p, sizeof hs, cudaMemcpyDeviceToHost));
+  NX_CUDA(cudaMemcpy(&hs, ex->d_sync.p, sizeof hs, cudaMemcpyDeviceToHost));
   if (hs.err) {
+    // Blocks that gave up left per-iteration and split-tile completion
+    // counters part-way: clear them so the graphs' next runs start clean.
+    for (uint32_t gi = 0; gi < count; ++gi) {
+      nx_graph* g = gs[gi];
+      NX_CUDA(cudaMemsetAsync(scal_of(g).ticket, 0, 8, s));
+      NX_CUDA(cudaMemsetAsync(g->tile_ticket.p, 0, g->tile_ticket.bytes, s));
+      g->last_prog = -1;
+    }
+    NX_CUDA(cudaStreamSynchronize(s));
     set_error("nx_run_multi: a grid barrier timed out; values are undefined");
     return NX_ERR_TIMEOUT;
   }
@@ -1282,6 +1356,7 @@ nx_status multi_impl(nx_graph** gs, uint32_t count, nx_program prog, float alpha
     st->ms = ms;
     st->edges_swept = edges * iters;
     st->launches = 1;
+    st->Q = hit ? 1u : 0u;  // 1: the cached executable graph was replayed
     uint64_t bytes = 0;
     for (uint32_t gi = 0; gi < count; ++gi) bytes += bytes_per_sweep(gs[gi], prog, gs[gi]->m);
     st->bytes_model = bytes * iters;
@@ -1289,7 +1364,26 @@ nx_status multi_impl(nx_graph** gs, uint32_t count, nx_program prog, float alpha
   return NX_OK;
 }
 
+// Largest finite value of a uint32 array plus one (0: none finite).
+__global__ void k_max_finite(const uint32_t* __restrict__ v, uint32_t n, uint32_t* __restrict__ out) {
+  uint32_t mx = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+    const uint32_t d = v[x];
+    if (d != kInf && d + 1 > mx) mx = d + 1;
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
 }  // namespace
+}  // namespace nx
+
+namespace nx {
+long long barrier_limit() {
+  const long long v = g_barrier_limit.load();
+  return v > 0 ? v : 4000000000ll;  // default: about two seconds at 2 GHz
+}
 }  // namespace nx
 
 // ---------------------------------------------------------------- C ABI
@@ -1360,6 +1454,28 @@ extern "C" nx_status nx_run_multi(nx_graph** graphs, uint32_t count, nx_program 
   return nx::multi_impl(graphs, count, program, alpha, iters, stats);
 }
 
+extern "C" nx_status nx_set_barrier_limit(uint64_t cycles) {
+  if (cycles > (1ull << 62)) return nx::invalid("nx_set_barrier_limit: limit too large");
+  nx::g_barrier_limit.store((long long)cycles);
+  return NX_OK;
+}
+
+extern "C" nx_status nx_bfs_max_depth(const nx_graph* g, int64_t* max_depth) {
+  if (!g || !max_depth) return nx::invalid("nx_bfs_max_depth: NULL argument");
+  if (g->last_prog != NX_BFS)
+    return nx::invalid("nx_bfs_max_depth: the graph's current values are not BFS depths");
+  uint32_t* slot = reinterpret_cast<uint32_t*>(g->scal.as<unsigned char>() + 32);
+  NX_CUDA(cudaMemsetAsync(slot, 0, 4, nx::stream()));
+  nx::k_max_finite<<<nx::grid_for(g->geo.n), 256, 0, nx::stream()>>>(
+      g->val[g->cur].as<uint32_t>(), g->geo.n, slot);
+  NX_LAUNCH_CHECK();
+  uint32_t h = 0;
+  NX_CUDA(cudaMemcpyAsync(&h, slot, 4, cudaMemcpyDeviceToHost, nx::stream()));
+  NX_CUDA(cudaStreamSynchronize(nx::stream()));
+  *max_depth = (int64_t)h - 1;
+  return NX_OK;
+}
+
 extern "C" nx_status nx_get_values(const nx_graph* g, void* out, uint64_t count,
                                    int32_t out_is_device) {
   if (!g || !out) return nx::invalid("nx_get_values: NULL argument");
@@ -1414,7 +1530,7 @@ extern "C" nx_status nx_set_values(nx_graph* g, nx_program program, const void* 
 extern "C" void nx_graph_free(nx_graph* g) {
   if (!g) return;
   cudaStreamSynchronize(nx::stream());
-  if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  nx::multi_cache_drop(g);
   delete g;
 }
 

@@ -221,9 +221,6 @@ struct nx_graph {
   nx::PinnedBuf hval[2];    // pinned host values of non-resident intervals
   nx::PinnedBuf hact;       // pinned host copy of the activity count + flags [P + 1]
   nx::DevBuf accres;        // MPU resident-column accumulators
-  cudaGraphExec_t gexec = nullptr;
-  int gexec_key = -1;
-  uint32_t gexec_iters = 0;
   uint64_t device_bytes() const;
 };
 

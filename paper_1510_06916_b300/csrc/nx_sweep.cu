@@ -725,10 +725,9 @@ __global__ void __launch_bounds__(kThreads) k_multi(const SweepArgs* __restrict_
 
 nx_status launch_multi(ProgKind kind, const SweepArgs* args, const MItem* items, uint32_t nitems,
                        uint32_t iters, uint32_t* ctr, MultiSync* sy, uint32_t tile_max,
-                       uint32_t nblocks, cudaStream_t s) {
+                       uint32_t nblocks, long long limit, cudaStream_t s) {
   const bool sums = (kind == PK_PR || kind == PK_WPR);
   const size_t smem = (size_t)tile_max * (sums ? 8 : 4) + (size_t)(kThreads + 1) * sizeof(FlatEnt);
-  const long long limit = 4000000000ll;  // about two seconds at 2 GHz
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

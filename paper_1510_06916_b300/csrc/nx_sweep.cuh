@@ -87,9 +87,13 @@ struct MItem {
 struct MultiSync {
   unsigned count, gen, err, pad;
 };
+// `limit`: clock cycles a block waits at a grid barrier before it gives up,
+// sets sy->err and returns.
 nx_status launch_multi(ProgKind kind, const SweepArgs* args, const MItem* items, uint32_t nitems,
                        uint32_t iters, uint32_t* ctr, MultiSync* sy, uint32_t tile_max,
-                       uint32_t nblocks, cudaStream_t s);
+                       uint32_t nblocks, long long limit, cudaStream_t s);
+// Grid-barrier wait limit of nx_run_multi in clock cycles (nx_set_barrier_limit).
+long long barrier_limit();
 // Co-resident blocks of the multi-graph kernel (occupancy x SMs).
 nx_status multi_blocks(ProgKind kind, uint32_t tile_max, uint32_t* nblocks);
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "nx_set_stream", "nx_last_error", "nx_build_dsss", "nx_graph_get_info", "nx_run",
     "nx_get_values", "nx_set_values", "nx_run_ppr_batch", "nx_adjoint_wpr", "nx_run_multi",
     "nx_graph_free", "nx_io_model", "nx_dsss_export", "nx_pagerank_step_noalloc",
-    "nx_autotune", "nx_get_relabel",
+    "nx_autotune", "nx_get_relabel", "nx_bfs_max_depth", "nx_set_barrier_limit",
 ]
 
 
@@ -95,6 +95,8 @@ def lib():
         L.nx_pagerank_step_noalloc.argtypes = [vp, f32, vp, vp]
         L.nx_autotune.argtypes = [vp, vp, u64, u32, u32, vp, i32, vp, u32, u32,
                                   ctypes.POINTER(u32), vp, ctypes.c_char_p]
+        L.nx_bfs_max_depth.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        L.nx_set_barrier_limit.argtypes = [u64]
         L.nx_graph_free.argtypes = [vp]
         L.nx_graph_free.restype = None
         L.nx_io_model.argtypes = [i32, d, d, d, d, d, d, d, d, ctypes.POINTER(d),
@@ -147,6 +149,11 @@ def set_stream(stream) -> None:
     """Stream for later calls: a torch.cuda.Stream, a raw handle, or None."""
     h = getattr(stream, "cuda_stream", stream)
     check(lib().nx_set_stream(ctypes.c_void_p(h or 0)))
+
+
+def set_barrier_limit(cycles: int) -> None:
+    """Grid-barrier wait limit of run_multi in GPU clock cycles (0: default)."""
+    check(lib().nx_set_barrier_limit(cycles))
 
 
 def io_model(strategy, n, m, P, B_M, B_a=4.0, B_v=4.0, B_e=4.0, d=15.0):
@@ -250,6 +257,12 @@ class Graph:
         check(lib().nx_run(self._h, PROGRAMS.get(program, program), ctypes.byref(prm), iters,
                            STRATEGIES.get(strategy, strategy), budget, ctypes.byref(st)))
         return st.as_dict()
+
+    def bfs_max_depth(self) -> int:
+        """Algorithm 4's Output for the last BFS run: largest finite depth (-1: none)."""
+        v = ctypes.c_int64()
+        check(lib().nx_bfs_max_depth(self._h, ctypes.byref(v)))
+        return v.value
 
     def values(self, out=None, dtype=None):
         """Current values: float32 ranks (PageRank family) or uint32 depth/labels."""

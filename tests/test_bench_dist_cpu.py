@@ -59,3 +59,31 @@ def test_reference_arm_runs_on_rank0_only(monkeypatch, capsys):
 
     assert bench.run_reference(Args(), bench.WORKLOADS["rmat16"]) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_reports_our_config(capsys):
+    # both arms name the same workload, metric and config (the reference runs
+    # the oracle's iteration loop only; its CSR is built before the steps)
+    import json
+
+    class Args:
+        steps, warmup, workload = 2, 1, "rmat16"
+
+    w = bench.WORKLOADS["rmat16"]
+    assert bench.run_reference(Args(), w) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["config"] == bench.config_for(w, "rmat16")
+    assert line["metric"] == bench.METRIC and line["unit"] == "GTEPS"
+    assert line["higher_is_better"] is True
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_default_workload_is_the_scale_26_graph():
+    w = bench.WORKLOADS["rmat26"]
+    cfg = bench.config_for(w, "rmat26")
+    assert cfg["m"] == 1_476_395_008 and cfg["n"] == 1 << 26 and cfg["P"] == 64
+    assert cfg["iters_per_step"] == 10
+    import argparse  # noqa: F401  (the parser's default is checked by name below)
+    src = open(bench.__file__).read()
+    assert 'ap.add_argument("--workload", default="rmat26"' in src
