@@ -49,8 +49,15 @@ typedef enum {
   NX_PPR = 1, /* personalized PageRank: teleport t, r0 = t, dangling mass by t    */
   NX_WPR = 2, /* weighted PageRank: p_uv = w_uv / W_u (needs NX_WITH_WEIGHTS)     */
   NX_BFS = 3, /* Algorithms 2-4: depth(root) = 0, min over in-edges of depth+1    */
-  NX_WCC = 4  /* min-label propagation along both edge directions (needs
+  NX_WCC = 4, /* min-label propagation along both edge directions (needs
                  NX_WITH_TRANSPOSE); label = smallest vertex id in the component */
+  NX_SCC = 5  /* strongly connected components (Section IV-D; needs
+                 NX_WITH_TRANSPOSE; SPU, no budget): label = smallest vertex id
+                 of the component, by rounds of forward color propagation over
+                 the DSSS and backward reach over its transpose. `iters` bounds
+                 the sweeps of all rounds; vertices still unassigned when it
+                 runs out keep 0xFFFFFFFF. stats: iters_done = sweeps,
+                 Q = coloring rounds                                           */
 } nx_program;
 
 /* Update strategies (Section III-B). */
@@ -116,9 +123,12 @@ typedef struct {
   uint64_t m;             /* edges                                              */
   uint64_t D;             /* distinct (sub-shard, destination) pairs = hub size */
   uint64_t D_t;           /* same for the transpose DSSS (0 if not built)       */
-  uint64_t device_bytes;  /* device memory held by the graph                    */
+  uint64_t device_bytes;  /* device memory held by the graph now (after a run
+                             with a budget: what that budget left resident)    */
   float build_ms;         /* time of nx_build_dsss on the device                */
   int32_t has_transpose, has_weights;
+  uint64_t host_bytes;    /* pinned host memory held by the graph (offloaded
+                             edges and indexes, staged intervals)             */
 } nx_graph_info;
 
 /* Stream for all later calls (a cudaStream_t; NULL = legacy default stream). */
@@ -180,8 +190,26 @@ nx_status nx_dsss_export(const nx_graph* g, int32_t transpose, uint32_t* src, ui
 /*
  * Runs `iters` synchronous iterations of `program` (BFS/WCC: at most `iters`,
  * stopping when no interval is active — Algorithm 1) under `strategy` with a
- * device-memory budget of mem_budget_bytes for intervals and sub-shards
- * (0 = unlimited, or the graph's budget from nx_graph_set_budget).
+ * device-memory budget of mem_budget_bytes (0 = unlimited).
+ * The budget B_M is accounted as in Section III-B: the ping-pong intervals
+ * (2 n B_a, B_a = 4) plus the edge words held on the device.
+ *  - B_M >= 2 n B_a (SPU, and MPU / AUTO with Q = P): shards [0, Jc) and the
+ *    head of shard Jc that fit stay on the device; the rest of the edge words
+ *    live only in pinned host memory and stream through two staging buffers
+ *    (bands of sub-shards of at most 64 MB, unless one sub-shard is larger)
+ *    on a side stream every iteration. DSSS the program does not read, the
+ *    hub index and (except for NX_WPR) the weights move to pinned host memory
+ *    too. The device then holds the budget plus: out-degrees and PageRank
+ *    contributions (12 n bytes), piece offsets (16 bytes per piece per DSSS),
+ *    tile tables, one column of accumulators and the staging buffers. The
+ *    layout persists after the run (nx_graph_get_info: device_bytes,
+ *    host_bytes); a later call that needs more on the device (a run without a
+ *    budget, nx_run_ppr_batch, nx_adjoint_wpr, nx_run_multi, nx_dsss_export)
+ *    uploads it again first. Shrinking copies the kept prefix once, so the
+ *    old and the new prefix coexist for the length of that copy.
+ *  - 2 L B_a <= B_M < 2 n B_a (MPU with Q < P, Algorithm 7; DPU): intervals
+ *    [Q, P) live in pinned host memory and are staged per row and column;
+ *    the edge words and hubs stay on the device.
  *   params : nullable (alpha 0.85, root 0, uniform teleport)
  *   stats  : nullable; filled on success
  * Every run starts from the program's Initialize (Algorithm 2 for BFS), with

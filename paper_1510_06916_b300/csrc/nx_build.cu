@@ -254,7 +254,8 @@ nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geom
   NX_CUDA(cudaMemcpyAsync(out.h_piece_off.data(), out.piece_off.p, (npieces + 1) * sizeof(uint64_t),
                           cudaMemcpyDeviceToHost, stream()));
   NX_CUDA(cudaStreamSynchronize(stream()));
-  out.dev_cols = geo.P;
+  out.words = mpad;
+  out.dev_words = mpad;
   return NX_OK;
 }
 
@@ -482,6 +483,15 @@ uint64_t nx_graph::device_bytes() const {
   uint64_t s = 0;
   for (auto* b : bufs) s += b->bytes;
   for (const auto& kv : plans) s += kv.second->items.bytes;
+  s += old_of_new.bytes + new_of_old.bytes;
+  return s;
+}
+
+uint64_t nx_graph::host_bytes() const {
+  const nx::PinnedBuf* bufs[] = {&fwd.h_ew, &fwd.h_hub_dst, &fwd.h_wt, &tr.h_ew, &tr.h_hub_dst,
+                                 &tr.h_wt, &h_orig_src, &h_orig_dst, &hval[0], &hval[1], &hact};
+  uint64_t s = 0;
+  for (auto* b : bufs) s += b->bytes;
   return s;
 }
 

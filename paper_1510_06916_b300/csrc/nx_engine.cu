@@ -372,20 +372,148 @@ nx_status dpu_iteration(nx_graph* g, nx_program prog, SweepArgs& a, uint32_t n_t
   return NX_OK;
 }
 
-// ---------------------------------------------------------------- shard streaming
-// Edge words of columns [first_col, P) of DSSS d held in pinned host memory
-// (created on first use from the device copy).
-nx_status ensure_host_shards(nx_graph* g, Dsss& d, uint32_t first_col) {
-  const auto& tb = g->geo.h_col_tb;
-  const uint64_t e0 = d.h_piece_off[(uint64_t)g->geo.P * tb[first_col]] & ~(kEdgeAlign - 1);
-  if (d.h_ew.p && d.h_ew_first <= e0) return NX_OK;
-  const uint64_t words = round_up(d.m, kEdgeAlign) + kEdgeAlign - e0;
-  NX_TRY(d.h_ew.alloc(words * 4));
-  NX_CUDA(cudaMemcpyAsync(d.h_ew.p, d.ew.as<uint32_t>() + e0, words * 4, cudaMemcpyDeviceToHost,
-                          stream()));
+}  // namespace
+
+// ---------------------------------------------------------------- residency
+// Whole-array moves between the device and pinned host memory (no-ops when
+// the array is already where it is asked to be).
+nx_status move_to_host(DevBuf& d, PinnedBuf& h) {
+  if (!d.p) return NX_OK;
+  NX_TRY(h.alloc(d.bytes));
+  NX_CUDA(cudaMemcpyAsync(h.p, d.p, d.bytes, cudaMemcpyDeviceToHost, stream()));
   NX_CUDA(cudaStreamSynchronize(stream()));
-  d.h_ew_first = e0;
+  d.release();
   return NX_OK;
+}
+
+nx_status move_to_device(PinnedBuf& h, DevBuf& d) {
+  if (d.p || !h.p) return NX_OK;
+  NX_TRY(d.alloc(h.bytes));
+  NX_CUDA(cudaMemcpyAsync(d.p, h.p, h.bytes, cudaMemcpyHostToDevice, stream()));
+  NX_CUDA(cudaStreamSynchronize(stream()));
+  h.release();
+  return NX_OK;
+}
+
+nx_status set_edge_residency(Dsss& d, uint64_t dev_words, uint64_t host_first) {
+  dev_words = std::min(dev_words, d.words);
+  host_first = std::min(host_first, dev_words);
+  const bool need_host = dev_words < d.words;
+  cudaStream_t s = stream();
+  if (need_host && (!d.h_ew.p || d.h_ew_first > host_first)) {
+    // a host image of words [host_first, words): the part below the old image
+    // comes from the device (which holds it: h_ew_first <= dev_words)
+    PinnedBuf nh;
+    NX_TRY(nh.alloc((d.words - host_first) * 4));
+    const uint64_t dev_end = d.h_ew.p ? d.h_ew_first : d.words;
+    if (dev_end > host_first)
+      NX_CUDA(cudaMemcpyAsync(nh.p, d.ew.as<uint32_t>() + host_first, (dev_end - host_first) * 4,
+                              cudaMemcpyDeviceToHost, s));
+    NX_CUDA(cudaStreamSynchronize(s));
+    if (d.h_ew.p)
+      memcpy(nh.as<uint32_t>() + (dev_end - host_first), d.h_ew.p, (d.words - dev_end) * 4);
+    std::swap(nh.p, d.h_ew.p);
+    std::swap(nh.bytes, d.h_ew.bytes);
+    d.h_ew_first = host_first;
+  }
+  if (dev_words != d.dev_words) {
+    // the new device prefix: words the device held, then words from the host image
+    DevBuf nb;
+    if (dev_words) {
+      NX_TRY(nb.alloc(dev_words * 4));
+      const uint64_t kept = std::min(dev_words, d.dev_words);
+      if (kept)
+        NX_CUDA(cudaMemcpyAsync(nb.p, d.ew.p, kept * 4, cudaMemcpyDeviceToDevice, s));
+      if (dev_words > kept)
+        NX_CUDA(cudaMemcpyAsync(nb.as<uint32_t>() + kept, d.h_ew.as<uint32_t>() + (kept - d.h_ew_first),
+                                (dev_words - kept) * 4, cudaMemcpyHostToDevice, s));
+    }
+    NX_CUDA(cudaStreamSynchronize(s));
+    d.ew = std::move(nb);
+    d.dev_words = dev_words;
+  }
+  if (!need_host && d.h_ew.p) {
+    d.h_ew.release();
+    d.h_ew_first = 0;
+  }
+  return NX_OK;
+}
+
+nx_status ensure_resident(nx_graph* g) {
+  Dsss* all_ds[2] = {&g->fwd, g->has_tr ? &g->tr : nullptr};
+  for (Dsss* d : all_ds) {
+    if (!d) continue;
+    NX_TRY(set_edge_residency(*d, d->words, 0));
+    NX_TRY(move_to_device(d->h_hub_dst, d->hub_dst));
+    NX_TRY(move_to_device(d->h_wt, d->wt));
+  }
+  NX_TRY(move_to_device(g->h_orig_src, g->orig_src));
+  NX_TRY(move_to_device(g->h_orig_dst, g->orig_dst));
+  return NX_OK;
+}
+
+bool fully_resident(const nx_graph* g) {
+  const Dsss* all_ds[2] = {&g->fwd, g->has_tr ? &g->tr : nullptr};
+  for (const Dsss* d : all_ds)
+    if (d && (d->dev_words != d->words || d->h_hub_dst.p || d->h_wt.p)) return false;
+  return !g->h_orig_src.p && !g->h_orig_dst.p;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- shard streaming
+// A streamed column is swept in bands of consecutive source intervals whose
+// edge words (over the DSSS of the sweep) fit one staging buffer of this many
+// words (64 MB), unless one sub-shard alone is larger; tile accumulators carry
+// between the bands of a column in device memory.
+constexpr uint64_t kStreamChunkWords = 16ull << 20;
+
+struct StreamBand {
+  uint32_t j, i0, i1;     // column and its source intervals [i0, i1)
+  uint64_t e0[2], e1[2];  // word range of each DSSS (aligned, padded)
+  bool first, last;       // first / last band of the column
+};
+
+// Bands of the streamed columns [Jc, P) (deterministic: plans are cached).
+std::vector<StreamBand> stream_bands(const nx_graph* g, const std::vector<const Dsss*>& ds,
+                                     uint32_t Jc) {
+  const uint32_t P = g->geo.P;
+  const auto& tb = g->geo.h_col_tb;
+  std::vector<StreamBand> out;
+  for (uint32_t j = Jc; j < P; ++j) {
+    const uint32_t nt = tb[j + 1] - tb[j];
+    if (nt == 0) continue;  // empty trailing interval: no tiles
+    // start of SS_ij in DSSS s (i = P: the column's end)
+    auto at = [&](size_t sx, uint32_t i) {
+      const Dsss& d = *ds[sx];
+      return i < P ? d.h_piece_off[piece_index(P, tb[j], nt, i, tb[j])]
+                   : d.h_piece_off[(uint64_t)P * tb[j + 1]];
+    };
+    uint32_t i0 = 0;
+    const size_t before = out.size();
+    while (i0 < P) {
+      uint32_t i1 = i0 + 1;
+      while (i1 < P) {
+        uint64_t w = 0;
+        for (size_t sx = 0; sx < ds.size(); ++sx) w += at(sx, i1 + 1) - at(sx, i0);
+        if (w > kStreamChunkWords) break;
+        ++i1;
+      }
+      StreamBand b{};
+      b.j = j;
+      b.i0 = i0;
+      b.i1 = i1;
+      for (size_t sx = 0; sx < ds.size(); ++sx) {
+        b.e0[sx] = at(sx, i0) & ~(kEdgeAlign - 1);
+        b.e1[sx] = round_up(at(sx, i1), kEdgeAlign) + kEdgeAlign;
+      }
+      out.push_back(b);
+      i0 = i1;
+    }
+    out[before].first = true;
+    out.back().last = true;
+  }
+  return out;
 }
 
 struct Streamer {
@@ -416,6 +544,7 @@ struct RunCtx {
   std::vector<const Dsss*> ds;
   uint32_t P, Q, Jc;
   uint64_t keep[2] = {0, 0};  // leading words of shard Jc (per DSSS) cached in device memory
+  uint64_t stage_off[2] = {0, 0};  // word offset of each DSSS's segment in a staging buffer
   const uint32_t* act_host = nullptr;  // BFS / WCC: this iteration's interval flags (host)
   const float* tele;
   uint64_t h2d = 0, d2h = 0;
@@ -423,49 +552,67 @@ struct RunCtx {
 };
 
 // SPU iteration with columns [Jc, P) streamed from pinned host memory on a
-// side stream (double-buffered); columns [0, Jc) are read in place. The
-// leading c.keep[s] words of column Jc are cached in device memory, so only
-// the rest of that column crosses the host link.
-nx_status spu_stream_iteration(RunCtx& c, SweepArgs& a, const std::vector<uint32_t>& col_off,
-                               Streamer& sm) {
+// side stream (double-buffered), band by band; columns [0, Jc) are read in
+// place. Words below each DSSS's device-resident prefix (the cached head of
+// column Jc) are read from the device, the rest cross the host link.
+nx_status spu_stream_iteration(RunCtx& c, SweepArgs& a, const std::vector<uint32_t>& off,
+                               const std::vector<StreamBand>& bands, Streamer& sm) {
   nx_graph* g = c.g;
   set_iter_ptrs(g, c.prog, a);
   a.mode = 0;
   const Item* all = a.items;
-  // resident columns
-  SweepArgs r = a;
-  r.items = all;
-  NX_TRY(launch_sweep(kind_of(c.prog), r, col_off[c.Jc], stream()));
-  ++c.launches;
-  const auto& tb = g->geo.h_col_tb;
-  for (uint32_t j = c.Jc; j < c.P; ++j) {
-    const int b = j & 1;
-    SweepArgs sa = a;
-    sa.items = all + col_off[j];
-    NX_CUDA(cudaStreamWaitEvent(sm.side, sm.used[b], 0));
-    for (size_t s = 0; s < c.ds.size(); ++s) {
-      const Dsss& d = *c.ds[s];
-      const uint64_t e0 = d.h_piece_off[(uint64_t)c.P * tb[j]] & ~(kEdgeAlign - 1);
-      const uint64_t e1 = round_up(d.h_piece_off[(uint64_t)c.P * tb[j + 1]], kEdgeAlign) + kEdgeAlign;
-      const uint64_t words = e1 - e0;
-      // stage[b] holds one shard per DSSS of the sweep (second half: transpose)
-      uint32_t* dst = g->stage[b].as<uint32_t>() + (s ? (g->stage[b].bytes / 8) : 0);
-      const uint64_t kw = (j == c.Jc) ? std::min(c.keep[s], words) : 0;
-      if (kw)
-        NX_CUDA(cudaMemcpyAsync(dst, d.ew.as<uint32_t>() + e0, kw * 4, cudaMemcpyDeviceToDevice,
-                                sm.side));
-      if (words > kw)
-        NX_CUDA(cudaMemcpyAsync(dst + kw, d.h_ew.as<uint32_t>() + (e0 + kw - d.h_ew_first),
-                                (words - kw) * 4, cudaMemcpyHostToDevice, sm.side));
-      c.h2d += (words - kw) * 4;
-      sa.src[s].ew = dst;
-      sa.ew_lo[s] = e0;
-    }
-    NX_CUDA(cudaEventRecord(sm.copied[b], sm.side));
-    NX_CUDA(cudaStreamWaitEvent(stream(), sm.copied[b], 0));
-    NX_TRY(launch_sweep(kind_of(c.prog), sa, col_off[j + 1] - col_off[j], stream()));
+  {  // resident columns
+    SweepArgs r = a;
+    r.items = all;
+    NX_TRY(launch_sweep(kind_of(c.prog), r, off[0], stream()));
     ++c.launches;
-    NX_CUDA(cudaEventRecord(sm.used[b], stream()));
+  }
+  uint32_t nstaged = 0;
+  for (size_t q = 0; q < bands.size(); ++q) {
+    const StreamBand& bd = bands[q];
+    SweepArgs sa = a;
+    sa.items = all + off[q];
+    sa.src_lo = bd.i0;
+    sa.src_hi = bd.i1;
+    sa.acc_base = bd.j * g->geo.L;
+    sa.accres = g->accres.p;
+    sa.acc_in = bd.first ? nullptr : g->accres.p;
+    sa.mode = bd.last ? 0 : 2;
+    const int b = (int)(nstaged & 1);
+    bool staged = false;
+    for (size_t sx = 0; sx < c.ds.size(); ++sx) {
+      const Dsss& d = *c.ds[sx];
+      if (bd.e1[sx] <= d.dev_words) {  // the whole band is on the device
+        sa.src[sx].ew = d.ew.as<uint32_t>();
+        sa.ew_lo[sx] = 0;
+        continue;
+      }
+      if (!staged) {
+        NX_CUDA(cudaStreamWaitEvent(sm.side, sm.used[b], 0));  // the launch two bands back is done
+        staged = true;
+      }
+      uint32_t* dst = g->stage[b].as<uint32_t>() + c.stage_off[sx];
+      const uint64_t e0 = bd.e0[sx], e1 = bd.e1[sx];
+      const uint64_t mid = std::max(e0, std::min(e1, d.dev_words));
+      if (mid > e0)
+        NX_CUDA(cudaMemcpyAsync(dst, d.ew.as<uint32_t>() + e0, (mid - e0) * 4,
+                                cudaMemcpyDeviceToDevice, sm.side));
+      NX_CUDA(cudaMemcpyAsync(dst + (mid - e0), d.h_ew.as<uint32_t>() + (mid - d.h_ew_first),
+                              (e1 - mid) * 4, cudaMemcpyHostToDevice, sm.side));
+      c.h2d += (e1 - mid) * 4;
+      sa.src[sx].ew = dst;
+      sa.ew_lo[sx] = e0;
+    }
+    if (staged) {
+      NX_CUDA(cudaEventRecord(sm.copied[b], sm.side));
+      NX_CUDA(cudaStreamWaitEvent(stream(), sm.copied[b], 0));
+    }
+    NX_TRY(launch_sweep(kind_of(c.prog), sa, off[q + 1] - off[q], stream()));
+    ++c.launches;
+    if (staged) {
+      NX_CUDA(cudaEventRecord(sm.used[b], stream()));
+      ++nstaged;
+    }
   }
   g->cur ^= 1;
   return NX_OK;
@@ -720,6 +867,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   g->last_prog = (int)prog;
   if (prog == NX_WPR) g->wpr_alpha = p.alpha;
   if (push) {
+    NX_TRY(ensure_resident(g));
     PushRun r;
     r.coarse = (strategy == NX_SRC_COARSE);
     r.iters = iters;
@@ -782,6 +930,46 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     }
   }
   const bool streaming = (strat == NX_SPU && c.Jc < P);
+  // Residency: under an SPU budget the device keeps only the words the
+  // schedule reads in place (shards [0, Jc) and the cached head of shard Jc);
+  // the streamed rest, every DSSS the program does not read, the hub index and
+  // (unless weighted PageRank reads them) the weights live in pinned host
+  // memory only. Other runs need their DSSS (and hubs) on the device.
+  const bool budgeted_spu = (strat == NX_SPU && budget != 0);
+  std::vector<StreamBand> bands;
+  if (streaming) bands = stream_bands(g, c.ds, c.Jc);
+  {
+    Dsss* all_ds[2] = {&g->fwd, g->has_tr ? &g->tr : nullptr};
+    for (Dsss* d : all_ds) {
+      if (!d) continue;
+      const auto it = std::find(c.ds.begin(), c.ds.end(), d);
+      const bool used = it != c.ds.end();
+      if (!budgeted_spu) {
+        if (used) {
+          NX_TRY(set_edge_residency(*d, d->words, 0));
+          if (strat == NX_DPU || staged) NX_TRY(move_to_device(d->h_hub_dst, d->hub_dst));
+        }
+        continue;
+      }
+      NX_TRY(move_to_host(d->hub_dst, d->h_hub_dst));
+      if (prog != NX_WPR) NX_TRY(move_to_host(d->wt, d->h_wt));
+      else if (used) NX_TRY(move_to_device(d->h_wt, d->wt));
+      if (!used) {
+        NX_TRY(set_edge_residency(*d, 0, 0));
+      } else if (c.Jc >= P) {
+        NX_TRY(set_edge_residency(*d, d->words, 0));
+      } else {
+        const size_t sx = (size_t)(it - c.ds.begin());
+        const uint64_t ej = d->h_piece_off[(uint64_t)P * tb[c.Jc]];
+        const uint64_t head = (ej & ~(kEdgeAlign - 1)) + c.keep[sx];
+        NX_TRY(set_edge_residency(*d, std::max(round_up(ej, kEdgeAlign), head), ej & ~(kEdgeAlign - 1)));
+      }
+    }
+    if (budgeted_spu) {
+      NX_TRY(move_to_host(g->orig_src, g->h_orig_src));
+      NX_TRY(move_to_host(g->orig_dst, g->h_orig_dst));
+    }
+  }
   // SPU bands: launches over groups of source intervals whose gathered values
   // fit in L2 together (the value array of the whole graph may not)
   uint32_t band = P;
@@ -817,14 +1005,13 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
                    std::max<uint64_t>(blk / nbands, 4096), plan);
       }
       launch_off.push_back((uint32_t)plan.items.size());
-    } else if (strat == NX_SPU) {  // per column groups: [0, Jc) then one per streamed column
-      launch_off.assign(P + 1, 0);
+    } else if (strat == NX_SPU) {  // columns [0, Jc) in place, then one launch per streamed band
       plan_tiles(g, c.ds, 0, P, 0, c.Jc, true, blk, plan);
-      for (uint32_t j = c.Jc; j < P; ++j) {
-        launch_off[j] = (uint32_t)plan.items.size();
-        plan_tiles(g, c.ds, 0, P, j, j + 1, true, blk, plan);
+      for (const StreamBand& bd : bands) {
+        launch_off.push_back((uint32_t)plan.items.size());
+        plan_tiles(g, c.ds, bd.i0, bd.i1, bd.j, bd.j + 1, true, blk, plan);
       }
-      launch_off[P] = (uint32_t)plan.items.size();  // launch_off[Jc]: resident item count
+      launch_off.push_back((uint32_t)plan.items.size());  // launch_off[0]: resident item count
     } else if (!staged) {  // DPU, intervals resident: ToHub items (all rows), then FromHub tiles
       for (size_t sx = 0; sx < c.ds.size(); ++sx)
         for (uint32_t i = 0; i < P; ++i) plan_row(g, *c.ds[sx], (uint32_t)sx, i, 0, P, blk, plan);
@@ -866,21 +1053,19 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
 
   a.split = g->split_buf.p;
 
-  // streaming buffers
+  // streaming buffers: two staging buffers, each with one segment per DSSS
+  // sized for that DSSS's largest band, and a column of tile accumulators
   Streamer sm;
-  std::vector<uint32_t> col_off;
   if (streaming) {
-    for (const Dsss* d : c.ds) NX_TRY(ensure_host_shards(g, *const_cast<Dsss*>(d), c.Jc));
-    uint64_t maxw = 0;
-    for (uint32_t j = c.Jc; j < P; ++j)
-      for (const Dsss* d : c.ds) {
-        const uint64_t e0 = d->h_piece_off[(uint64_t)P * tb[j]] & ~(kEdgeAlign - 1);
-        const uint64_t e1 = round_up(d->h_piece_off[(uint64_t)P * tb[j + 1]], kEdgeAlign) + kEdgeAlign;
-        maxw = std::max(maxw, e1 - e0);
-      }
-    for (int b = 0; b < 2; ++b) NX_TRY(ensure(g->stage[b], maxw * 4 * 2));
+    uint64_t seg[2] = {0, 0};
+    for (const StreamBand& bd : bands)
+      for (size_t sx = 0; sx < c.ds.size(); ++sx)
+        if (bd.e1[sx] > c.ds[sx]->dev_words) seg[sx] = std::max(seg[sx], bd.e1[sx] - bd.e0[sx]);
+    c.stage_off[0] = 0;
+    c.stage_off[1] = seg[0];
+    for (int b = 0; b < 2; ++b) NX_TRY(ensure(g->stage[b], std::max<uint64_t>(seg[0] + seg[1], 1) * 4));
+    NX_TRY(ensure(g->accres, (size_t)L * 4));
     NX_TRY(sm.init());
-    col_off = pl.off;
   }
   // staged intervals (MPU): device accumulators for resident columns, pinned
   // host arrays for the rest, per-interval staging buffers
@@ -948,7 +1133,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     } else if (strat == NX_SPU && !streaming) {
       NX_TRY(spu_band_iteration(c, a, pl.off, band));
     } else if (streaming) {
-      NX_TRY(spu_stream_iteration(c, a, col_off, sm));
+      NX_TRY(spu_stream_iteration(c, a, pl.off, bands, sm));
     } else if (!staged) {
       NX_TRY(dpu_iteration(g, prog, a, n_a, n_b));
       c.launches += 2;
@@ -996,6 +1181,187 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   return NX_OK;
 }
 
+// ---------------------------------------------------------------- SCC
+// Strongly connected components (Section IV-D names SCC; the paper gives no
+// algorithm) by coloring over the DSSS and its transpose. Each round:
+//  1. every unassigned vertex v takes color(v) = its own label (caller id);
+//     forward min-propagation along edges between unassigned vertices makes
+//     color(v) the smallest label of a vertex that reaches v;
+//  2. a vertex whose color is its own label is a root; the vertices of its
+//     color that reach it form its component (a vertex u of that color
+//     reaches the root, and the root reaches u because it has the smallest
+//     label among u's reachers), found by backward reach over the transpose
+//     DSSS; each is assigned the root's label, the smallest in the component;
+//  3. repeat over the vertices left unassigned.
+// Colors never increase along an edge between unassigned vertices, so a
+// vertex's out-neighbours of its own color are exactly those whose reach
+// value (color + 1) equals its color + 1: the backward sweep is a max
+// reduction compared against the vertex's own color.
+__global__ void k_scc_fwd_init(uint32_t n, const uint32_t* __restrict__ lab,
+                               const uint32_t* __restrict__ ids, uint32_t* __restrict__ col) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    col[v] = lab[v] == kInf ? (ids ? ids[v] : (uint32_t)v) : kInf;
+}
+
+// Roots (color == own label) start reached; their intervals start active.
+__global__ void k_scc_bwd_init(uint32_t n, uint32_t L, const uint32_t* __restrict__ col,
+                               const uint32_t* __restrict__ ids, uint32_t* __restrict__ bw,
+                               uint32_t* __restrict__ act) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const uint32_t c = col[v];
+    const bool root = c != kInf && c == (ids ? ids[v] : (uint32_t)v);
+    bw[v] = root ? c + 1u : 0u;
+    if (root) act[v / L] = 1u;
+  }
+}
+
+// Reached vertices take their color as label; counts the vertices left.
+__global__ void k_scc_assign(uint32_t n, const uint32_t* __restrict__ col,
+                             const uint32_t* __restrict__ bw, uint32_t* __restrict__ lab,
+                             uint32_t* __restrict__ left) {
+  uint32_t c = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    uint32_t l = lab[v];
+    if (l == kInf && bw[v] != 0u) lab[v] = l = col[v];
+    c += l == kInf ? 1u : 0u;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(left, c);
+}
+
+constexpr int kTrPlanKey = -7;  // plan over the transpose DSSS (adjoint, SCC)
+
+nx_status tr_plan(nx_graph* g, nx_graph::Plan** out) {
+  auto& slot = g->plans[kTrPlanKey];
+  if (!slot) {
+    slot.reset(new nx_graph::Plan());
+    PlanOut plan;
+    std::vector<const Dsss*> ds{&g->tr};
+    plan_tiles(g, ds, 0, g->geo.P, 0, g->geo.P, true, target_block_edges(g->m), plan);
+    NX_TRY(upload_items(g, plan, *slot));
+    slot->na = (uint32_t)plan.items.size();
+  }
+  NX_TRY(ensure_split(g, slot->slots));
+  *out = slot.get();
+  return NX_OK;
+}
+
+nx_status scc_impl(nx_graph* g, uint32_t max_sweeps, nx_run_stats* st) {
+  const uint32_t n = g->geo.n, P = g->geo.P;
+  cudaStream_t s = stream();
+  NX_TRY(ensure_resident(g));
+  NX_TRY(prepare(g));
+  for (int k = 0; k < 2; ++k) NX_TRY(ensure(g->aux[k], (size_t)n * 4));
+  NX_TRY(ensure(g->ybuf, (size_t)n * 4));  // labels while the rounds run
+  // plans: tiles over the forward DSSS and over the transpose
+  const int fkey = ((int)NX_SPU * 16 + 1) * 4096 * 2048;
+  auto& fslot = g->plans[fkey];
+  if (!fslot) {
+    fslot.reset(new nx_graph::Plan());
+    PlanOut plan;
+    std::vector<const Dsss*> ds{&g->fwd};
+    plan_tiles(g, ds, 0, P, 0, P, true, target_block_edges(g->m), plan);
+    NX_TRY(upload_items(g, plan, *fslot));
+    fslot->na = (uint32_t)plan.items.size();
+  }
+  NX_TRY(ensure_split(g, fslot->slots));
+  nx_graph::Plan* tpl = nullptr;
+  NX_TRY(tr_plan(g, &tpl));
+  nx_params p{};
+  p.alpha = 0.85f;
+  SweepArgs fa = base_args(g, NX_BFS, p, nullptr);
+  fa.items = fslot->items.as<Item>();
+  fa.split = g->split_buf.p;
+  SweepArgs ba = fa;
+  ba.src[0].ew = g->tr.ew.as<uint32_t>();
+  ba.src[0].wt = nullptr;
+  ba.src[0].piece_off = g->tr.piece_off.as<uint64_t>();
+  ba.items = tpl->items.as<Item>();
+  const uint32_t* ids = g->relabeled ? g->old_of_new.as<uint32_t>() : nullptr;
+  uint32_t* lab = g->ybuf.as<uint32_t>();
+  uint32_t* col[2] = {g->val[0].as<uint32_t>(), g->val[1].as<uint32_t>()};
+  uint32_t* bw[2] = {g->aux[0].as<uint32_t>(), g->aux[1].as<uint32_t>()};
+  uint32_t* act[2] = {g->act[0].as<uint32_t>(), g->act[1].as<uint32_t>()};
+  Scal sc = scal_of(g);
+  uint32_t* left = reinterpret_cast<uint32_t*>(g->scal.as<unsigned char>() + 36);
+  if (g->hact.bytes < ((size_t)P + 1) * 4) NX_TRY(g->hact.alloc(((size_t)P + 1) * 4));
+  uint32_t* hact = g->hact.as<uint32_t>();
+  const unsigned gb = grid_for(n);
+  EventPair ev;
+  NX_TRY(ev.create());
+  NX_CUDA(cudaMemsetAsync(lab, 0xFF, (size_t)n * 4, s));
+  NX_CUDA(cudaEventRecord(ev.e0, s));
+  uint32_t sweeps = 0, rounds = 0, cc = 0;
+  uint64_t swept = 0;
+  uint32_t remaining = n;
+  // one propagation to a fixed point: sweeps until no interval changed
+  auto propagate = [&](ProgKind K, SweepArgs& a, uint32_t nitems, uint32_t** vals, int& cur,
+                       uint32_t& ca) -> nx_status {
+    for (;;) {
+      if (sweeps >= max_sweeps) return NX_OK;
+      a.gsrc = vals[cur];
+      a.vold = vals[cur];
+      a.vnew = vals[1 - cur];
+      a.act_in = act[ca];
+      a.act_out = act[1 - ca];
+      NX_TRY(launch_sweep(K, a, nitems, s));
+      ++sweeps;
+      swept += g->m;
+      cur ^= 1;
+      ca ^= 1;
+      NX_CUDA(cudaMemcpyAsync(hact, sc.act_count, 4, cudaMemcpyDeviceToHost, s));
+      NX_CUDA(cudaStreamSynchronize(s));
+      if (hact[0] == 0) return NX_OK;
+    }
+  };
+  while (remaining && sweeps < max_sweeps) {
+    ++rounds;
+    int cf = 0, cb = 0;
+    uint32_t ca = 0;
+    k_scc_fwd_init<<<gb, 256, 0, s>>>(n, lab, ids, col[0]);
+    NX_LAUNCH_CHECK();
+    std::vector<uint32_t> ones(P, 1u);
+    NX_CUDA(cudaMemcpyAsync(act[0], ones.data(), (size_t)P * 4, cudaMemcpyHostToDevice, s));
+    NX_CUDA(cudaMemsetAsync(act[1], 0, (size_t)P * 4, s));
+    NX_TRY(propagate(PK_SCCF, fa, fslot->na, col, cf, ca));
+    if (sweeps >= max_sweeps) break;
+    const uint32_t* colf = col[cf];
+    NX_CUDA(cudaMemsetAsync(act[ca], 0, (size_t)P * 4, s));
+    NX_CUDA(cudaMemsetAsync(act[1 - ca], 0, (size_t)P * 4, s));
+    k_scc_bwd_init<<<gb, 256, 0, s>>>(n, g->geo.L, colf, ids, bw[0], act[ca]);
+    NX_LAUNCH_CHECK();
+    ba.aux_u32 = colf;
+    NX_TRY(propagate(PK_SCCB, ba, tpl->na, bw, cb, ca));
+    NX_CUDA(cudaMemsetAsync(left, 0, 4, s));
+    k_scc_assign<<<gb, 256, 0, s>>>(n, colf, bw[cb], lab, left);
+    NX_LAUNCH_CHECK();
+    NX_CUDA(cudaMemcpyAsync(&remaining, left, 4, cudaMemcpyDeviceToHost, s));
+    NX_CUDA(cudaStreamSynchronize(s));
+    if (sweeps >= max_sweeps) break;
+  }
+  NX_CUDA(cudaMemcpyAsync(col[cc], lab, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  NX_CUDA(cudaEventRecord(ev.e1, s));
+  float ms = 0.f;
+  NX_TRY(ev.elapsed(&ms));
+  g->cur = cc;
+  g->last_prog = NX_SCC;
+  g->values_set_for = -1;
+  if (st) {
+    memset(st, 0, sizeof *st);
+    st->iters_done = sweeps;
+    st->Q = rounds;  // coloring rounds
+    st->strategy = NX_SPU;
+    st->ms = ms;
+    st->edges_swept = swept;
+    st->bytes_model = (uint64_t)sweeps * (4 * g->m + 12 * (uint64_t)n);
+    st->launches = sweeps + 3 * rounds;
+  }
+  return NX_OK;
+}
+
 // ---------------------------------------------------------------- adjoint
 // dL/dw_e = a r_u / W_u (lambda_v - y_u) for edge e = (u, v) in caller order;
 // dL/dt_v = (1 - a) lambda_v.
@@ -1032,7 +1398,6 @@ __global__ void k_partial_sum(const float* __restrict__ x, uint32_t n, double* _
   }
 }
 
-constexpr int kAdjPlanKey = -7;
 
 nx_status adjoint_impl(nx_graph* g, const float* grad_r, uint32_t K, float* grad_w, float* grad_t,
                        int dev, nx_run_stats* st) {
@@ -1060,16 +1425,9 @@ nx_status adjoint_impl(nx_graph* g, const float* grad_r, uint32_t K, float* grad
   k_sum_parts<<<1, 256, 0, s>>>(g->init_part.as<double>(), gb, sc.dm);
   NX_LAUNCH_CHECK();
   // plan over the transpose DSSS
-  auto& slot = g->plans[kAdjPlanKey];
-  if (!slot) {
-    slot.reset(new nx_graph::Plan());
-    PlanOut plan;
-    std::vector<const Dsss*> ds{&g->tr};
-    plan_tiles(g, ds, 0, P, 0, P, true, target_block_edges(m), plan);
-    NX_TRY(upload_items(g, plan, *slot));
-    slot->na = (uint32_t)plan.items.size();
-  }
-  NX_TRY(ensure_split(g, slot->slots));
+  nx_graph::Plan* slotp = nullptr;
+  NX_TRY(tr_plan(g, &slotp));
+  auto* slot = slotp;
   nx_params p{};
   p.alpha = g->wpr_alpha;
   SweepArgs a = base_args(g, NX_WPR, p, nullptr);
@@ -1210,6 +1568,7 @@ nx_status multi_impl(nx_graph** gs, uint32_t count, nx_program prog, float alpha
   uint64_t edges = 0;
   for (uint32_t gi = 0; gi < count; ++gi) {
     nx_graph* g = gs[gi];
+    NX_TRY(ensure_resident(g));
     NX_TRY(prepare(g));
     NX_TRY(initialize(g, prog, p, nullptr, nullptr));  // sets cur = 0
     g->values_set_for = -1;
@@ -1403,6 +1762,7 @@ extern "C" nx_status nx_graph_get_info(const nx_graph* g, nx_graph_info* info) {
   info->build_ms = g->build_ms;
   info->has_transpose = g->has_tr;
   info->has_weights = g->has_w;
+  info->host_bytes = g->host_bytes();
   return NX_OK;
 }
 
@@ -1410,8 +1770,14 @@ extern "C" nx_status nx_run(nx_graph* g, nx_program program, const nx_params* pa
                             uint32_t iters, nx_strategy strategy, uint64_t mem_budget_bytes,
                             nx_run_stats* stats) {
   if (!g) return nx::invalid("nx_run: graph is NULL");
-  if ((int)program < 0 || (int)program > 4) return nx::invalid("nx_run: unknown program");
+  if ((int)program < 0 || (int)program > 5) return nx::invalid("nx_run: unknown program");
   if ((int)strategy < 0 || (int)strategy > 5) return nx::invalid("nx_run: unknown strategy");
+  if (program == NX_SCC) {
+    if (!g->has_tr) return nx::invalid("nx_run: SCC needs the transpose DSSS (NX_WITH_TRANSPOSE)");
+    if ((strategy != NX_SPU && strategy != NX_AUTO) || mem_budget_bytes)
+      return nx::invalid("nx_run: SCC runs under SPU without a budget");
+    return nx::scc_impl(g, iters, stats);
+  }
   nx_params p{};
   p.alpha = 0.85f;
   if (params) p = *params;
@@ -1433,6 +1799,7 @@ extern "C" nx_status nx_adjoint_wpr(nx_graph* g, const float* grad_r, uint32_t a
   if (g->last_prog != NX_WPR)
     return nx::invalid("nx_adjoint_wpr: run NX_WPR first (its ranks are the forward state)");
   if (adj_terms == 0) return nx::invalid("nx_adjoint_wpr: adj_terms must be >= 1");
+  NX_TRY(nx::ensure_resident(g));
   return nx::adjoint_impl(g, grad_r, adj_terms, grad_w, grad_t, ptrs_are_device, stats);
 }
 
@@ -1440,7 +1807,8 @@ extern "C" nx_status nx_run_multi(nx_graph** graphs, uint32_t count, nx_program 
                                   float alpha, uint32_t iters, nx_run_stats* stats) {
   if (!graphs || count == 0) return nx::invalid("nx_run_multi: no graphs");
   if (program == NX_PPR) return nx::invalid("nx_run_multi: PPR needs a teleport; use PR, WPR, BFS, WCC");
-  if ((int)program < 0 || (int)program > 4) return nx::invalid("nx_run_multi: unknown program");
+  if ((int)program < 0 || (int)program > 4)
+    return nx::invalid("nx_run_multi: unknown program (SCC runs through nx_run)");
   if (!(alpha >= 0.f && alpha < 1.f)) return nx::invalid("nx_run_multi: alpha must be in [0, 1)");
   for (uint32_t q = 0; q < count; ++q) {
     const nx_graph* g = graphs[q];
@@ -1505,7 +1873,8 @@ extern "C" nx_status nx_set_values(nx_graph* g, nx_program program, const void* 
                                    int32_t in_is_device) {
   if (!g || !in) return nx::invalid("nx_set_values: NULL argument");
   if (count != g->geo.n) return nx::invalid("nx_set_values: count must equal n");
-  if ((int)program < 0 || (int)program > 4) return nx::invalid("nx_set_values: unknown program");
+  if ((int)program < 0 || (int)program > 4)
+    return nx::invalid("nx_set_values: unknown program (SCC does not resume)");
   NX_TRY(nx::prepare(g));
   if (g->relabeled) {  // caller order -> internal order
     nx::DevBuf tmp;
@@ -1604,6 +1973,7 @@ extern "C" nx_status nx_dsss_export(const nx_graph* g, int32_t transpose, uint32
                                     uint32_t* dst, uint64_t* sub_off) {
   if (!g || !src || !dst) return nx::invalid("nx_dsss_export: NULL argument");
   if (transpose && !g->has_tr) return nx::invalid("nx_dsss_export: no transpose DSSS");
+  NX_TRY(nx::ensure_resident(const_cast<nx_graph*>(g)));
   const nx::Dsss& d = transpose ? g->tr : g->fwd;
   const uint64_t m = g->m, np = (uint64_t)g->geo.P * g->geo.ntiles;
   nx::DevBuf s, t;

@@ -134,17 +134,24 @@ nx_status prefer_l1(const void* fn, int threads, size_t smem);
 // swapped (its "destination" is the original source).
 struct Dsss {
   uint64_t m = 0;
-  DevBuf ew;         // uint32 [round_up(m,8)+8]: ((dst - tile_start) << lb) | src_local
-  DevBuf wt;         // float  [same]: normalised weight of each edge (weighted graphs)
+  uint64_t words = 0;  // edge words with padding: round_up(m, kEdgeAlign) + kEdgeAlign
+  DevBuf ew;         // uint32 [dev_words]: ((dst - tile_start) << lb) | src_local
+  DevBuf wt;         // float  [words]: normalised weight of each edge (weighted graphs)
   DevBuf piece_off;  // uint64 [npieces+1]
   DevBuf hub_off;    // uint64 [npieces+1]: hub entries before each piece
   DevBuf hub_dst;    // uint16 [D]: destination offset in its tile of each hub entry
   uint64_t D = 0;
   std::vector<uint64_t> h_piece_off;
-  // Pinned host copy of the edge words of streamed shards (MPU / budgets).
-  PinnedBuf h_ew;    // holds words [h_ew_first, m) (rounded to 8)
+  // Residency under a device budget: words [0, dev_words) of the edge array
+  // are on the device; the pinned host image h_ew holds words
+  // [h_ew_first, words) (h_ew_first <= dev_words, so together they hold every
+  // word). Without a budget dev_words == words and h_ew is empty.
+  uint64_t dev_words = 0;
+  PinnedBuf h_ew;
   uint64_t h_ew_first = 0;
-  uint32_t dev_cols = 0;  // shards [0, dev_cols) are held on the device
+  // Arrays moved whole to pinned host memory while a budgeted run does not
+  // need them on the device (hub index, weights).
+  PinnedBuf h_hub_dst, h_wt;
 };
 
 struct Geometry {
@@ -184,6 +191,7 @@ struct nx_graph {
   nx::DevBuf outdeg;   // uint32 [n]
   nx::DevBuf wsum;     // float [n]  W_u (weighted)
   nx::DevBuf orig_src, orig_dst;  // uint32 [m] caller order (weighted: edge grads)
+  nx::PinnedBuf h_orig_src, h_orig_dst;  // their host copies while offloaded
   // Degree-ordered ids (NX_RELABEL): internal id k holds caller vertex
   // old_of_new[k]; every vertex-indexed input and output is mapped at the ABI.
   bool relabeled = false;
@@ -222,6 +230,7 @@ struct nx_graph {
   nx::PinnedBuf hact;       // pinned host copy of the activity count + flags [P + 1]
   nx::DevBuf accres;        // MPU resident-column accumulators
   uint64_t device_bytes() const;
+  uint64_t host_bytes() const;
 };
 
 namespace nx {
@@ -248,5 +257,16 @@ nx_status gather_u32(const uint32_t* idx, const void* in, void* out, uint64_t n)
 // are device pointers and must not alias.
 nx_status vertex_to_internal(const nx_graph* g, const void* in, void* out);
 nx_status vertex_to_caller(const nx_graph* g, const void* in, void* out);
+
+// Residency (nx_engine.cu). set_edge_residency keeps words [0, dev_words) of
+// d's edge array on the device and words [host_first, words) in pinned host
+// memory (host_first <= dev_words), moving data between the two as needed.
+// ensure_resident brings every array of the graph back to the device and
+// frees the host copies (entry points that read the whole graph call it).
+nx_status set_edge_residency(Dsss& d, uint64_t dev_words, uint64_t host_first);
+nx_status ensure_resident(nx_graph* g);
+bool fully_resident(const nx_graph* g);
+nx_status move_to_host(DevBuf& d, PinnedBuf& h);
+nx_status move_to_device(PinnedBuf& h, DevBuf& d);
 }  // namespace nx
 

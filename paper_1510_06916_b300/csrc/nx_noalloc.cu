@@ -88,6 +88,9 @@ extern "C" nx_status nx_pagerank_step_noalloc(const nx_graph* g, float alpha, co
   if (g->relabeled)  // mapping caller order would need scratch of n entries
     return nx::invalid("nx_pagerank_step_noalloc: the graph was built with NX_RELABEL");
   const uint32_t ntiles = g->geo.ntiles, n = g->geo.n;
+  if (!nx::fully_resident(g))
+    return nx::invalid("nx_pagerank_step_noalloc: part of the graph is in host memory after a run "
+                       "with a device budget; run nx_run without a budget first");
   if (ntiles > nx::kMaxTiles)
     return nx::invalid("nx_pagerank_step_noalloc: the graph has more destination tiles than the "
                        "4 MiB scratch holds (at most 523,232)");

@@ -74,6 +74,21 @@ struct MinU {  // BFS / WCC: min of uint32
   }
 };
 
+struct MaxU {  // SCC backward reach: max of uint32 (0 = nothing reached)
+  using V = uint32_t;
+  static constexpr bool compensated = false;
+  __device__ static V identity() { return 0u; }
+  __device__ static V op(V a, V b) { return a > b ? a : b; }
+  __device__ static void emit(Acc<V> acc, uint32_t k, V v) {
+    if (v != 0u) atomicMax(acc.hi + k, v);
+  }
+  __device__ static void emit_short(Acc<V> acc, uint32_t k, V v) { emit(acc, k, v); }
+  __device__ static V read(Acc<V> acc, uint32_t k) { return acc.hi[k]; }
+  __device__ static void emit_global(V* p, V v) {
+    if (v > *p) atomicMax(p, v);
+  }
+};
+
 // Load of a gathered source value (random 4-byte access). NX_GATHER_MODE picks
 // the cache operator: 0 = read-only path (ld.global.nc), 1 = L2 only (.cg).
 #ifndef NX_GATHER_MODE
@@ -123,6 +138,16 @@ struct Prog<PK_BFS> : MinU {  // depth[u] + 1 (infinity stays infinity)
 };
 template <>
 struct Prog<PK_WCC> : MinU {  // label[u]
+  static constexpr bool weighted = false;
+  __device__ static uint32_t gather(uint32_t raw, const uint32_t*, uint32_t, float) { return raw; }
+};
+template <>
+struct Prog<PK_SCCF> : MinU {  // color[u] (assigned: 0xFFFFFFFF, the identity)
+  static constexpr bool weighted = false;
+  __device__ static uint32_t gather(uint32_t raw, const uint32_t*, uint32_t, float) { return raw; }
+};
+template <>
+struct Prog<PK_SCCB> : MaxU {  // reach value of the out-neighbour v (transpose DSSS)
   static constexpr bool weighted = false;
   __device__ static uint32_t gather(uint32_t raw, const uint32_t*, uint32_t, float) { return raw; }
 };
@@ -425,11 +450,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
   const uint32_t tb = a.col_tb[j], nt = a.col_tb[j + 1] - tb;
 
   if (a.mode == 3) {  // epilogue from the stored accumulators of resident columns
-    const V* ar = static_cast<const V*>(a.accres);
-    for (uint32_t k = threadIdx.x; k < T; k += kThreads) acc.hi[k] = ar[ts + k];
+    const V* ar = static_cast<const V*>(a.accres) + (ts - a.acc_base);
+    for (uint32_t k = threadIdx.x; k < T; k += kThreads) acc.hi[k] = ar[k];
   } else if (a.acc_in && it.sub == 0) {  // banded sweep: continue from the earlier bands
-    const V* ai = static_cast<const V*>(a.acc_in);
-    for (uint32_t k = threadIdx.x; k < T; k += kThreads) acc.hi[k] = ai[ts + k];
+    const V* ai = static_cast<const V*>(a.acc_in) + (ts - a.acc_base);
+    for (uint32_t k = threadIdx.x; k < T; k += kThreads) acc.hi[k] = ai[k];
   } else {
     for (uint32_t k = threadIdx.x; k < T; k += kThreads) acc.hi[k] = PG::identity();
   }
@@ -531,10 +556,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
     const uint16_t* hd = a.hub_dst[sx];
     const uint64_t h0 = ho[pc], h1 = ho[pc + 1];
     if (j < a.q_res) {  // destination resident: update it in place
-      V* ar = static_cast<V*>(a.accres);
+      V* ar = static_cast<V*>(a.accres) + (ts - a.acc_base);
       for (uint64_t k = h0 + threadIdx.x; k < h1; k += kThreads) {
         const uint32_t o = hd[k];
-        PG::emit_global(ar + ts + o, PG::read(acc, o));
+        PG::emit_global(ar + o, PG::read(acc, o));
       }
     } else {  // destination on the host side: write the hub
       V* hv = static_cast<V*>(a.hubs[sx]);
@@ -543,8 +568,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
     return;
   }
   if (a.mode == 2) {
-    V* ar = static_cast<V*>(a.accres);
-    for (uint32_t k = threadIdx.x; k < T; k += kThreads) ar[ts + k] = PG::read(acc, k);
+    V* ar = static_cast<V*>(a.accres) + (ts - a.acc_base);
+    for (uint32_t k = threadIdx.x; k < T; k += kThreads) ar[k] = PG::read(acc, k);
     return;
   }
 
@@ -590,9 +615,17 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
       const uint32_t v = ts + k - a.out_base;
       const uint32_t o = vo[v];
       const uint32_t ak = acc.hi[k];
-      const uint32_t nv = ak < o ? ak : o;
+      uint32_t nv;
+      if constexpr (K == PK_SCCF) {  // assigned vertices keep their mark
+        nv = (o == kInf || ak >= o) ? o : ak;
+      } else if constexpr (K == PK_SCCB) {  // reached once an out-neighbour of its color is
+        const uint32_t c = a.aux_u32[ts + k];
+        nv = (o == 0u && c != kInf && ak == c + 1u) ? ak : o;
+      } else {
+        nv = ak < o ? ak : o;
+      }
       vn[v] = nv;
-      changed |= nv < o;
+      changed |= nv != o;
     }
     if (__syncthreads_or(changed) && threadIdx.x == 0) a.act_out[j] = 1u;
   }
@@ -776,6 +809,8 @@ const void* sweep_fn(ProgKind kind) {
     case PK_WCC: return reinterpret_cast<const void*>(k_sweep<PK_WCC>);
     case PK_PRD: return reinterpret_cast<const void*>(k_sweep<PK_PRD>);
     case PK_ADJ: return reinterpret_cast<const void*>(k_sweep<PK_ADJ>);
+    case PK_SCCF: return reinterpret_cast<const void*>(k_sweep<PK_SCCF>);
+    case PK_SCCB: return reinterpret_cast<const void*>(k_sweep<PK_SCCB>);
   }
   return nullptr;
 }
@@ -813,6 +848,8 @@ nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaS
     case PK_WCC: k_sweep<PK_WCC><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_PRD: k_sweep<PK_PRD><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_ADJ: k_sweep<PK_ADJ><<<nitems, kThreads, smem, s>>>(a); break;
+    case PK_SCCF: k_sweep<PK_SCCF><<<nitems, kThreads, smem, s>>>(a); break;
+    case PK_SCCB: k_sweep<PK_SCCB><<<nitems, kThreads, smem, s>>>(a); break;
   }
   NX_LAUNCH_CHECK();
   return NX_OK;

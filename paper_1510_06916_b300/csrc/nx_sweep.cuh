@@ -14,7 +14,14 @@ struct SweepSrc {
 // array), used by the allocation-free single-step entry point.
 // PK_ADJ: the weighted-PageRank adjoint step over the transpose DSSS,
 // lambda'_u = g_u + a (sum_v w^_uv lambda_v + [outdeg(u) = 0] S / n), S = sum lambda.
-enum ProgKind : int { PK_PR = 0, PK_WPR = 1, PK_BFS = 2, PK_WCC = 3, PK_PRD = 4, PK_ADJ = 5 };
+// PK_SCCF / PK_SCCB: the two propagations of strongly connected components
+// (coloring): the forward min-color sweep over unassigned vertices (color
+// 0xFFFFFFFF = assigned, never updated) and the backward max-reach sweep over
+// the transpose DSSS (value 0 = not reached, color + 1 = reached; a vertex is
+// reached when an out-neighbour of its own color is; aux_u32 = the colors).
+enum ProgKind : int {
+  PK_PR = 0, PK_WPR = 1, PK_BFS = 2, PK_WCC = 3, PK_PRD = 4, PK_ADJ = 5, PK_SCCF = 6, PK_SCCB = 7
+};
 
 struct SweepArgs {
   SweepSrc src[2];
@@ -65,6 +72,8 @@ struct SweepArgs {
   void* hubs[2] = {nullptr, nullptr};  // hub values [D_s]
   uint32_t hub_lo = 0, hub_hi = 0;
   void* accres = nullptr;             // accumulators of resident columns [n_res]
+  uint32_t acc_base = 0;              // vertex id of accres[0] (acc_in too)
+  const uint32_t* aux_u32 = nullptr;  // PK_SCCB: the forward colors
   // staged (non-resident) intervals: the source interval stage_i is read from
   // gstage[0..L); epilogue values of a staged column go to vnew/cnew at
   // v - out_base and previous values come from vold at v - out_base.

@@ -16,12 +16,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "csrc", "libnxgraph.so")
 
 NX_OK, NX_ERR_INVALID_ARG, NX_ERR_OOM, NX_ERR_BUDGET_TOO_SMALL, NX_ERR_CUDA, NX_ERR_TIMEOUT = range(6)
-PR, PPR, WPR, BFS, WCC = range(5)
+PR, PPR, WPR, BFS, WCC, SCC = range(6)
 SPU, DPU, MPU, AUTO, SRC_COARSE, SRC_FINE = range(6)
 HOST_PTRS, DEV_PTRS, WITH_TRANSPOSE, WITH_WEIGHTS, RELABEL = 0, 1, 2, 4, 8
 INF = 0xFFFFFFFF
 
-PROGRAMS = {"pr": PR, "ppr": PPR, "wpr": WPR, "bfs": BFS, "wcc": WCC}
+PROGRAMS = {"pr": PR, "ppr": PPR, "wpr": WPR, "bfs": BFS, "wcc": WCC, "scc": SCC}
 STRATEGIES = {"spu": SPU, "dpu": DPU, "mpu": MPU, "auto": AUTO,
               "src_coarse": SRC_COARSE, "src_fine": SRC_FINE}
 
@@ -57,7 +57,7 @@ class NxGraphInfo(ctypes.Structure):
                 ("lb", ctypes.c_uint32), ("m", ctypes.c_uint64), ("D", ctypes.c_uint64),
                 ("D_t", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("build_ms", ctypes.c_float), ("has_transpose", ctypes.c_int32),
-                ("has_weights", ctypes.c_int32)]
+                ("has_weights", ctypes.c_int32), ("host_bytes", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

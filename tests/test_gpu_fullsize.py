@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 from nxtol import assert_grad_t_close, assert_grad_w_close, assert_pr_close
+from test_gpu_parity import _budget_slack
 from paper_1510_06916_b300 import inputs
 from paper_1510_06916_b300 import nxgraph as nx
 
@@ -40,6 +41,10 @@ def test_rmat26_p64_spu_and_mpu_6gb():
     st = g.run("pr", 10, "mpu", budget=6 * 10**9)
     assert st["streamed_cols"] > 0 and st["Q"] == P
     _pr_close(g.values(), ref, "rmat26 PR MPU 6GB")
+    info = g.info()  # the device holds the budget plus the stated slack only
+    print(f"rmat26 PR MPU 6GB: device {info['device_bytes'] / 1e9:.2f} GB, "
+          f"pinned host {info['host_bytes'] / 1e9:.2f} GB")
+    assert info["device_bytes"] <= 6 * 10**9 + _budget_slack(info, 1), info
     del ref
     bfs = oracle.bfs(n, s, d, 0)
     g.run("bfs", 1000, "spu", root=0)
@@ -53,6 +58,9 @@ def test_rmat26_p64_spu_and_mpu_6gb():
     st = g.run("wcc", 1000, "mpu", budget=6 * 10**9)
     assert st["streamed_cols"] > 0 and st["Q"] == P
     assert (g.values(dtype=np.uint32) == wcc).all()
+    info = g.info()
+    print(f"rmat26 WCC MPU 6GB: device {info['device_bytes'] / 1e9:.2f} GB")
+    assert info["device_bytes"] <= 6 * 10**9 + _budget_slack(info, 2), info
     g.free()
 
 

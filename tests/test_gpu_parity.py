@@ -87,6 +87,78 @@ def test_bfs_max_depth_is_algorithm4_output():
     g.free()
 
 
+# ------------------------------------------------------------------ SCC
+
+@pytest.mark.parametrize("P", [1, 3, 8])
+def test_scc_bitexact_rmat(P):
+    # strongly connected components (Section IV-D) by coloring rounds over the
+    # DSSS and its transpose: labels = smallest id per component, bit-exact
+    for scale, ef, seed in ((12, 4, 3), (14, 8, 17)):
+        n = 1 << scale
+        s, d, _ = rmat(scale, ef, seed)
+        g = nx.Graph(s, d, n, P, transpose=True)
+        st = g.run("scc", 100000)
+        ref = oracle.scc(n, s, d)
+        assert (g.values(dtype=np.uint32) == ref).all(), (scale, P)
+        assert st["Q"] >= 1 and st["iters_done"] >= 2
+        print(f"SCC scale {scale} P={P}: {len(np.unique(ref))} components, "
+              f"{st['Q']} rounds, {st['iters_done']} sweeps")
+        g.free()
+
+
+def test_scc_special_graphs():
+    # a cycle (one component), a path (all singletons), two cycles joined one
+    # way, self-loops, an empty graph, a ragged n
+    n = 37
+    cyc = np.arange(n, dtype=np.uint32)
+    for s, d in ((cyc, (cyc + 1) % n), (cyc[:-1], cyc[1:]),
+                 (np.array([0, 1, 2, 2, 5, 6, 9, 9], np.uint32),
+                  np.array([1, 2, 0, 5, 6, 5, 9, 30], np.uint32)),
+                 (np.zeros(0, np.uint32), np.zeros(0, np.uint32))):
+        for P in (1, 4, 9):
+            g = nx.Graph(s, d, n, P, transpose=True)
+            g.run("scc", 10000)
+            assert (g.values(dtype=np.uint32) == oracle.scc(n, s, d)).all(), (len(s), P)
+            g.free()
+
+
+def test_scc_relabel_and_limits():
+    n = 1 << 13
+    s, d, _ = rmat(13, 6, 29)
+    ref = oracle.scc(n, s, d)
+    g = nx.Graph(s, d, n, 4, transpose=True, relabel=True)
+    g.run("scc", 100000)
+    assert (g.values(dtype=np.uint32) == ref).all()  # smallest caller id, caller order
+    g.free()
+    g = nx.Graph(s, d, n, 4, transpose=True)
+    st = g.run("scc", 3)  # out of sweeps: unassigned vertices keep 0xFFFFFFFF
+    assert st["iters_done"] == 3
+    lab = g.values(dtype=np.uint32)
+    done = lab != nx.INF
+    assert (lab[done] == ref[done]).all()
+    with pytest.raises(nx.NxError):
+        g.run("scc", 10, "dpu")
+    with pytest.raises(nx.NxError):
+        g.run("scc", 10, "spu", budget=1 << 30)
+    g.free()
+    g = nx.Graph(s, d, n, 4)
+    with pytest.raises(nx.NxError):
+        g.run("scc", 10)  # no transpose
+    g.free()
+
+
+def test_scc_rmat22_bitexact():
+    n = 1 << 22
+    s, d, _ = rmat(22, 16, 2)
+    g = nx.Graph(s, d, n, 16, transpose=True)
+    st = g.run("scc", 1000000)
+    ref = oracle.scc(n, s, d)
+    assert (g.values(dtype=np.uint32) == ref).all()
+    print(f"SCC scale 22: {st['Q']} rounds, {st['iters_done']} sweeps, {st['ms']:.1f} ms, "
+          f"largest component {np.bincount(ref).max()} vertices")
+    g.free()
+
+
 def test_invalid_inputs():
     s = np.array([0, 5], np.uint32)
     d = np.array([1, 2], np.uint32)
@@ -313,6 +385,52 @@ def test_spu_streams_shards_from_host(frac):
     st = g.run("wcc", 1000, "spu", budget=budget + int(frac * 4 * m))
     assert st["streamed_cols"] > 0
     assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+
+
+def _budget_slack(info, nds):
+    """Device bytes outside a budget's accounting (intervals 2 n B_a + resident
+    edge words): out-degrees and PageRank contributions (12 n), piece and hub
+    offsets (16 B per piece per DSSS), tile tables, the accumulators of one
+    streamed column (4 L), two staging buffers (at most 64 MB per DSSS each
+    while no streamed sub-shard is larger), plans, split slots and scalars."""
+    n, P, nt, L = info["n"], info["P"], info["ntiles"], info["L"]
+    return (12 * n + 16 * (P * nt + 1) * nds + 8 * (nt + P + 2) + 4 * L
+            + 2 * nds * (64 << 20) + (64 << 20))
+
+
+def test_budget_bounds_device_memory_and_is_undone():
+    # Under a budget, streamed shards, the unread transpose and the hub index
+    # live in pinned host memory only; a later run without a budget brings
+    # them back; results are unchanged throughout.
+    n = 1 << 16
+    s, d, _ = rmat(16, 16, 13)
+    g = nx.Graph(s, d, n, 8, transpose=True)
+    ref = oracle.pagerank(n, s, d, 0.85, 10)
+    wcc = oracle.wcc(n, s, d)
+    m = len(s)
+    for frac in (0.1, 0.5):
+        budget = 2 * n * 4 + int(frac * 4 * m)
+        st = g.run("pr", 10, "mpu", budget=budget)
+        assert st["streamed_cols"] > 0 and st["h2d_bytes"] > 0
+        assert_pr_close(g.values(), ref, f"budget {frac} PR")
+        info = g.info()
+        assert info["device_bytes"] <= budget + _budget_slack(info, 1), (frac, info)
+        assert info["host_bytes"] >= 4 * m  # the unread transpose lives in pinned host memory
+        st = g.run("wcc", 1000, "mpu", budget=budget + int(frac * 4 * m))
+        assert (g.values(dtype=np.uint32) == wcc).all()
+        info = g.info()
+        assert info["device_bytes"] <= budget + int(frac * 4 * m) + _budget_slack(info, 2)
+    # no budget: everything back on the device, same results
+    g.run("pr", 10)
+    assert_pr_close(g.values(), ref, "PR after budgets")
+    back = g.info()
+    assert back["host_bytes"] < 64 << 20
+    gs, gd, _ = g.export()  # reads the whole (restored) DSSS
+    order, _ = oracle.dsss_order(n, 8, s, d)
+    assert (gs == s[order]).all() and (gd == d[order]).all()
+    g.run("wcc", 1000, "dpu")  # hubs restored
+    assert (g.values(dtype=np.uint32) == wcc).all()
+    g.free()
 
 
 # ------------------------------------------------------------------ batched PPR
