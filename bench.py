@@ -11,7 +11,7 @@ needed between steps. `--workload rmat22` measures the scale-22 graph (P = 16,
 20 iterations) instead; its numbers also appear under `extras`.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-       [--workload rmat26|rmat22|rmat16]
+       [--workload rmat26|rmat25|rmat22|rmat16]
 Under torchrun every rank runs its own replica ("replicas only": the sweep has
 no exchange step on one GPU) and rank 0 prints one JSON line. The full extras
 record is printed on the line before it.
@@ -35,6 +35,8 @@ WORKLOADS = {
     # degree-ordered ids (the paper's degreeing) pay once the 268 MB value array exceeds L2
     "rmat26": dict(scale=26, ef=22, seed=5, P=64, iters=10, relabel=True),
     "rmat16": dict(scale=16, ef=16, seed=1, P=4, iters=20),
+    # half the scale-26 graph: small enough for an ncu capture, values above L2
+    "rmat25": dict(scale=25, ef=22, seed=5, P=64, iters=10, relabel=True),
 }
 METRIC = "PageRank GTEPS/iter & HBM roofline %"
 
@@ -454,6 +456,10 @@ def measure_sweep(nx, inputs, torch, w, steps, warmup, world=1, local=0, clocks=
     clock_rec = clk.stop() if clk else None
     ms = ev0.elapsed_time(ev1)
     ms_max = barrier_max(ms, world)
+    # the sweep's loads and gathers alone (no reduction): the practical
+    # ceiling of a sweep that gathers one 4-byte value per edge
+    g.gather_probe(3)
+    probe_ms = g.gather_probe(2 * iters)
     g.free()
     torch.cuda.empty_cache()
     # Roofline of the sweep kernel: algorithmic bytes of one sweep (one
@@ -468,7 +474,12 @@ def measure_sweep(nx, inputs, torch, w, steps, warmup, world=1, local=0, clocks=
     t_sweep = kern_ms / 1e3 / sweeps
     peak, peak_kind = load_peaks()
     achieved = alg / t_sweep / 1e9
+    ceiling = {"probe_ms_per_sweep": probe_ms, "sweep_ms": t_sweep * 1e3,
+               "ceiling_gbs": alg / (probe_ms / 1e3) / 1e9,
+               "ceiling_frac_of_peak": alg / (probe_ms / 1e3) / 1e9 / peak,
+               "sweep_over_ceiling": probe_ms / (t_sweep * 1e3)}
     return {
+        "gather_ceiling": ceiling,
         "value": aggregate_gteps(m, iters, steps, world, ms_max), "ms_max": ms_max,
         "ms_per_step": ms_max / steps, "launches": launches, "clocks": clock_rec,
         "graph": {"D": D, "ntiles": info["ntiles"], "build_ms": info["build_ms"],
@@ -524,7 +535,7 @@ def compact(extras):
         "strategies": ("spu_pr_ms", "dpu_pr_ms", "mpu_pr_ms", "dpu_over_spu_pr",
                        "src_coarse_over_spu_pr", "src_fine_over_spu_pr"),
         "relabel": ("relabel_over_ids",),
-        "gather_ceiling": ("ceiling_gbs", "sweep_over_ceiling"),
+        "gather_ceiling": ("ceiling_gbs", "ceiling_frac_of_peak", "sweep_over_ceiling"),
         "scc": ("ms", "gteps_swept"),
     }
     out = {}
@@ -582,6 +593,7 @@ def main():
     head = measure_sweep(nx, inputs, torch, w, args.steps, args.warmup, world, local, clocks=True)
     roof = dict(head["roofline"])
     roof["traffic"] = traffic_record(args.workload)
+    roof["gather_ceiling_frac"] = head["gather_ceiling"]["sweep_over_ceiling"]
 
     # end to end through the C ABI from pinned host buffers: DSSS build from
     # host edges + the workload's iterations + ranks back to host memory
@@ -631,7 +643,7 @@ def main():
 
     extras = None
     if not args.no_extras:
-        extras = {}
+        extras = {"gather_ceiling": dict(head["gather_ceiling"], workload=config_for(w, args.workload)["workload"])}
         for name, fn in EXTRAS.items():
             try:
                 extras[name] = fn(nx, inputs, torch)

@@ -243,9 +243,10 @@ nx_status nx_set_values(nx_graph* g, nx_program program, const void* in, uint64_
  * sweep per iteration over the DSSS with B values per vertex.
  *   teleport : [n][B] row-major float (vertex-major), host or device
  *   ranks    : output [n][B] float, host or device (same flag)
- * r0 = t and dangling mass spread by each column's t; damping `alpha`.
- * Errors: INVALID_ARG (NULL pointers, B not in [1, 64], iters == 0, alpha
- * outside [0, 1)), OOM, CUDA.
+ * r0 = t and dangling mass spread by each column's t; damping `alpha`
+ * (iters = 0 returns r0 = t).
+ * Errors: INVALID_ARG (NULL pointers, B not in [1, 64], alpha outside
+ * [0, 1)), OOM, CUDA.
  */
 nx_status nx_run_ppr_batch(nx_graph* g, const float* teleport, uint32_t B, uint32_t iters,
                            float alpha, float* ranks, int32_t ptrs_are_device,
@@ -293,6 +294,18 @@ nx_status nx_run_multi(nx_graph** graphs, uint32_t count, nx_program program, fl
  * Errors: INVALID_ARG (NULL, the graph's last run was not NX_BFS), CUDA.
  */
 nx_status nx_bfs_max_depth(const nx_graph* g, int64_t* max_depth);
+
+/*
+ * Measurement aid (no counterpart in the paper): times `sweeps` passes of the
+ * PageRank SPU sweep's memory access pattern alone over the forward DSSS --
+ * the same thread blocks, launches, edge-word loads and one 4-byte source
+ * gather per edge, but no reduction, accumulation or epilogue -- and returns
+ * the mean time of one pass. It bounds from below the time of any sweep that
+ * gathers one value per edge in DSSS order on this GPU.
+ *   ms_per_sweep : host float
+ * Errors: INVALID_ARG (NULL, sweeps == 0), OOM, CUDA.
+ */
+nx_status nx_gather_probe(nx_graph* g, uint32_t sweeps, float* ms_per_sweep);
 
 /*
  * How long a thread block of nx_run_multi's persistent kernel waits at a grid

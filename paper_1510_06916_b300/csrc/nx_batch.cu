@@ -506,7 +506,6 @@ extern "C" nx_status nx_run_ppr_batch(nx_graph* g, const float* teleport, uint32
                                       int32_t ptrs_are_device, nx_run_stats* stats) {
   if (!g || !teleport || !ranks) return nx::invalid("nx_run_ppr_batch: NULL argument");
   if (B == 0 || B > 64) return nx::invalid("nx_run_ppr_batch: B must be in [1, 64]");
-  if (iters == 0) return nx::invalid("nx_run_ppr_batch: iters must be >= 1");
   if (!(alpha >= 0.f && alpha < 1.f)) return nx::invalid("nx_run_ppr_batch: alpha must be in [0, 1)");
   if (g->geo.P > 1024) return nx::invalid("nx_run_ppr_batch: P too large");
   NX_TRY(nx::ensure_resident(g));

@@ -1181,6 +1181,73 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   return NX_OK;
 }
 
+// ---------------------------------------------------------------- gather probe
+// Times the PageRank sweep's loads and gathers alone (PK_PROBE) with the
+// launches an SPU PageRank run would make: the same plan (bands included).
+nx_status probe_impl(nx_graph* g, uint32_t sweeps, float* ms_per_sweep) {
+  const uint32_t n = g->geo.n, P = g->geo.P, L = g->geo.L;
+  NX_TRY(ensure_resident(g));
+  NX_TRY(prepare(g));
+  NX_TRY(ensure(g->aux[0], (size_t)n * 4));
+  NX_TRY(ensure(g->aux[1], (size_t)n * 4));
+  uint32_t band = P;
+  const uint64_t kBandBytes = 128ull << 20;  // the rule of the SPU run
+  if ((uint64_t)n * 4 > kBandBytes && P >= 32)
+    band = (uint32_t)std::max<uint64_t>(1, kBandBytes / ((uint64_t)L * 4));
+  const uint32_t nbands = (uint32_t)ceil_div(P, band);
+  const int key = (((int)NX_SPU * 16 + 1) * 4096) * 2048 + (int)(nbands > 1 ? band : 0);
+  auto& slot = g->plans[key];
+  if (!slot) {
+    slot.reset(new nx_graph::Plan());
+    PlanOut plan;
+    std::vector<const Dsss*> ds{&g->fwd};
+    std::vector<uint32_t> off;
+    const uint64_t blk = target_block_edges(g->m);
+    if (nbands == 1) {
+      plan_tiles(g, ds, 0, P, 0, P, true, blk, plan);
+    } else {
+      for (uint32_t i0 = 0; i0 < P; i0 += band) {
+        off.push_back((uint32_t)plan.items.size());
+        plan_tiles(g, ds, i0, std::min(P, i0 + band), 0, P, true,
+                   std::max<uint64_t>(blk / nbands, 4096), plan);
+      }
+      off.push_back((uint32_t)plan.items.size());
+    }
+    NX_TRY(upload_items(g, plan, *slot));
+    slot->na = (uint32_t)plan.items.size();
+    slot->off = off;
+  }
+  NX_TRY(ensure_split(g, slot->slots));
+  nx_params p{};
+  p.alpha = 0.85f;
+  SweepArgs a = base_args(g, NX_PR, p, nullptr);
+  a.items = slot->items.as<Item>();
+  a.split = g->split_buf.p;
+  a.gsrc = g->aux[0].p;
+  a.vnew = g->aux[1].p;  // the probe's sink (never written in practice)
+  EventPair ev;
+  NX_TRY(ev.create());
+  NX_CUDA(cudaEventRecord(ev.e0, stream()));
+  for (uint32_t q = 0; q < sweeps; ++q) {
+    if (nbands == 1) {
+      NX_TRY(launch_sweep(PK_PROBE, a, slot->na, stream()));
+    } else {
+      for (uint32_t b = 0; b < nbands; ++b) {
+        SweepArgs ab = a;
+        ab.items = a.items + slot->off[b];
+        ab.src_lo = b * band;
+        ab.src_hi = std::min(P, (b + 1) * band);
+        NX_TRY(launch_sweep(PK_PROBE, ab, slot->off[b + 1] - slot->off[b], stream()));
+      }
+    }
+  }
+  NX_CUDA(cudaEventRecord(ev.e1, stream()));
+  float ms = 0.f;
+  NX_TRY(ev.elapsed(&ms));
+  *ms_per_sweep = sweeps ? ms / (float)sweeps : 0.f;
+  return NX_OK;
+}
+
 // ---------------------------------------------------------------- SCC
 // Strongly connected components (Section IV-D names SCC; the paper gives no
 // algorithm) by coloring over the DSSS and its transpose. Each round:
@@ -1820,6 +1887,12 @@ extern "C" nx_status nx_run_multi(nx_graph** graphs, uint32_t count, nx_program 
     if (g->relabeled) return nx::invalid("nx_run_multi: a graph was built with NX_RELABEL");
   }
   return nx::multi_impl(graphs, count, program, alpha, iters, stats);
+}
+
+extern "C" nx_status nx_gather_probe(nx_graph* g, uint32_t sweeps, float* ms_per_sweep) {
+  if (!g || !ms_per_sweep) return nx::invalid("nx_gather_probe: NULL argument");
+  if (sweeps == 0) return nx::invalid("nx_gather_probe: sweeps must be >= 1");
+  return nx::probe_impl(g, sweeps, ms_per_sweep);
 }
 
 extern "C" nx_status nx_set_barrier_limit(uint64_t cycles) {

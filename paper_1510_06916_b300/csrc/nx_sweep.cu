@@ -16,6 +16,7 @@
 // counter) combines the slots in a fixed order, so results do not depend on
 // block scheduling except for the order of shared-memory atomics inside a block.
 #include <mutex>
+#include <type_traits>
 #include <set>
 #include <utility>
 
@@ -141,6 +142,13 @@ struct Prog<PK_WCC> : MinU {  // label[u]
   static constexpr bool weighted = false;
   __device__ static uint32_t gather(uint32_t raw, const uint32_t*, uint32_t, float) { return raw; }
 };
+// The gather probe: the PageRank sweep's loads and gathers without the
+// reduction (each warp step adds its 256 gathered values into one float).
+template <>
+struct Prog<PK_PROBE> : PrSum {
+  static constexpr bool weighted = false;
+  __device__ static float gather(float raw, const uint32_t*, uint32_t, float) { return raw; }
+};
 template <>
 struct Prog<PK_SCCF> : MinU {  // color[u] (assigned: 0xFFFFFFFF, the identity)
   static constexpr bool weighted = false;
@@ -212,6 +220,14 @@ __device__ __forceinline__ void process_step(const EdgeRegs<kEPL>& cur, uint64_t
     V raw = PG::identity();
     if (valid) raw = ld_gather(static_cast<const V*>(g) + u);
     val[k] = valid ? PG::gather(raw, od, u, wf) : PG::identity();
+  }
+  if constexpr (std::is_same<PG, Prog<PK_PROBE>>::value) {
+    float x = 0.f;
+#pragma unroll
+    for (int k = 0; k < kEPL; ++k) x += val[k];
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_down_sync(0xffffffffu, x, d);
+    if (lane == 0) atomicAdd(acc.hi, x);
+    return;
   }
   // runs of equal destination inside the lane: first (head), middle, last (tail)
   uint32_t hk = key[0], ck = key[0];
@@ -492,6 +508,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
         }
         vo += len;
       }
+    }
+    if constexpr (K == PK_PROBE) {  // keep the loads alive, skip everything after them
+      __syncthreads();
+      if (threadIdx.x == 0 && acc.hi[0] == 12345.678f) static_cast<float*>(a.vnew)[0] = acc.hi[0];
+      return;
     }
     // FromHub (Algorithm 6, 7): fold hub entries of pieces (i, t), i in [hub_lo, hub_hi)
     if (a.mode == 0 && it.sub == 0 && a.hub_lo < a.hub_hi) {
@@ -810,6 +831,7 @@ const void* sweep_fn(ProgKind kind) {
     case PK_PRD: return reinterpret_cast<const void*>(k_sweep<PK_PRD>);
     case PK_ADJ: return reinterpret_cast<const void*>(k_sweep<PK_ADJ>);
     case PK_SCCF: return reinterpret_cast<const void*>(k_sweep<PK_SCCF>);
+    case PK_PROBE: return reinterpret_cast<const void*>(k_sweep<PK_PROBE>);
     case PK_SCCB: return reinterpret_cast<const void*>(k_sweep<PK_SCCB>);
   }
   return nullptr;
@@ -838,7 +860,8 @@ nx_status configure_sweep(ProgKind kind, size_t smem) {
 
 nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaStream_t s) {
   if (nitems == 0) return NX_OK;
-  const bool sums = (kind == PK_PR || kind == PK_WPR || kind == PK_PRD || kind == PK_ADJ);
+  const bool sums = (kind == PK_PR || kind == PK_WPR || kind == PK_PRD || kind == PK_ADJ ||
+                     kind == PK_PROBE);
   const size_t smem = (size_t)a.tile_max * (sums ? 8 : 4) + flat_table_bytes(a);
   NX_TRY(configure_sweep(kind, smem));
   switch (kind) {
@@ -849,6 +872,7 @@ nx_status launch_sweep(ProgKind kind, const SweepArgs& a, uint32_t nitems, cudaS
     case PK_PRD: k_sweep<PK_PRD><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_ADJ: k_sweep<PK_ADJ><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_SCCF: k_sweep<PK_SCCF><<<nitems, kThreads, smem, s>>>(a); break;
+    case PK_PROBE: k_sweep<PK_PROBE><<<nitems, kThreads, smem, s>>>(a); break;
     case PK_SCCB: k_sweep<PK_SCCB><<<nitems, kThreads, smem, s>>>(a); break;
   }
   NX_LAUNCH_CHECK();

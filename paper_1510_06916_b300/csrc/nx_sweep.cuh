@@ -20,7 +20,8 @@ struct SweepSrc {
 // the transpose DSSS (value 0 = not reached, color + 1 = reached; a vertex is
 // reached when an out-neighbour of its own color is; aux_u32 = the colors).
 enum ProgKind : int {
-  PK_PR = 0, PK_WPR = 1, PK_BFS = 2, PK_WCC = 3, PK_PRD = 4, PK_ADJ = 5, PK_SCCF = 6, PK_SCCB = 7
+  PK_PR = 0, PK_WPR = 1, PK_BFS = 2, PK_WCC = 3, PK_PRD = 4, PK_ADJ = 5, PK_SCCF = 6, PK_SCCB = 7,
+  PK_PROBE = 8  // the PageRank sweep's edge loads and gathers alone (a measurement)
 };
 
 struct SweepArgs {

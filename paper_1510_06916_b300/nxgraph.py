@@ -30,6 +30,7 @@ EXPORTS = [
     "nx_get_values", "nx_set_values", "nx_run_ppr_batch", "nx_adjoint_wpr", "nx_run_multi",
     "nx_graph_free", "nx_io_model", "nx_dsss_export", "nx_pagerank_step_noalloc",
     "nx_autotune", "nx_get_relabel", "nx_bfs_max_depth", "nx_set_barrier_limit",
+    "nx_gather_probe",
 ]
 
 
@@ -97,6 +98,7 @@ def lib():
                                   ctypes.POINTER(u32), vp, ctypes.c_char_p]
         L.nx_bfs_max_depth.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         L.nx_set_barrier_limit.argtypes = [u64]
+        L.nx_gather_probe.argtypes = [vp, u32, ctypes.POINTER(f32)]
         L.nx_graph_free.argtypes = [vp]
         L.nx_graph_free.restype = None
         L.nx_io_model.argtypes = [i32, d, d, d, d, d, d, d, d, ctypes.POINTER(d),
@@ -257,6 +259,12 @@ class Graph:
         check(lib().nx_run(self._h, PROGRAMS.get(program, program), ctypes.byref(prm), iters,
                            STRATEGIES.get(strategy, strategy), budget, ctypes.byref(st)))
         return st.as_dict()
+
+    def gather_probe(self, sweeps=10) -> float:
+        """ms per pass of the sweep's loads and gathers alone (no reduction)."""
+        v = ctypes.c_float()
+        check(lib().nx_gather_probe(self._h, sweeps, ctypes.byref(v)))
+        return v.value
 
     def bfs_max_depth(self) -> int:
         """Algorithm 4's Output for the last BFS run: largest finite depth (-1: none)."""

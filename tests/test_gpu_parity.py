@@ -552,8 +552,10 @@ def test_run_multi_replays_its_cuda_graph():
     st2 = nx.run_multi(graphs, "pr", 15)
     assert st1["Q"] == 0 and st2["Q"] == 1
     for g, v, (n, s, d) in zip(graphs, first, data):
-        assert np.array_equal(g.values(), v)
-        assert_pr_close(v, oracle.pagerank(n, s, d, 0.85, 15), f"replayed n={n}")
+        ref = oracle.pagerank(n, s, d, 0.85, 15)
+        assert_pr_close(v, ref, f"captured n={n}")
+        assert_pr_close(g.values(), ref, f"replayed n={n}")  # (shared-memory atomics
+        # fold in a run-dependent order, so two runs agree to rounding, not bit for bit)
     assert nx.run_multi(graphs, "pr", 16)["Q"] == 0  # another iteration count: new capture
     st3 = nx.run_multi(graphs, "bfs", 30)
     assert st3["Q"] == 0 and nx.run_multi(graphs, "bfs", 30)["Q"] == 1
@@ -768,8 +770,8 @@ def test_relabel_device_pointers_batch_and_adjoint():
     g.adjoint_wpr(gv, 20, dw, dt)
     ref = oracle.wpr_adjoint(n, s, d, w.astype(np.float64), gv.astype(np.float64), 0.85, 20, 20)
     assert_pr_close(g.values(), ref["r"], "relabel WPR")
-    for got, want, what in ((dt, ref["dt"], "dL/dt"), (dw, ref["dw"], "dL/dw")):
-        _grad_close(got, want, f"relabel {what}")
+    assert_grad_t_close(dt, ref["dt"], "relabel dL/dt")
+    assert_grad_w_close(dw, ref, s, d, w, 0.85, "relabel dL/dw")
 
 
 def test_relabel_rejected_where_unsupported():
