@@ -27,6 +27,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -238,6 +240,9 @@ def measure_ppr_batch(nx, inputs, torch, B=64, iters=30, scale=24, seed=3, P=16,
     T = torch.zeros((n, B), dtype=torch.float32, device="cuda")
     T[torch.from_numpy(v).cuda(), torch.from_numpy(b).cuda()] = torch.from_numpy(t).cuda()
     R = torch.empty_like(T)
+    # batch shape (rows in flight, destinations per sub-tile) by the autotuner
+    shapes = [(2, 128), (4, 128), (8, 128), (4, 64), (4, 256)]
+    bi, bms = g.autotune_ppr_batch(T, iters=3, shapes=shapes)
     g.ppr_batch(T, iters=2, out=R)  # warm-up
     _, st = g.ppr_batch(T, iters=iters, out=R)
     t0 = T[:, 0].contiguous()
@@ -253,6 +258,8 @@ def measure_ppr_batch(nx, inputs, torch, B=64, iters=30, scale=24, seed=3, P=16,
                     f"{B} PPR vectors x {iters} iterations",
         "bytes_per_iter": alg, "bytes_formula": "4m + 4D + 2*B*4n",
         "roofline_frac": alg / (st["ms"] / 1e3 / iters) / 1e9 / peak,
+        "batch_shape": {"rows": shapes[bi][0], "sub": shapes[bi][1]},
+        "batch_shape_ms_per_iter": {f"rows={r},sub={q}": t for (r, q), t in zip(shapes, bms)},
         "batched_ms": st["ms"], "single_vector_ms": one["ms"],
         "vector_edges_per_s_batched": m * B * iters / (st["ms"] / 1e3),
         "vector_edges_per_s_single": m * iters / (one["ms"] / 1e3),
@@ -409,14 +416,42 @@ def measure_relabel(nx, inputs, torch, scale=22, seed=2, P=16, iters=20):
 
 
 def measure_autotune(nx, inputs, torch, scale=22, seed=2):
-    """P autotuned over {8, 16, 32, 64} for PageRank on the scale-22 graph."""
+    """P and tile shape autotuned for PageRank on the scale-22 graph: P over
+    {8, 16, 32, 64} with the default tiles, then tile caps 2^10..2^12 and an
+    edge target of 2^15 at each of the two fastest P."""
     n, m = 1 << scale, 16 << scale
     src, dst, _ = inputs.rmat_edges_device(scale, m, seed)
-    P, ms = nx.autotune(src, dst, n, candidates=(8, 16, 32, 64), iters=10)
+    Ps = (8, 16, 32, 64)
+    best, ms = nx.autotune_shape(src, dst, n, [(P, 0, 0) for P in Ps], iters=10)
+    top = [Ps[i] for i in np.argsort(ms)[:2]]
+    shapes = [(P, c, e) for P in top for c, e in ((0, 0), (10, 0), (12, 0), (11, 15))]
+    best2, ms2 = nx.autotune_shape(src, dst, n, shapes, iters=10)
     del src, dst
     torch.cuda.empty_cache()
+    P, cap, edges = shapes[best2]
     return {"workload": f"R-MAT scale {scale} ef 16 seed {seed}, PageRank x10 per candidate",
-            "best_P": P, "ms_per_iter": dict(zip(("8", "16", "32", "64"), ms))}
+            "best_P": P, "best_tile_cap": 1 << (cap or 11),
+            "best_tile_edges": (1 << edges) if edges else "auto",
+            "ms_per_iter_by_P": dict(zip(map(str, Ps), ms)),
+            "ms_per_iter_by_shape": {f"P={p},cap={1 << (c or 11)},edges={(1 << e) if e else 'auto'}": t
+                                     for (p, c, e), t in zip(shapes, ms2)}}
+
+
+def measure_scc(nx, inputs, torch, scale=22, seed=2, P=16):
+    """Strongly connected components of the scale-22 graph (coloring rounds)."""
+    n, m = 1 << scale, 16 << scale
+    src, dst, _ = inputs.rmat_edges_device(scale, m, seed)
+    g = nx.Graph(src, dst, n, P, transpose=True)
+    del src, dst
+    g.run("scc", 1 << 20)  # warm-up
+    st = g.run("scc", 1 << 20)
+    bfs = g.run("bfs", 1000)
+    g.free()
+    torch.cuda.empty_cache()
+    return {"workload": f"R-MAT scale {scale} ef 16 seed {seed}, P={P}, with transpose",
+            "ms": st["ms"], "rounds": st["Q"], "sweeps": st["iters_done"],
+            "gteps_swept": st["edges_swept"] / (st["ms"] / 1e3) / 1e9,
+            "bfs_ms": bfs["ms"], "scc_over_bfs": st["ms"] / bfs["ms"]}
 
 
 def measure_sweep(nx, inputs, torch, w, steps, warmup, world=1, local=0, clocks=False):
@@ -528,15 +563,15 @@ def compact(extras):
     keep = {
         "rmat22": ("gteps", "roofline_frac"),
         "ppr_batch": ("vector_edges_per_s_batched", "speedup_vs_64_single", "roofline_frac",
-                      "batched_ms"),
+                      "batched_ms", "batch_shape"),
         "adjoint": ("adjoint_gteps", "forward_gteps", "adjoint_over_forward"),
         "multi_graph": ("gteps", "multi_ms", "separate_runs_kernel_ms"),
-        "autotune": ("best_P",),
+        "autotune": ("best_P", "best_tile_cap", "best_tile_edges"),
         "strategies": ("spu_pr_ms", "dpu_pr_ms", "mpu_pr_ms", "dpu_over_spu_pr",
                        "src_coarse_over_spu_pr", "src_fine_over_spu_pr"),
         "relabel": ("relabel_over_ids",),
         "gather_ceiling": ("ceiling_gbs", "ceiling_frac_of_peak", "sweep_over_ceiling"),
-        "scc": ("ms", "gteps_swept"),
+        "scc": ("ms", "rounds", "sweeps", "scc_over_bfs"),
     }
     out = {}
     for name, rec in (extras or {}).items():
@@ -678,7 +713,7 @@ def main():
 EXTRAS = {"rmat22": measure_rmat22, "ppr_batch": measure_ppr_batch, "adjoint": measure_adjoint,
           "multi_graph": measure_multi, "autotune": measure_autotune,
           "strategies": measure_strategies, "budget_sweep": measure_budget_sweep,
-          "relabel": measure_relabel}
+          "relabel": measure_relabel, "scc": measure_scc}
 
 
 if __name__ == "__main__":

@@ -82,6 +82,12 @@ typedef enum {
 #define NX_WITH_WEIGHTS 4u       /* w (float, > 0) is given: weighted PageRank     */
 #define NX_RELABEL 8u            /* degree-ordered internal ids (Section III-A
                                     "degreeing"): see nx_get_relabel              */
+/* Tile shape (below the interval level; nx_autotune_shape searches it):
+ * destination tiles of at most 2^k vertices (8 <= k <= 13; default 2^11), and
+ * a tile also ends where its in-edges pass a multiple of 2^e (10 <= e <= 20;
+ * default m / (8 x SMs) clamped to [2^14, 2^16]). 0 = the default.          */
+#define NX_TILE_CAP_LOG2(k) ((uint32_t)(k) << 8)
+#define NX_TILE_EDGES_LOG2(e) ((uint32_t)(e) << 12)
 
 typedef struct nx_graph nx_graph; /* opaque; owns all its device and pinned memory */
 
@@ -347,24 +353,68 @@ void nx_graph_free(nx_graph* g);
 nx_status nx_pagerank_step_noalloc(const nx_graph* g, float alpha, const float* r_in,
                                    float* r_out);
 
+/* A partition and tile shape: P intervals, tiles of at most 2^tile_cap_log2
+ * vertices ending where their in-edges pass multiples of 2^tile_edges_log2
+ * (0 = the default of each; the NX_TILE_* flags). */
+typedef struct {
+  uint32_t P, tile_cap_log2, tile_edges_log2, pad_;
+} nx_shape;
+
 /*
- * Autotuner (Exp 2, Section IV-B2: the paper finds P = 12..48 good): builds
- * the DSSS for every candidate P, times `iters` iterations of `program` under
- * SPU (after one warm-up run) and returns the fastest P.
- *   src, dst, m, n, flags, w : as nx_build_dsss
- *   candidates, count        : P values to try (each 1 <= P <= min(n, 1024))
- *   best_P                   : receives the fastest candidate
+ * Autotuner over the partition and the tile shape (Exp 2, Section IV-B2: the
+ * paper finds P = 12..48 good on its CPU): builds the DSSS for every
+ * candidate, times `iters` iterations of `program` under SPU (after one
+ * warm-up run) and returns the index of the fastest candidate.
+ *   src, dst, m, n, flags, w : as nx_build_dsss (the candidates' shapes
+ *                              replace any NX_TILE_* bits of flags)
+ *   candidates, count        : shapes to try
+ *   best                     : receives the fastest candidate's index
  *   ms_per_iter              : [count] measured ms per iteration (nullable)
  *   cache_path               : text file of earlier results keyed by GPU name,
- *                              n, m, program and candidates (nullable: none).
- *                              A hit returns the stored P without timing
- *                              (ms_per_iter then holds -1).
+ *                              n, m, flags, program and candidates (nullable:
+ *                              none). A hit returns the stored index without
+ *                              timing (ms_per_iter then holds -1).
  * Errors: as nx_build_dsss and nx_run.
+ */
+nx_status nx_autotune_shape(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n,
+                            uint32_t flags, const float* w, nx_program program,
+                            const nx_shape* candidates, uint32_t count, uint32_t iters,
+                            uint32_t* best, float* ms_per_iter, const char* cache_path);
+
+/*
+ * nx_autotune_shape over P alone (tile shape from flags): best_P receives the
+ * fastest of candidates[count].
  */
 nx_status nx_autotune(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n,
                       uint32_t flags, const float* w, nx_program program,
                       const uint32_t* candidates, uint32_t count, uint32_t iters,
                       uint32_t* best_P, float* ms_per_iter, const char* cache_path);
+
+/* Shape of the batched PPR sweep: source rows each lane group keeps in
+ * flight (2, 4 or 8) and destinations per sub-tile (32, 64, 128 or 256; a
+ * block's shared-memory rows). Default {4, 128}. */
+typedef struct {
+  uint32_t rows, sub;
+} nx_batch_shape;
+
+/* Sets the batched-PPR shape used by later nx_run_ppr_batch calls on g.
+ * Errors: INVALID_ARG (NULL, a value outside the sets above). */
+nx_status nx_set_batch_shape(nx_graph* g, uint32_t rows, uint32_t sub);
+
+/*
+ * Autotuner of the batched-PPR shape: runs nx_run_ppr_batch with each
+ * candidate (a warm-up run, then a timed one), keeps the fastest on the graph
+ * (as nx_set_batch_shape) and returns its index. Arguments as
+ * nx_run_ppr_batch (the ranks go to a scratch buffer the tuner allocates);
+ * ms_per_iter, cache_path as nx_autotune_shape (the key holds the GPU name,
+ * n, m, P, tile count, padded B and the candidates).
+ * Errors: INVALID_ARG (NULL, no candidates, iters == 0, a shape out of
+ * range), and those of nx_run_ppr_batch.
+ */
+nx_status nx_autotune_ppr_batch(nx_graph* g, const float* teleport, uint32_t B, uint32_t iters,
+                                float alpha, int32_t ptrs_are_device,
+                                const nx_batch_shape* candidates, uint32_t count, uint32_t* best,
+                                float* ms_per_iter, const char* cache_path);
 
 /* Planner model of Section III-B (Table II): bytes read / written per
  * iteration for strategy s with n vertices, m edges, P intervals, budget B_M,

@@ -31,11 +31,9 @@ namespace {
 
 constexpr int kBT = 256;  // threads per block
 constexpr int kBW = kBT / 32;
-constexpr uint32_t kSub = 128;  // destinations per sub-tile
-#ifndef NX_ROWS
-#define NX_ROWS 4
-#endif
-constexpr int kRows = NX_ROWS;  // source rows in flight per warp
+// Shape (run-time choices, nx_set_batch_shape / nx_autotune_ppr_batch): the
+// destinations per sub-tile (a block's shared-memory rows) and the source
+// rows each lane group keeps in flight (a template parameter: 2, 4 or 8).
 
 struct BItem {
   uint32_t tile, sub;      // tile and sub-tile index inside it
@@ -58,9 +56,10 @@ struct BArgs {
   float* c_out;       // [n][Bp]
   const double* dm_in;  // [Bp]
   double* dm_out;       // [Bp] (accumulated with atomics; zeroed before)
-  float* split;         // split slots [kSub * Bp] each
+  float* split;         // split slots [sub * Bp] each
   uint32_t* ticket;     // per split group
   float alpha;
+  uint32_t sub;         // destinations per sub-tile
 };
 
 // First position in ew[p0, p1) whose destination offset (word >> lb) is >= key.
@@ -84,7 +83,7 @@ __device__ __forceinline__ uint32_t acc_pos(uint32_t b) {
   return (b % 4) * (BP / 4) + b / 4;
 }
 
-template <int BP>
+template <int BP, int kRows>
 __global__ void __launch_bounds__(kBT) k_ppr_batch(const BArgs a) {
   constexpr int C = BP / 32;   // columns per lane in the epilogue
   constexpr int LPE = BP / 4;  // lanes per edge in the sweep
@@ -92,7 +91,8 @@ __global__ void __launch_bounds__(kBT) k_ppr_batch(const BArgs a) {
   constexpr int EPG = 32 / NG; // chunk edges per group
   static_assert(EPG % kRows == 0, "kRows must divide the edges of a group");
   extern __shared__ __align__(16) unsigned char smem[];
-  float* acc = reinterpret_cast<float*>(smem);                          // [kSub][BP]
+  const uint32_t kSub = a.sub;
+  float* acc = reinterpret_cast<float*>(smem);                          // [sub][BP]
   uint64_t* rlo = reinterpret_cast<uint64_t*>(acc + kSub * BP);          // [P]
   uint64_t* rlen = rlo + a.P;                                             // [P + 1] (prefix)
   __shared__ int s_last;
@@ -242,7 +242,8 @@ __global__ void k_subtile_cost(const uint32_t* __restrict__ ew, const uint64_t* 
                                const uint32_t* __restrict__ tile_start,
                                const uint32_t* __restrict__ col_tb, const uint32_t* __restrict__ sub_of,
                                const uint32_t* __restrict__ sub_tile, uint32_t nsub, uint32_t P,
-                               uint32_t L, uint32_t lb, unsigned long long* __restrict__ cost) {
+                               uint32_t L, uint32_t lb, uint32_t kSub,
+                               unsigned long long* __restrict__ cost) {
   const uint64_t total = (uint64_t)nsub * P;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
@@ -314,6 +315,20 @@ __global__ void k_ppr_out(const float* __restrict__ r, uint32_t B, uint32_t BP, 
   }
 }
 
+// The kernel instance for B padded to BP and `rows` source rows in flight.
+void (*batch_kernel(uint32_t BP, uint32_t rows))(const BArgs) {
+  if (BP == 32) {
+    if (rows == 2) return k_ppr_batch<32, 2>;
+    if (rows == 4) return k_ppr_batch<32, 4>;
+    if (rows == 8) return k_ppr_batch<32, 8>;
+  } else {
+    if (rows == 2) return k_ppr_batch<64, 2>;
+    if (rows == 4) return k_ppr_batch<64, 4>;
+    if (rows == 8) return k_ppr_batch<64, 8>;
+  }
+  return nullptr;
+}
+
 unsigned grid_of(uint64_t work) {
   return (unsigned)std::min<uint64_t>(ceil_div(work ? work : 1, 256), (uint64_t)num_sms() * 16);
 }
@@ -322,6 +337,7 @@ nx_status ppr_batch_impl(nx_graph* g, const float* tele_in, uint32_t B, uint32_t
                          float alpha, float* ranks, int dev_ptrs, nx_run_stats* st) {
   const uint32_t n = g->geo.n, P = g->geo.P, L = g->geo.L;
   const uint32_t BP = B <= 32 ? 32 : 64;
+  const uint32_t kSub = g->ppr_sub;
   cudaStream_t s = stream();
   // sub-tiles
   const auto& tsh = g->geo.h_tile_start;
@@ -343,7 +359,7 @@ nx_status ppr_batch_impl(nx_graph* g, const float* tele_in, uint32_t B, uint32_t
   k_subtile_cost<<<grid_of((uint64_t)nsub * P), 256, 0, s>>>(
       g->fwd.ew.as<uint32_t>(), g->fwd.piece_off.as<uint64_t>(), g->geo.tile_start.as<uint32_t>(),
       g->geo.col_tb.as<uint32_t>(), d_sub_of.as<uint32_t>(), d_sub_tile.as<uint32_t>(), nsub, P, L,
-      g->geo.lb, d_cost.as<unsigned long long>());
+      g->geo.lb, kSub, d_cost.as<unsigned long long>());
   NX_LAUNCH_CHECK();
   std::vector<uint64_t> cost(nsub);
   NX_CUDA(cudaMemcpyAsync(cost.data(), d_cost.p, (size_t)nsub * 8, cudaMemcpyDeviceToHost, s));
@@ -436,17 +452,14 @@ nx_status ppr_batch_impl(nx_graph* g, const float* tele_in, uint32_t B, uint32_t
   a.split = d_split.as<float>();
   a.ticket = d_ticket.as<uint32_t>();
   a.alpha = alpha;
+  a.sub = kSub;
   a.r_out = rv.as<float>();
   const size_t smem = (size_t)kSub * BP * 4 + (size_t)(2 * P + 1) * 8;
-  if (smem > 48 * 1024) {
-    if (BP == 32)
-      NX_CUDA(cudaFuncSetAttribute(k_ppr_batch<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    else
-      NX_CUDA(cudaFuncSetAttribute(k_ppr_batch<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
-  NX_TRY(prefer_l1(BP == 32 ? reinterpret_cast<const void*>(k_ppr_batch<32>)
-                             : reinterpret_cast<const void*>(k_ppr_batch<64>),
-                   kBT, smem));
+  void (*kern)(const BArgs) = batch_kernel(BP, g->ppr_rows);
+  if (!kern) return invalid("nx_run_ppr_batch: unsupported rows in flight");
+  if (smem > 48 * 1024)
+    NX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  NX_TRY(prefer_l1(reinterpret_cast<const void*>(kern), kBT, smem));
   EventPair ev;
   NX_TRY(ev.create());
   NX_CUDA(cudaEventRecord(ev.e0, s));
@@ -459,8 +472,7 @@ nx_status ppr_batch_impl(nx_graph* g, const float* tele_in, uint32_t B, uint32_t
     a.dm_in = dm.as<double>() + cur * BP;
     a.dm_out = dm.as<double>() + (1 - cur) * BP;
     NX_CUDA(cudaMemsetAsync(dm.as<double>() + (1 - cur) * BP, 0, BP * 8, s));
-    if (BP == 32) k_ppr_batch<32><<<(unsigned)items.size(), kBT, smem, s>>>(a);
-    else k_ppr_batch<64><<<(unsigned)items.size(), kBT, smem, s>>>(a);
+    kern<<<(unsigned)items.size(), kBT, smem, s>>>(a);
     NX_LAUNCH_CHECK();
     k_seed_apply<<<grid_of(nnz), 256, 0, s>>>(nnz, sv.as<uint32_t>(), sb.as<uint32_t>(),
                                               sval.as<float>(), BP, g->outdeg.as<uint32_t>(),

@@ -23,12 +23,10 @@
 namespace nx {
 namespace {
 
-#ifndef NX_TILE_CAP
-#define NX_TILE_CAP 2048
-#endif
-// Most vertices in a destination tile: the block's accumulators (hi + lo
-// floats) take 8 B per vertex of shared memory.
-constexpr uint32_t kTileMaxCap = NX_TILE_CAP;
+// Most vertices in a destination tile unless the build flags choose another
+// cap (NX_TILE_CAP_LOG2): the block's accumulators (hi + lo floats) take 8 B
+// per vertex of shared memory.
+constexpr uint32_t kTileMaxCap = 2048;
 
 __global__ void k_check_ids(const uint32_t* __restrict__ a, uint64_t m, uint32_t n,
                             uint32_t* __restrict__ bad) {
@@ -260,11 +258,12 @@ nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geom
 }
 
 nx_status build_geometry(nx_graph* g, const uint32_t* deg_a, const uint32_t* deg_b,
-                         uint64_t m_bal, DevBuf& tile_of) {
+                         uint64_t m_bal, uint32_t edges_log2, DevBuf& tile_of) {
   Geometry& geo = g->geo;
   const uint32_t n = geo.n;
   uint64_t E = m_bal / ((uint64_t)num_sms() * 8);
   E = std::max<uint64_t>(16384, std::min<uint64_t>(E, 65536));
+  if (edges_log2) E = 1ull << edges_log2;
   DevBuf pre, flag;
   NX_TRY(pre.alloc((uint64_t)n * sizeof(uint64_t)));
   NX_TRY(flag.alloc((uint64_t)n * sizeof(uint32_t)));
@@ -426,10 +425,12 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   geo.P = P;
   geo.L = (uint32_t)ceil_div(n, P);
   geo.lb = bits_for(geo.L);
-  geo.tile_max = (uint32_t)std::min<uint64_t>(kTileMaxCap, 1ull << (32 - geo.lb));
+  const uint32_t cap_log2 = (flags >> 8) & 0xFu, edges_log2 = (flags >> 12) & 0x1Fu;
+  const uint64_t cap = cap_log2 ? (1ull << cap_log2) : kTileMaxCap;
+  geo.tile_max = (uint32_t)std::min<uint64_t>(cap, 1ull << (32 - geo.lb));
   DevBuf tile_of;
   NX_TRY(build_geometry(g, indeg.as<uint32_t>(), want_t ? g->outdeg.as<uint32_t>() : nullptr,
-                        want_t ? 2 * m : m, tile_of));
+                        want_t ? 2 * m : m, edges_log2, tile_of));
   indeg.release();
   // weights: W_u in FP64, normalised weights in input order
   DevBuf wn;
@@ -505,6 +506,14 @@ extern "C" nx_status nx_build_dsss(const uint32_t* src, const uint32_t* dst, uin
     return nx::invalid("nx_build_dsss: P must be in [1, min(n, 1024)]");
   if (m >= (1ull << 32)) return nx::invalid("nx_build_dsss: m must be < 2^32");
   if (m && (!src || !dst)) return nx::invalid("nx_build_dsss: src/dst is NULL");
+  {
+    const uint32_t cap_log2 = (flags >> 8) & 0xFu, edges_log2 = (flags >> 12) & 0x1Fu;
+    if (cap_log2 && (cap_log2 < 8 || cap_log2 > 13))
+      return nx::invalid("nx_build_dsss: NX_TILE_CAP_LOG2 must be in [8, 13]");
+    if (edges_log2 && (edges_log2 < 10 || edges_log2 > 20))
+      return nx::invalid("nx_build_dsss: NX_TILE_EDGES_LOG2 must be in [10, 20]");
+    if (flags & ~0x1FFFFu) return nx::invalid("nx_build_dsss: unknown flag bits");
+  }
   if ((flags & NX_WITH_WEIGHTS) && m && !w)
     return nx::invalid("nx_build_dsss: NX_WITH_WEIGHTS needs w");
   nx_graph* g = new (std::nothrow) nx_graph();

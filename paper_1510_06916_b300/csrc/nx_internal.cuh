@@ -224,6 +224,8 @@ struct nx_graph {
   nx::DevBuf tele;          // float [n] teleport copy (PPR/WPR)
   nx::DevBuf lam[2], ybuf;  // adjoint scratch
   float wpr_alpha = 0.85f;  // damping of the last weighted PageRank run
+  uint32_t ppr_rows = 4;    // batched PPR: source rows in flight per lane group
+  uint32_t ppr_sub = 128;   // batched PPR: destinations per sub-tile
   nx::DevBuf stage[2];      // staging for streamed shards
   nx::DevBuf vstage[8];     // staging for non-resident intervals (MPU), double-buffered
   nx::PinnedBuf hval[2];    // pinned host values of non-resident intervals

@@ -805,6 +805,13 @@ nx_status launch_multi(ProgKind kind, const SweepArgs* args, const MItem* items,
 nx_status multi_blocks(ProgKind kind, uint32_t tile_max, uint32_t* nblocks) {
   const bool sums = (kind == PK_PR || kind == PK_WPR);
   const size_t smem = (size_t)tile_max * (sums ? 8 : 4) + (size_t)(kThreads + 1) * sizeof(FlatEnt);
+  if (smem > 40 * 1024) {  // tiles above the default cap: opt in to more shared memory
+    const void* fn = kind == PK_PR ? reinterpret_cast<const void*>(k_multi<PK_PR>)
+                   : kind == PK_WPR ? reinterpret_cast<const void*>(k_multi<PK_WPR>)
+                   : kind == PK_BFS ? reinterpret_cast<const void*>(k_multi<PK_BFS>)
+                                    : reinterpret_cast<const void*>(k_multi<PK_WCC>);
+    NX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  }
   int per_sm = 0;
   switch (kind) {
     case PK_PR: NX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi<PK_PR>, kThreads, smem)); break;

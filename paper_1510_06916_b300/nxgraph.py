@@ -30,7 +30,7 @@ EXPORTS = [
     "nx_get_values", "nx_set_values", "nx_run_ppr_batch", "nx_adjoint_wpr", "nx_run_multi",
     "nx_graph_free", "nx_io_model", "nx_dsss_export", "nx_pagerank_step_noalloc",
     "nx_autotune", "nx_get_relabel", "nx_bfs_max_depth", "nx_set_barrier_limit",
-    "nx_gather_probe",
+    "nx_gather_probe", "nx_autotune_shape", "nx_set_batch_shape", "nx_autotune_ppr_batch",
 ]
 
 
@@ -50,6 +50,15 @@ class NxRunStats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class NxShape(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_uint32), ("tile_cap_log2", ctypes.c_uint32),
+                ("tile_edges_log2", ctypes.c_uint32), ("pad_", ctypes.c_uint32)]
+
+
+class NxBatchShape(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_uint32), ("sub", ctypes.c_uint32)]
 
 
 class NxGraphInfo(ctypes.Structure):
@@ -99,6 +108,12 @@ def lib():
         L.nx_bfs_max_depth.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         L.nx_set_barrier_limit.argtypes = [u64]
         L.nx_gather_probe.argtypes = [vp, u32, ctypes.POINTER(f32)]
+        L.nx_autotune_shape.argtypes = [vp, vp, u64, u32, u32, vp, i32, ctypes.POINTER(NxShape),
+                                        u32, u32, ctypes.POINTER(u32), vp, ctypes.c_char_p]
+        L.nx_set_batch_shape.argtypes = [vp, u32, u32]
+        L.nx_autotune_ppr_batch.argtypes = [vp, vp, u32, u32, f32, i32,
+                                            ctypes.POINTER(NxBatchShape), u32, ctypes.POINTER(u32),
+                                            vp, ctypes.c_char_p]
         L.nx_graph_free.argtypes = [vp]
         L.nx_graph_free.restype = None
         L.nx_io_model.argtypes = [i32, d, d, d, d, d, d, d, d, ctypes.POINTER(d),
@@ -170,7 +185,7 @@ class Graph:
     """A DSSS built on the current device (owns it; free() or context exit)."""
 
     def __init__(self, src, dst, n: int, P: int, transpose: bool = False, weights=None,
-                 relabel: bool = False):
+                 relabel: bool = False, tile_cap_log2: int = 0, tile_edges_log2: int = 0):
         if isinstance(src, np.ndarray):
             src = np.ascontiguousarray(src, dtype=np.uint32)
         if isinstance(dst, np.ndarray):
@@ -193,6 +208,7 @@ class Graph:
             flags |= WITH_TRANSPOSE
         if relabel:
             flags |= RELABEL
+        flags |= (tile_cap_log2 << 8) | (tile_edges_log2 << 12)
         wp = None
         if weights is not None:
             wp, wd = _ptr(weights)
@@ -296,6 +312,23 @@ class Graph:
         check(lib().nx_run_ppr_batch(self._h, tp, B, iters, alpha, op, td, ctypes.byref(st)))
         return out, st.as_dict()
 
+    def set_batch_shape(self, rows=4, sub=128):
+        """Batched-PPR shape: source rows in flight per lane group, destinations per sub-tile."""
+        check(lib().nx_set_batch_shape(self._h, rows, sub))
+
+    def autotune_ppr_batch(self, teleport, iters=5, shapes=((2, 128), (4, 128), (8, 128)),
+                           alpha=0.85, cache=None):
+        """Fastest batched-PPR shape [(rows, sub), ...], kept on the graph.
+        Returns (index, ms_per_iter list)."""
+        cand = (NxBatchShape * len(shapes))(*[NxBatchShape(int(r), int(q)) for r, q in shapes])
+        ms = np.empty(len(shapes), dtype=np.float32)
+        best = ctypes.c_uint32()
+        tp, td = _ptr(teleport)
+        check(lib().nx_autotune_ppr_batch(self._h, tp, teleport.shape[1], iters, alpha, td, cand,
+                                          len(shapes), ctypes.byref(best), ms.ctypes.data,
+                                          cache.encode() if cache else None))
+        return int(best.value), ms.tolist()
+
     def adjoint_wpr(self, grad_r, adj_terms, grad_w, grad_t=None) -> dict:
         gp, gd = _ptr(grad_r)
         wp, wd = _ptr(grad_w)
@@ -322,6 +355,25 @@ def autotune(src, dst, n, candidates=(8, 16, 32, 64), program="pr", iters=10, ca
     check(lib().nx_autotune(sp, dp, len(src), n, flags, None, PROGRAMS.get(program, program),
                             cand.ctypes.data, len(cand), iters, ctypes.byref(best), ms.ctypes.data,
                             cache.encode() if cache else None))
+    return int(best.value), ms.tolist()
+
+
+def autotune_shape(src, dst, n, shapes, program="pr", iters=10, cache=None, transpose=False):
+    """Fastest of `shapes` [(P, tile_cap_log2, tile_edges_log2), ...] (0 = default).
+    Returns (index, ms_per_iter list); ms are -1 when served from the cache."""
+    if isinstance(src, np.ndarray):
+        src = np.ascontiguousarray(src, dtype=np.uint32)
+        dst = np.ascontiguousarray(dst, dtype=np.uint32)
+    sp, sd = _ptr(src)
+    dp, _ = _ptr(dst)
+    cand = (NxShape * len(shapes))(*[NxShape(int(p), int(c), int(e), 0) for p, c, e in shapes])
+    ms = np.empty(len(shapes), dtype=np.float32)
+    best = ctypes.c_uint32()
+    flags = (DEV_PTRS if sd else HOST_PTRS) | (WITH_TRANSPOSE if transpose else 0)
+    check(lib().nx_autotune_shape(sp, dp, len(src), n, flags, None,
+                                  PROGRAMS.get(program, program), cand, len(shapes), iters,
+                                  ctypes.byref(best), ms.ctypes.data,
+                                  cache.encode() if cache else None))
     return int(best.value), ms.tolist()
 
 

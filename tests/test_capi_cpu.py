@@ -103,3 +103,33 @@ def test_io_model_rejects_strategies_it_does_not_model():
         with pytest.raises(nx.NxError) as e:
             nx.io_model(s, 1e6, 1e7, 16, 1e8)
         assert e.value.code == nx.NX_ERR_INVALID_ARG
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_device():
+    import ctypes
+
+    L = nx.lib()
+    z = np.zeros(1, np.uint32)
+    # tile shape flags out of range, unknown flag bits
+    for flags in (14 << 8, 7 << 8, 9 << 12, 21 << 12, 1 << 20):
+        h = ctypes.c_void_p()
+        rc = L.nx_build_dsss(z.ctypes.data, z.ctypes.data, 1, 4, 1, flags, None, ctypes.byref(h))
+        assert rc == nx.NX_ERR_INVALID_ARG, flags
+    assert L.nx_set_batch_shape(None, 4, 128) == nx.NX_ERR_INVALID_ARG
+    assert L.nx_gather_probe(None, 1, ctypes.byref(ctypes.c_float())) == nx.NX_ERR_INVALID_ARG
+    assert L.nx_bfs_max_depth(None, ctypes.byref(ctypes.c_int64())) == nx.NX_ERR_INVALID_ARG
+    assert L.nx_set_barrier_limit(1 << 63) == nx.NX_ERR_INVALID_ARG
+    assert L.nx_set_barrier_limit(0) == nx.NX_OK
+    shapes = (nx.NxShape * 1)(nx.NxShape(4, 0, 0, 0))
+    best = ctypes.c_uint32()
+    assert L.nx_autotune_shape(z.ctypes.data, z.ctypes.data, 1, 4, 0, None, 0, shapes, 0, 1,
+                               ctypes.byref(best), None, None) == nx.NX_ERR_INVALID_ARG
+    bshapes = (nx.NxBatchShape * 1)(nx.NxBatchShape(4, 128))
+    assert L.nx_autotune_ppr_batch(None, None, 1, 1, ctypes.c_float(0.85), 0, bshapes, 1,
+                                   ctypes.byref(best), None, None) == nx.NX_ERR_INVALID_ARG
+
+
+def test_scc_is_a_program_of_the_abi():
+    assert nx.PROGRAMS["scc"] == nx.SCC == 5
+    text = open(HDR).read()
+    assert "NX_SCC = 5" in text

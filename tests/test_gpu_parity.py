@@ -627,6 +627,62 @@ def test_autotune_picks_a_candidate_and_caches(tmp_path):
     assert P2 == P and all(x == -1 for x in ms2)  # served from the cache file
 
 
+def test_autotune_shapes_pick_argmin_and_cache(tmp_path):
+    # P and tile shape together; every shape gives the oracle's results
+    n = 1 << 14
+    s, d, _ = rmat(14, 16, 16)
+    cache = str(tmp_path / "tune.txt")
+    shapes = [(4, 0, 0), (4, 9, 0), (8, 12, 12), (16, 13, 15)]
+    best, ms = nx.autotune_shape(s, d, n, shapes, iters=5, cache=cache)
+    assert all(x > 0 for x in ms) and best == int(np.argmin(ms))
+    best2, ms2 = nx.autotune_shape(s, d, n, shapes, iters=5, cache=cache)
+    assert best2 == best and all(x == -1 for x in ms2)
+    ref_pr = oracle.pagerank(n, s, d, 0.85, 20)
+    ref_wcc = oracle.wcc(n, s, d)
+    for P, cap, edges in shapes:
+        g = nx.Graph(s, d, n, P, transpose=True, tile_cap_log2=cap, tile_edges_log2=edges)
+        info = g.info()
+        if cap:
+            assert info["tile_max"] <= 1 << cap
+        g.run("pr", 20)
+        assert_pr_close(g.values(), ref_pr, f"shape {(P, cap, edges)}")
+        g.run("wcc", 1000)
+        assert (g.values(dtype=np.uint32) == ref_wcc).all()
+        g.free()
+    with pytest.raises(nx.NxError):
+        nx.Graph(s, d, n, 4, tile_cap_log2=14)
+
+
+def test_autotune_batch_shape_and_every_shape_matches(tmp_path):
+    import torch
+
+    n = 1 << 13
+    s, d, _ = rmat(13, 16, 14)
+    B = 12
+    T = inputs.ppr_teleports(n, B, 5, max_seeds=40)
+    g = nx.Graph(s, d, n, 4)
+    refs = {b: oracle.personalized_pagerank(n, s, d, T[:, b], 0.85, 15) for b in (0, 7, 11)}
+    for rows in (2, 4, 8):
+        for sub in (32, 64, 128, 256):
+            g.set_batch_shape(rows, sub)
+            R, _ = g.ppr_batch(T, iters=15)
+            for b, ref in refs.items():
+                assert_pr_close(R[:, b], ref, f"batch rows={rows} sub={sub} col {b}")
+    Tt = torch.from_numpy(T).cuda()
+    shapes = [(2, 64), (4, 128), (8, 128), (4, 256)]
+    cache = str(tmp_path / "batch.txt")
+    best, ms = g.autotune_ppr_batch(Tt, iters=5, shapes=shapes, cache=cache)
+    assert all(x > 0 for x in ms) and best == int(np.argmin(ms))
+    best2, ms2 = g.autotune_ppr_batch(Tt, iters=5, shapes=shapes, cache=cache)
+    assert best2 == best and all(x == -1 for x in ms2)
+    R, _ = g.ppr_batch(Tt, iters=15)  # runs with the tuned shape
+    assert_pr_close(R[:, 7].cpu().numpy(), refs[7], "tuned batch")
+    for bad in ((3, 128), (4, 100)):
+        with pytest.raises(nx.NxError):
+            g.set_batch_shape(*bad)
+    g.free()
+
+
 # ------------------------------------------------- Table IV ablation (Exp 1)
 
 @pytest.mark.parametrize("strategy", ["src_coarse", "src_fine"])
