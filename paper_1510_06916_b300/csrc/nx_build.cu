@@ -489,8 +489,10 @@ uint64_t nx_graph::device_bytes() const {
 }
 
 uint64_t nx_graph::host_bytes() const {
-  const nx::PinnedBuf* bufs[] = {&fwd.h_ew, &fwd.h_hub_dst, &fwd.h_wt, &tr.h_ew, &tr.h_hub_dst,
-                                 &tr.h_wt, &h_orig_src, &h_orig_dst, &hval[0], &hval[1], &hact};
+  const nx::PinnedBuf* bufs[] = {&fwd.h_ew, &fwd.h_hub_dst, &fwd.h_wt, &fwd.h_piece_pin,
+                                 &fwd.h_hub_off, &tr.h_ew, &tr.h_hub_dst, &tr.h_wt,
+                                 &tr.h_piece_pin, &tr.h_hub_off, &h_orig_src, &h_orig_dst,
+                                 &hval[0], &hval[1], &hact};
   uint64_t s = 0;
   for (auto* b : bufs) s += b->bytes;
   return s;

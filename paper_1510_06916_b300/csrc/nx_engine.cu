@@ -444,6 +444,8 @@ nx_status ensure_resident(nx_graph* g) {
   for (Dsss* d : all_ds) {
     if (!d) continue;
     NX_TRY(set_edge_residency(*d, d->words, 0));
+    NX_TRY(move_to_device(d->h_piece_pin, d->piece_off));
+    NX_TRY(move_to_device(d->h_hub_off, d->hub_off));
     NX_TRY(move_to_device(d->h_hub_dst, d->hub_dst));
     NX_TRY(move_to_device(d->h_wt, d->wt));
   }
@@ -455,7 +457,9 @@ nx_status ensure_resident(nx_graph* g) {
 bool fully_resident(const nx_graph* g) {
   const Dsss* all_ds[2] = {&g->fwd, g->has_tr ? &g->tr : nullptr};
   for (const Dsss* d : all_ds)
-    if (d && (d->dev_words != d->words || d->h_hub_dst.p || d->h_wt.p)) return false;
+    if (d && (d->dev_words != d->words || d->h_hub_dst.p || d->h_wt.p || d->h_piece_pin.p ||
+              d->h_hub_off.p))
+      return false;
   return !g->h_orig_src.p && !g->h_orig_dst.p;
 }
 
@@ -954,8 +958,10 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       NX_TRY(move_to_host(d->hub_dst, d->h_hub_dst));
       if (prog != NX_WPR) NX_TRY(move_to_host(d->wt, d->h_wt));
       else if (used) NX_TRY(move_to_device(d->h_wt, d->wt));
-      if (!used) {
+      if (!used) {  // nothing of it stays on the device
         NX_TRY(set_edge_residency(*d, 0, 0));
+        NX_TRY(move_to_host(d->piece_off, d->h_piece_pin));
+        NX_TRY(move_to_host(d->hub_off, d->h_hub_off));
       } else if (c.Jc >= P) {
         NX_TRY(set_edge_residency(*d, d->words, 0));
       } else {
@@ -968,7 +974,18 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     if (budgeted_spu) {
       NX_TRY(move_to_host(g->orig_src, g->h_orig_src));
       NX_TRY(move_to_host(g->orig_dst, g->h_orig_dst));
+      // scratch of other programs and schedules (reallocated when they run)
+      DevBuf* scratch[] = {&g->hubs, &g->hubs_t, &g->lam[0], &g->lam[1], &g->ybuf, &g->accres,
+                           &g->split_buf, &g->stage[0], &g->stage[1], &g->vstage[0],
+                           &g->vstage[1], &g->vstage[2], &g->vstage[3], &g->vstage[4],
+                           &g->vstage[5], &g->vstage[6], &g->vstage[7]};
+      for (DevBuf* b : scratch) b->release();
+      if (prog != NX_PPR && prog != NX_WPR) g->tele.release();
     }
+  }
+  for (const Dsss* d : c.ds) {  // the piece and hub offsets of every DSSS the run reads
+    NX_TRY(move_to_device(const_cast<Dsss*>(d)->h_piece_pin, const_cast<Dsss*>(d)->piece_off));
+    NX_TRY(move_to_device(const_cast<Dsss*>(d)->h_hub_off, const_cast<Dsss*>(d)->hub_off));
   }
   // SPU bands: launches over groups of source intervals whose gathered values
   // fit in L2 together (the value array of the whole graph may not)

@@ -152,6 +152,7 @@ struct Dsss {
   // Arrays moved whole to pinned host memory while a budgeted run does not
   // need them on the device (hub index, weights).
   PinnedBuf h_hub_dst, h_wt;
+  PinnedBuf h_piece_pin, h_hub_off;  // piece and hub offsets while the DSSS is unread
 };
 
 struct Geometry {

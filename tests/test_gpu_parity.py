@@ -390,12 +390,13 @@ def test_spu_streams_shards_from_host(frac):
 def _budget_slack(info, nds):
     """Device bytes outside a budget's accounting (intervals 2 n B_a + resident
     edge words): out-degrees and PageRank contributions (12 n), piece and hub
-    offsets (16 B per piece per DSSS), tile tables, the accumulators of one
-    streamed column (4 L), two staging buffers (at most 64 MB per DSSS each
-    while no streamed sub-shard is larger), plans, split slots and scalars."""
+    offsets of the DSSS the run reads (16 B per piece each), tile tables, the
+    accumulators of one streamed column (4 L), two staging buffers (at most
+    64 MB per DSSS each while no streamed sub-shard is larger), and 256 MB for
+    plans, split-tile slots and scalars."""
     n, P, nt, L = info["n"], info["P"], info["ntiles"], info["L"]
     return (12 * n + 16 * (P * nt + 1) * nds + 8 * (nt + P + 2) + 4 * L
-            + 2 * nds * (64 << 20) + (64 << 20))
+            + 2 * nds * (64 << 20) + (256 << 20))
 
 
 def test_budget_bounds_device_memory_and_is_undone():
