@@ -437,6 +437,43 @@ def measure_autotune(nx, inputs, torch, scale=22, seed=2):
                                      for (p, c, e), t in zip(shapes, ms2)}}
 
 
+def measure_onchip(nx, inputs, torch, scale=26, ef=22, seed=5, P=64, iters=10, runs=5):
+    """PageRank under NX_DPU_ONCHIP (Algorithm 6 with shared-memory intervals)
+    on the scale-26 graph, beside the SPU sweep on the same graph."""
+    n, m = 1 << scale, ef << scale
+    src, dst, _ = inputs.rmat_edges_device(scale, m, seed)
+    g = nx.Graph(src, dst, n, P, relabel=True, onchip=True)
+    del src, dst
+    torch.cuda.empty_cache()
+    info = g.info()
+    H = info["H_onchip"]
+    for _ in range(3):
+        g.run("pr", iters, "dpu_onchip")
+    ms = [g.run("pr", iters, "dpu_onchip")["ms"] for _ in range(runs)]
+    r_oc = torch.empty(n, dtype=torch.float32, device="cuda")
+    g.values(r_oc)
+    for _ in range(2):
+        g.run("pr", iters, "spu")
+    ms_spu = [g.run("pr", iters, "spu")["ms"] for _ in range(runs)]
+    r_spu = torch.empty_like(r_oc)
+    g.values(r_spu)
+    g.free()
+    t = statistics.median(ms) / iters / 1e3
+    peak, _ = load_peaks()
+    alg = 4 * m + 10 * H + 16 * n  # edge words, hub values out and in, hub offsets, c, outdeg, r, c
+    out = {"workload": f"R-MAT scale {scale} ef {ef} seed {seed}, degree-ordered ids, PageRank x{iters}",
+           "H": H, "H_over_m": H / m, "ms_per_iter": t * 1e3,
+           "gteps": m / t / 1e9, "bytes_per_iter": alg, "bytes_formula": "4m + 10H + 16n",
+           "roofline_frac": alg / t / 1e9 / peak,
+           "spu_ms_per_iter": statistics.median(ms_spu) / iters,
+           "speedup_vs_spu": statistics.median(ms_spu) / statistics.median(ms),
+           "l1_vs_spu": float((r_oc.double() - r_spu.double()).abs().sum()),
+           "build_ms": info["build_ms"], "device_bytes": info["device_bytes"]}
+    del r_oc, r_spu
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_scc(nx, inputs, torch, scale=22, seed=2, P=16):
     """Strongly connected components of the scale-22 graph (coloring rounds)."""
     n, m = 1 << scale, 16 << scale
@@ -572,6 +609,7 @@ def compact(extras):
         "relabel": ("relabel_over_ids",),
         "gather_ceiling": ("ceiling_gbs", "ceiling_frac_of_peak", "sweep_over_ceiling"),
         "scc": ("ms", "rounds", "sweeps", "scc_over_bfs"),
+        "dpu_onchip": ("gteps", "roofline_frac", "speedup_vs_spu", "H_over_m", "l1_vs_spu"),
     }
     out = {}
     for name, rec in (extras or {}).items():
@@ -713,7 +751,7 @@ def main():
 EXTRAS = {"rmat22": measure_rmat22, "ppr_batch": measure_ppr_batch, "adjoint": measure_adjoint,
           "multi_graph": measure_multi, "autotune": measure_autotune,
           "strategies": measure_strategies, "budget_sweep": measure_budget_sweep,
-          "relabel": measure_relabel, "scc": measure_scc}
+          "relabel": measure_relabel, "scc": measure_scc, "dpu_onchip": measure_onchip}
 
 
 if __name__ == "__main__":

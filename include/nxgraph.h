@@ -72,7 +72,13 @@ typedef enum {
      0): the same sub-shards read in source order from the transpose DSSS, each
      edge pushing its contribution to the destination with an atomic add.      */
   NX_SRC_COARSE = 4, /* one thread block per sub-shard (coarse-grained model)  */
-  NX_SRC_FINE = 5    /* edge-balanced chunks of the source-sorted order         */
+  NX_SRC_FINE = 5,   /* edge-balanced chunks of the source-sorted order         */
+  /* Algorithm 6 with intervals held in shared memory (PR and PPR; the graph
+     built with NX_ONCHIP_HUBS; budget 0): ToHub streams the edges row by row
+     with the source interval (2^15 vertices) staged on chip and writes one hub
+     value per (row, destination) run; FromHub folds the hubs column by column
+     into a destination interval (2^14 vertices) accumulated on chip.          */
+  NX_DPU_ONCHIP = 6
 } nx_strategy;
 
 /* nx_build_dsss flags. */
@@ -82,6 +88,8 @@ typedef enum {
 #define NX_WITH_WEIGHTS 4u       /* w (float, > 0) is given: weighted PageRank     */
 #define NX_RELABEL 8u            /* degree-ordered internal ids (Section III-A
                                     "degreeing"): see nx_get_relabel              */
+#define NX_ONCHIP_HUBS 16u       /* also build the row-major structure of
+                                    NX_DPU_ONCHIP (n up to about 9.5e7)          */
 /* Tile shape (below the interval level; nx_autotune_shape searches it):
  * destination tiles of at most 2^k vertices (8 <= k <= 13; default 2^11), and
  * a tile also ends where its in-edges pass a multiple of 2^e (10 <= e <= 20;
@@ -135,6 +143,9 @@ typedef struct {
   int32_t has_transpose, has_weights;
   uint64_t host_bytes;    /* pinned host memory held by the graph (offloaded
                              edges and indexes, staged intervals)             */
+  uint64_t H_onchip;      /* hub entries of the NX_ONCHIP_HUBS structure (0 if
+                             not built): runs of equal (source interval of
+                             2^15, destination), cut every 2048 edges         */
 } nx_graph_info;
 
 /* Stream for all later calls (a cudaStream_t; NULL = legacy default stream). */

@@ -451,6 +451,7 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
     g->has_w = true;
   }
   NX_TRY(build_one(s, d, m, geo, tile_of.as<uint32_t>(), want_w ? wn.as<float>() : nullptr, g->fwd));
+  if (flags & NX_ONCHIP_HUBS) NX_TRY(build_onchip(g, s, d, m));
   if (want_t) {
     NX_TRY(build_one(d, s, m, geo, tile_of.as<uint32_t>(), want_w ? wn.as<float>() : nullptr,
                      g->tr));
@@ -485,6 +486,9 @@ uint64_t nx_graph::device_bytes() const {
   for (auto* b : bufs) s += b->bytes;
   for (const auto& kv : plans) s += kv.second->items.bytes;
   s += old_of_new.bytes + new_of_old.bytes;
+  const nx::DevBuf* ocb[] = {&oc.ew, &oc.seg_e, &oc.seg_h, &oc.hub_dst, &oc.hub_val, &oc.chunks,
+                             &oc.items_a, &oc.items_b, &oc.split, &oc.ticket, &oc.part};
+  for (auto* b : ocb) s += b->bytes;
   return s;
 }
 
@@ -492,7 +496,7 @@ uint64_t nx_graph::host_bytes() const {
   const nx::PinnedBuf* bufs[] = {&fwd.h_ew, &fwd.h_hub_dst, &fwd.h_wt, &fwd.h_piece_pin,
                                  &fwd.h_hub_off, &tr.h_ew, &tr.h_hub_dst, &tr.h_wt,
                                  &tr.h_piece_pin, &tr.h_hub_off, &h_orig_src, &h_orig_dst,
-                                 &hval[0], &hval[1], &hact};
+                                 &hval[0], &hval[1], &hact, &oc.h_ew, &oc.h_hub_dst};
   uint64_t s = 0;
   for (auto* b : bufs) s += b->bytes;
   return s;

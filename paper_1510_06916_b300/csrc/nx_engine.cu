@@ -451,6 +451,11 @@ nx_status ensure_resident(nx_graph* g) {
   }
   NX_TRY(move_to_device(g->h_orig_src, g->orig_src));
   NX_TRY(move_to_device(g->h_orig_dst, g->orig_dst));
+  if (g->oc.built) {
+    NX_TRY(move_to_device(g->oc.h_ew, g->oc.ew));
+    NX_TRY(move_to_device(g->oc.h_hub_dst, g->oc.hub_dst));
+    if (!g->oc.hub_val.p) NX_TRY(g->oc.hub_val.alloc(std::max<uint64_t>(g->oc.H, 1) * 4));
+  }
   return NX_OK;
 }
 
@@ -460,7 +465,7 @@ bool fully_resident(const nx_graph* g) {
     if (d && (d->dev_words != d->words || d->h_hub_dst.p || d->h_wt.p || d->h_piece_pin.p ||
               d->h_hub_off.p))
       return false;
-  return !g->h_orig_src.p && !g->h_orig_dst.p;
+  return !g->h_orig_src.p && !g->h_orig_dst.p && !g->oc.h_ew.p && !g->oc.h_hub_dst.p;
 }
 
 namespace {
@@ -805,6 +810,12 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   if (push && !g->has_tr)
     return invalid("nx_run: the source-sorted ablation reads the transpose DSSS (NX_WITH_TRANSPOSE)");
   if (push && budget) return invalid("nx_run: the source-sorted ablation takes no budget");
+  const bool onchip = (strategy == NX_DPU_ONCHIP);
+  if (onchip && prog != NX_PR && prog != NX_PPR)
+    return invalid("nx_run: NX_DPU_ONCHIP runs PR and PPR only");
+  if (onchip && !g->oc.built)
+    return invalid("nx_run: NX_DPU_ONCHIP needs a graph built with NX_ONCHIP_HUBS");
+  if (onchip && budget) return invalid("nx_run: NX_DPU_ONCHIP takes no budget");
   // strategy from the budget (Section III-B3: Q <= B_M P / (2 n B_a))
   const double Ba = 4.0;
   uint32_t Qb = P;
@@ -870,6 +881,43 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   g->values_set_for = -1;
   g->last_prog = (int)prog;
   if (prog == NX_WPR) g->wpr_alpha = p.alpha;
+  if (onchip) {
+    NX_TRY(ensure_resident(g));
+    Scal sc = scal_of(g);
+    EventPair ev;
+    NX_TRY(ev.create());
+    NX_CUDA(cudaEventRecord(ev.e0, stream()));
+    for (uint32_t it = 0; it < iters; ++it) {
+      const int c = g->cur, nn = 1 - g->cur;
+      OcRun r;
+      r.c_in = g->aux[c].as<float>();
+      r.r_out = g->val[nn].as<float>();
+      r.c_out = g->aux[nn].as<float>();
+      r.tele = (prog == NX_PPR) ? tele : nullptr;
+      r.dang_by_tele = (prog == NX_PPR) ? 1 : 0;
+      r.alpha = p.alpha;
+      r.dm_in = sc.dm + c;
+      r.dm_out = sc.dm + nn;
+      NX_TRY(onchip_iteration(g, r, stream()));
+      g->cur ^= 1;
+    }
+    NX_CUDA(cudaEventRecord(ev.e1, stream()));
+    float ms = 0.f;
+    NX_TRY(ev.elapsed(&ms));
+    if (st) {
+      const uint64_t n64 = g->geo.n;
+      memset(st, 0, sizeof *st);
+      st->iters_done = iters;
+      st->Q = P;
+      st->strategy = (uint32_t)strategy;
+      st->ms = ms;
+      st->edges_swept = g->m * iters;
+      // words, hub values written and read, hub offsets, staged c, outdeg, r, c
+      st->bytes_model = (uint64_t)iters * (4 * g->m + 10 * g->oc.H + 16 * n64);
+      st->launches = (g->oc.na ? 2 : 1) * iters;
+    }
+    return NX_OK;
+  }
   if (push) {
     NX_TRY(ensure_resident(g));
     PushRun r;
@@ -981,6 +1029,11 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
                            &g->vstage[5], &g->vstage[6], &g->vstage[7]};
       for (DevBuf* b : scratch) b->release();
       if (prog != NX_PPR && prog != NX_WPR) g->tele.release();
+      if (g->oc.built) {  // the on-chip double-phase structure
+        NX_TRY(move_to_host(g->oc.ew, g->oc.h_ew));
+        NX_TRY(move_to_host(g->oc.hub_dst, g->oc.h_hub_dst));
+        g->oc.hub_val.release();
+      }
     }
   }
   for (const Dsss* d : c.ds) {  // the piece and hub offsets of every DSSS the run reads
@@ -1847,6 +1900,7 @@ extern "C" nx_status nx_graph_get_info(const nx_graph* g, nx_graph_info* info) {
   info->has_transpose = g->has_tr;
   info->has_weights = g->has_w;
   info->host_bytes = g->host_bytes();
+  info->H_onchip = g->oc.built ? g->oc.H : 0;
   return NX_OK;
 }
 
@@ -1855,7 +1909,7 @@ extern "C" nx_status nx_run(nx_graph* g, nx_program program, const nx_params* pa
                             nx_run_stats* stats) {
   if (!g) return nx::invalid("nx_run: graph is NULL");
   if ((int)program < 0 || (int)program > 5) return nx::invalid("nx_run: unknown program");
-  if ((int)strategy < 0 || (int)strategy > 5) return nx::invalid("nx_run: unknown strategy");
+  if ((int)strategy < 0 || (int)strategy > 6) return nx::invalid("nx_run: unknown strategy");
   if (program == NX_SCC) {
     if (!g->has_tr) return nx::invalid("nx_run: SCC needs the transpose DSSS (NX_WITH_TRANSPOSE)");
     if ((strategy != NX_SPU && strategy != NX_AUTO) || mem_budget_bytes)

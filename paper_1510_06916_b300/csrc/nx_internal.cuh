@@ -155,6 +155,45 @@ struct Dsss {
   PinnedBuf h_piece_pin, h_hub_off;  // piece and hub offsets while the DSSS is unread
 };
 
+// The on-chip double-phase structure (NX_ONCHIP_HUBS): the paper's DPU
+// (Algorithm 6) with source intervals of 2^kOcSrcBits vertices, small enough
+// to stage in shared memory for ToHub, and destination intervals of
+// 2^kOcDstBits vertices, whose compensated accumulators fit shared memory for
+// FromHub. Edges are sorted by (source interval i, destination interval j,
+// destination, source), rows (i) outermost, and stored as one word each:
+// src_local | dst_local << 15 | (ordinal of the sub-shard (i, j) & 1) << 29.
+// A hub entry is a run of equal (i, j, destination), also cut at every
+// multiple of kOcSeg edges; a segment is a window of the edge array between
+// cuts and row starts, so no hub entry crosses a segment.
+constexpr uint32_t kOcSrcBits = 15;
+constexpr uint32_t kOcDstBits = 14;
+constexpr uint32_t kOcSeg = 2048;
+struct OcItemA {   // ToHub work item: segments [s0, s1) of row `row`
+  uint32_t row, s0, s1, pad;
+};
+struct OcItemB {   // FromHub work item: hub chunks [c0, c1) of column `col`
+  uint32_t col, c0, c1;
+  uint32_t nsplit, part, slot;  // blocks sharing the column, this block, first split slot
+  uint32_t group, pad;          // completion counter of a split column
+};
+struct OnChip {
+  bool built = false;
+  uint32_t PA = 0, PB = 0;     // source (row) and destination (column) intervals
+  uint64_t m = 0, H = 0;       // edges, hub entries
+  DevBuf ew;                   // uint32 [round_up(m, 16) + 16]
+  DevBuf seg_e;                // uint64 [nseg + 1]: first edge of each segment
+  DevBuf seg_h;                // uint64 [nseg]: first hub entry of each segment
+  DevBuf hub_dst;              // uint16 [H]: destination offset in its column
+  DevBuf hub_val;              // float [H]
+  DevBuf chunks;               // uint64 [nchunks]: (first hub entry << 32) | entries (<= 256),
+                               // the nonempty pieces (i, j) column by column
+  DevBuf items_a, items_b;     // OcItemA [na], OcItemB [nb]
+  DevBuf split, ticket, part;  // split-column slots, completion counters, dangling partials
+  PinnedBuf h_ew, h_hub_dst;   // host copies while a budgeted run holds them off the device
+  uint32_t na = 0, nb = 0, nseg = 0, slots = 0, groups = 0;
+  uint64_t nchunks = 0;
+};
+
 struct Geometry {
   uint32_t n = 0, P = 0, L = 0, lb = 0, tile_max = 0, ntiles = 0;
   DevBuf tile_start;  // uint32 [ntiles+1]
@@ -224,6 +263,7 @@ struct nx_graph {
   uint64_t split_floats = 0;
   nx::DevBuf tele;          // float [n] teleport copy (PPR/WPR)
   nx::DevBuf lam[2], ybuf;  // adjoint scratch
+  nx::OnChip oc;            // the on-chip double-phase structure (NX_ONCHIP_HUBS)
   float wpr_alpha = 0.85f;  // damping of the last weighted PageRank run
   uint32_t ppr_rows = 4;    // batched PPR: source rows in flight per lane group
   uint32_t ppr_sub = 128;   // batched PPR: destinations per sub-tile
@@ -248,6 +288,21 @@ struct PushRun {
   double* dm;          // [2] dangling mass ping-pong
 };
 nx_status push_run(nx_graph* g, const PushRun& r, uint32_t* launches, float* ms);
+
+// The on-chip double-phase structure (nx_onchip.cu): built from the internal
+// edge arrays; one iteration of PageRank / personalized PageRank over it.
+nx_status build_onchip(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64_t m);
+struct OcRun {
+  const float* c_in;     // contributions r / outdeg of the current values
+  float* r_out;          // new ranks
+  float* c_out;          // new contributions
+  const float* tele;     // teleport (nullptr: uniform 1/n)
+  int dang_by_tele;
+  float alpha;
+  const double* dm_in;   // dangling mass of the current values
+  double* dm_out;        // of the new values
+};
+nx_status onchip_iteration(nx_graph* g, const OcRun& r, cudaStream_t s);
 
 // Relabel (nx_relabel.cu). relabel_edges computes the vertex order (out-degree
 // descending, ties by caller id) into g and writes the renamed endpoints

@@ -17,13 +17,13 @@ LIB_PATH = os.path.join(_HERE, "csrc", "libnxgraph.so")
 
 NX_OK, NX_ERR_INVALID_ARG, NX_ERR_OOM, NX_ERR_BUDGET_TOO_SMALL, NX_ERR_CUDA, NX_ERR_TIMEOUT = range(6)
 PR, PPR, WPR, BFS, WCC, SCC = range(6)
-SPU, DPU, MPU, AUTO, SRC_COARSE, SRC_FINE = range(6)
-HOST_PTRS, DEV_PTRS, WITH_TRANSPOSE, WITH_WEIGHTS, RELABEL = 0, 1, 2, 4, 8
+SPU, DPU, MPU, AUTO, SRC_COARSE, SRC_FINE, DPU_ONCHIP = range(7)
+HOST_PTRS, DEV_PTRS, WITH_TRANSPOSE, WITH_WEIGHTS, RELABEL, ONCHIP_HUBS = 0, 1, 2, 4, 8, 16
 INF = 0xFFFFFFFF
 
 PROGRAMS = {"pr": PR, "ppr": PPR, "wpr": WPR, "bfs": BFS, "wcc": WCC, "scc": SCC}
 STRATEGIES = {"spu": SPU, "dpu": DPU, "mpu": MPU, "auto": AUTO,
-              "src_coarse": SRC_COARSE, "src_fine": SRC_FINE}
+              "src_coarse": SRC_COARSE, "src_fine": SRC_FINE, "dpu_onchip": DPU_ONCHIP}
 
 EXPORTS = [
     "nx_set_stream", "nx_last_error", "nx_build_dsss", "nx_graph_get_info", "nx_run",
@@ -67,7 +67,8 @@ class NxGraphInfo(ctypes.Structure):
                 ("lb", ctypes.c_uint32), ("m", ctypes.c_uint64), ("D", ctypes.c_uint64),
                 ("D_t", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("build_ms", ctypes.c_float), ("has_transpose", ctypes.c_int32),
-                ("has_weights", ctypes.c_int32), ("host_bytes", ctypes.c_uint64)]
+                ("has_weights", ctypes.c_int32), ("host_bytes", ctypes.c_uint64),
+                ("H_onchip", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -185,7 +186,8 @@ class Graph:
     """A DSSS built on the current device (owns it; free() or context exit)."""
 
     def __init__(self, src, dst, n: int, P: int, transpose: bool = False, weights=None,
-                 relabel: bool = False, tile_cap_log2: int = 0, tile_edges_log2: int = 0):
+                 relabel: bool = False, tile_cap_log2: int = 0, tile_edges_log2: int = 0,
+                 onchip: bool = False):
         if isinstance(src, np.ndarray):
             src = np.ascontiguousarray(src, dtype=np.uint32)
         if isinstance(dst, np.ndarray):
@@ -208,6 +210,8 @@ class Graph:
             flags |= WITH_TRANSPOSE
         if relabel:
             flags |= RELABEL
+        if onchip:
+            flags |= ONCHIP_HUBS
         flags |= (tile_cap_log2 << 8) | (tile_edges_log2 << 12)
         wp = None
         if weights is not None:

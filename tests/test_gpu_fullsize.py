@@ -32,12 +32,14 @@ def test_rmat26_p64_spu_and_mpu_6gb():
 
     src = torch.from_numpy(s.view(np.int32)).cuda()
     dst = torch.from_numpy(d.view(np.int32)).cuda()
-    g = nx.Graph(src, dst, n, P, transpose=True)
+    g = nx.Graph(src, dst, n, P, transpose=True, onchip=True)
     del src, dst
     torch.cuda.empty_cache()
     ref = oracle.pagerank(n, s, d, 0.85, 10)
     g.run("pr", 10, "spu")
     _pr_close(g.values(), ref, "rmat26 PR SPU")
+    g.run("pr", 10, "dpu_onchip")  # Algorithm 6 with shared-memory intervals
+    _pr_close(g.values(), ref, "rmat26 PR DPU on chip")
     st = g.run("pr", 10, "mpu", budget=6 * 10**9)
     assert st["streamed_cols"] > 0 and st["Q"] == P
     _pr_close(g.values(), ref, "rmat26 PR MPU 6GB")

@@ -87,6 +87,90 @@ def test_bfs_max_depth_is_algorithm4_output():
     g.free()
 
 
+# ------------------------------------------------- on-chip double-phase update
+
+def _onchip_hub_count(s, d):
+    """Hub entries of the NX_ONCHIP_HUBS layout from its definition: edges in
+    (source interval of 2^15, destination interval of 2^14, destination,
+    source) order; an entry starts at a new (source interval, destination) or
+    at every multiple of 2048 edges."""
+    s = np.asarray(s, np.int64)
+    d = np.asarray(d, np.int64)
+    order = np.lexsort((s & 0x7FFF, d & 0x3FFF, d >> 14, s >> 15))
+    k = ((s >> 15) << 40 | d)[order]
+    head = np.ones(len(k), bool)
+    head[1:] = k[1:] != k[:-1]
+    head[::2048] = True
+    return int(head.sum())
+
+
+@pytest.mark.parametrize("scale,ef,seed,P", [(12, 16, 3, 4), (17, 16, 5, 8), (18, 8, 6, 16)])
+def test_dpu_onchip_matches_oracle(scale, ef, seed, P):
+    # Algorithm 6 with the source interval (2^15) and the destination interval
+    # (2^14) held in shared memory: PageRank and PPR vs the FP64 oracle
+    n = 1 << scale
+    s, d, _ = rmat(scale, ef, seed)
+    g = nx.Graph(s, d, n, P, onchip=True)
+    assert g.info()["H_onchip"] == _onchip_hub_count(s, d)
+    st = g.run("pr", 20, "dpu_onchip")
+    assert st["iters_done"] == 20 and st["strategy"] == nx.DPU_ONCHIP
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"onchip PR scale {scale}")
+    t = inputs.ppr_teleports(n, 1, seed + 1, max_seeds=50)[:, 0].copy()
+    g.run("ppr", 15, "dpu_onchip", teleport=t)
+    ref = oracle.personalized_pagerank(n, s, d, t, 0.85, 15)
+    assert_pr_close(g.values(), ref, f"onchip PPR scale {scale}")
+    g.free()
+
+
+def test_dpu_onchip_ragged_hub_relabel_and_empty():
+    # ragged n (partial last intervals), a 300k-edge in-star (runs cut every
+    # 2048 edges), degree-ordered ids, an empty graph, and rejections
+    n = 100_003
+    rng = np.random.default_rng(4)
+    k = 300_000
+    s = np.concatenate([rng.integers(0, n, k), rng.integers(0, n, 200_000)]).astype(np.uint32)
+    d = np.concatenate([np.full(k, n - 2), rng.integers(0, n, 200_000)]).astype(np.uint32)
+    ref = oracle.pagerank(n, s, d, 0.85, 20)
+    for relabel in (False, True):
+        g = nx.Graph(s, d, n, 7, relabel=relabel, onchip=True)
+        g.run("pr", 20, "dpu_onchip")
+        assert_pr_close(g.values(), ref, f"onchip ragged relabel={relabel}")
+        g.free()
+    g = nx.Graph(s, d, n, 7, onchip=True)
+    assert g.info()["H_onchip"] == _onchip_hub_count(s, d)
+    # the DSSS sweeps on the same graph continue to work, and agree
+    g.run("pr", 20, "spu")
+    assert_pr_close(g.values(), ref, "spu on an onchip graph")
+    for bad in (dict(program="bfs"), dict(budget=1 << 30)):
+        with pytest.raises(nx.NxError):
+            g.run(bad.get("program", "pr"), 5, "dpu_onchip", budget=bad.get("budget", 0))
+    g.free()
+    e = np.zeros(0, np.uint32)
+    g = nx.Graph(e, e, 50, 2, onchip=True)
+    g.run("pr", 5, "dpu_onchip")
+    assert_pr_close(g.values(), oracle.pagerank(50, e, e, 0.85, 5), "onchip empty")
+    g.free()
+    g = nx.Graph(s, d, n, 7)
+    with pytest.raises(nx.NxError):
+        g.run("pr", 5, "dpu_onchip")  # not built with the on-chip structure
+    g.free()
+
+
+def test_dpu_onchip_under_a_budget_elsewhere():
+    # a budgeted SPU run moves the on-chip structure to host memory; the next
+    # on-chip run brings it back
+    n = 1 << 16
+    s, d, _ = rmat(16, 16, 9)
+    g = nx.Graph(s, d, n, 8, onchip=True)
+    ref = oracle.pagerank(n, s, d, 0.85, 10)
+    g.run("pr", 10, "spu", budget=2 * n * 4 + 4 * len(s) // 3)
+    assert_pr_close(g.values(), ref, "budget before onchip")
+    assert g.info()["host_bytes"] >= 4 * len(s)
+    g.run("pr", 10, "dpu_onchip")
+    assert_pr_close(g.values(), ref, "onchip after budget")
+    g.free()
+
+
 # ------------------------------------------------------------------ SCC
 
 @pytest.mark.parametrize("P", [1, 3, 8])
