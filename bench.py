@@ -638,6 +638,8 @@ def main():
                     help="diagnostic: run one extra measurement and print it (for profiling)")
     ap.add_argument("--batch-scale", type=int, default=24,
                     help="R-MAT scale of the batched-PPR measurement (profiling uses 22)")
+    ap.add_argument("--onchip-scale", type=int, default=26,
+                    help="R-MAT scale (edge factor 22) of the on-chip DPU measurement (profiling uses 24)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -654,6 +656,8 @@ def main():
         fn = EXTRAS[args.extras_only]
         if args.extras_only == "ppr_batch":
             out = fn(nx, inputs, torch, scale=args.batch_scale)
+        elif args.extras_only == "dpu_onchip":
+            out = fn(nx, inputs, torch, scale=args.onchip_scale)
         else:
             out = fn(nx, inputs, torch)
         if rank == 0:

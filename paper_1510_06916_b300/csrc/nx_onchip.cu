@@ -99,8 +99,91 @@ struct ArgsA {
   const float* c_in;
   float* hub_val;
   uint64_t H;
-  uint32_t n;
+  uint32_t n, nseg;
 };
+
+// One 256-edge step of a segment (see oc_segment). FULL: every edge of the
+// step lies inside the segment, so no edge needs a range check.
+template <bool FULL>
+__device__ __forceinline__ void oc_step(const uint4 w0, const uint4 w1, uint64_t base, uint64_t e0,
+                                        uint64_t e1, const float* __restrict__ csh,
+                                        float* __restrict__ hv, uint32_t hlim, uint32_t& ckey,
+                                        uint32_t& cnt, float& csum) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+  uint32_t key[8];
+  float val[8];
+  const uint64_t p0 = base + (uint64_t)lane * 8;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (FULL) {
+      key[k] = wv[k] >> 15;
+      val[k] = csh[wv[k] & (kSrcLen - 1)];
+    } else {
+      const bool valid = p0 + k >= e0 && p0 + k < e1;
+      key[k] = valid ? (wv[k] >> 15) : kSent;
+      val[k] = valid ? csh[wv[k] & (kSrcLen - 1)] : 0.f;
+    }
+  }
+  uint32_t pk = __shfl_up_sync(0xffffffffu, key[7], 1);
+  if (lane == 0) pk = ckey;
+  uint32_t hm = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t prev = k ? key[k - 1] : pk;
+    const bool h = FULL ? (key[k] != prev) : (key[k] != kSent && key[k] != prev);
+    hm |= (h ? 1u : 0u) << k;
+  }
+  const uint32_t hc = __popc(hm);
+  uint32_t incl = hc;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const uint32_t hb = cnt + incl - hc;  // entries of the segment started before this lane
+  const uint32_t htot = __shfl_sync(0xffffffffu, incl, 31);
+  // in-lane runs: F before the first head, the open run from the last head;
+  // runs between two heads of the lane are complete and written here
+  float run = 0.f, F = 0.f;
+  uint32_t nh = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if ((hm >> k) & 1u) {
+      if (nh == 0) {
+        F = run;
+      } else {
+        const uint32_t idx = hb + nh - 1;
+        if (idx < hlim) hv[idx] = run;
+      }
+      ++nh;
+      run = 0.f;
+    }
+    run += val[k];
+  }
+  if (nh == 0) F = run;
+  // runs across lanes: segmented inclusive scan of the lanes' open partials
+  float x = nh ? run : F;
+  if (lane == 0 && nh == 0) x += csum;
+  const uint32_t starts = __ballot_sync(0xffffffffu, nh != 0);
+  const uint32_t le = starts & (0xffffffffu >> (31 - lane));
+  const int seg0 = le ? 31 - __clz(le) : 0;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane - d >= seg0) x += y;
+  }
+  float prev = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane == 0) prev = csum;
+  // the run that ends just before this lane's first head
+  if (nh && (hb > 0 || ckey != kSent)) {
+    const uint32_t idx = hb - 1;
+    if (idx < hlim) hv[idx] = prev + F;
+  }
+  csum = __shfl_sync(0xffffffffu, x, 31);
+  ckey = __shfl_sync(0xffffffffu, key[7], 31);  // the open run's key (a later step follows a full one)
+  cnt += htot;
+}
 
 // One warp, one segment: 256-edge steps (two 16-byte loads per lane, the
 // next step prefetched), source values from shared memory, runs of equal
@@ -110,6 +193,9 @@ __device__ __forceinline__ void oc_segment(const ArgsA& a, const float* __restri
                                            uint32_t q) {
   const int lane = threadIdx.x & 31;
   const uint64_t e0 = a.seg_e[q], e1 = a.seg_e[q + 1], h0 = a.seg_h[q];
+  const uint64_t h1 = (q + 1 < a.nseg) ? a.seg_h[q + 1] : a.H;
+  const uint32_t hlim = h1 > h0 ? (uint32_t)(h1 - h0) : 0u;  // entries of this segment
+  float* hv = a.hub_val + h0;
   uint64_t base = e0 & ~7ull;
   uint4 nx0 = make_uint4(0, 0, 0, 0), nx1 = nx0;
   {
@@ -131,80 +217,13 @@ __device__ __forceinline__ void oc_segment(const ArgsA& a, const float* __restri
         nx1 = __ldcs(reinterpret_cast<const uint4*>(a.ew + p + 4));
       }
     }
-    const uint32_t wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-    uint32_t key[8];
-    float val[8];
-    const uint64_t p0 = base + (uint64_t)lane * 8;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const bool valid = p0 + k >= e0 && p0 + k < e1;
-      key[k] = valid ? (wv[k] >> 15) : kSent;
-      val[k] = valid ? csh[wv[k] & (kSrcLen - 1)] : 0.f;
-    }
-    uint32_t pk = __shfl_up_sync(0xffffffffu, key[7], 1);
-    if (lane == 0) pk = ckey;
-    uint32_t hm = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t prev = k ? key[k - 1] : pk;
-      if (key[k] != kSent && key[k] != prev) hm |= 1u << k;
-    }
-    const uint32_t hc = __popc(hm);
-    uint32_t incl = hc;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += y;
-    }
-    const uint32_t hb = incl - hc;                          // entries started in earlier lanes
-    const uint32_t htot = __shfl_sync(0xffffffffu, incl, 31);
-    // in-lane runs: F before the first head, T from the last head; runs
-    // between two heads of the lane are complete and written here
-    float run = 0.f, F = 0.f;
-    uint32_t nh = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if ((hm >> k) & 1u) {
-        if (nh == 0) {
-          F = run;
-        } else {
-          const uint64_t idx = h0 + cnt + hb + nh - 1;
-          if (idx < a.H) a.hub_val[idx] = run;
-        }
-        ++nh;
-        run = 0.f;
-      }
-      run += val[k];
-    }
-    if (nh == 0) F = run;
-    // runs across lanes: segmented inclusive scan of the lanes' open partials
-    float x = nh ? run : F;
-    if (lane == 0 && nh == 0) x += csum;
-    const uint32_t starts = __ballot_sync(0xffffffffu, nh != 0);
-    const uint32_t le = starts & (0xffffffffu >> (31 - lane));
-    const int seg0 = le ? 31 - __clz(le) : 0;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const float y = __shfl_up_sync(0xffffffffu, x, d);
-      if (lane - d >= seg0) x += y;
-    }
-    float prev = __shfl_up_sync(0xffffffffu, x, 1);
-    if (lane == 0) prev = csum;
-    // the run that ends just before this lane's first head
-    if (nh && (hb > 0 || ckey != kSent)) {
-      const uint64_t idx = h0 + cnt + hb - 1;
-      if (idx < a.H) a.hub_val[idx] = prev + F;
-    }
-    csum = __shfl_sync(0xffffffffu, x, 31);
-    const uint32_t last = __shfl_sync(0xffffffffu, key[7], 31);
-    cnt += htot;
-    ckey = last;  // the open run's key (a later step exists only after a full one)
+    if (base >= e0 && nbase <= e1)
+      oc_step<true>(w0, w1, base, e0, e1, csh, hv, hlim, ckey, cnt, csum);
+    else
+      oc_step<false>(w0, w1, base, e0, e1, csh, hv, hlim, ckey, cnt, csum);
     base = nbase;
   }
-  if (lane == 0 && cnt) {  // the segment's last run
-    const uint64_t idx = h0 + cnt - 1;
-    if (idx < a.H) a.hub_val[idx] = csum;
-  }
+  if (lane == 0 && cnt && cnt - 1 < hlim) hv[cnt - 1] = csum;  // the segment's last run
 }
 
 __global__ void __launch_bounds__(kOcThreads) k_oc_tohub(const __grid_constant__ ArgsA a) {
@@ -265,15 +284,27 @@ __global__ void __launch_bounds__(kOcThreads) k_oc_fromhub(const __grid_constant
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // a chunk (<= 256 entries): every lane issues its loads first, then folds
+  static_assert(kChunk == 8 * 32, "eight entries per lane per chunk");
   for (uint32_t c = it.c0 + warp; c < it.c1; c += kOcWarps) {
     const uint64_t ch = a.chunks[c];
     const uint64_t h0 = ch >> 32;
     const uint32_t len = (uint32_t)(ch & 0xFFFFFFFFull);
-    for (uint32_t x = lane; x < len; x += 32) {
-      const uint32_t o = a.hub_dst[h0 + x];
-      const float v = __ldcs(a.hub_val + h0 + x);
-      if (o < kDstLen) twosum_add(hi, lo, o, v);
+    uint32_t o[8];
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t x = lane + 32 * q;
+      o[q] = kDstLen;
+      v[q] = 0.f;
+      if (x < len) {
+        o[q] = a.hub_dst[h0 + x];
+        v[q] = __ldcs(a.hub_val + h0 + x);
+      }
     }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (o[q] < kDstLen) twosum_add(hi, lo, o[q], v[q]);
   }
   __syncthreads();
   if (it.nsplit > 1) {  // combine the blocks of a split column in slot order
@@ -533,6 +564,7 @@ nx_status onchip_iteration(nx_graph* g, const OcRun& r, cudaStream_t s) {
     a.hub_val = oc.hub_val.as<float>();
     a.H = oc.H;
     a.n = g->geo.n;
+    a.nseg = oc.nseg;
     k_oc_tohub<<<oc.na, kOcThreads, smem_a, s>>>(a);
     NX_LAUNCH_CHECK();
   }
