@@ -26,7 +26,7 @@ constexpr int kOcWarps = kOcThreads / 32;
 constexpr uint32_t kSrcLen = 1u << kOcSrcBits;  // source interval (ToHub)
 constexpr uint32_t kDstLen = 1u << kOcDstBits;  // destination interval (FromHub)
 constexpr uint32_t kChunk = 256;                // hub entries per FromHub chunk
-constexpr uint32_t kSegsPerItem = 64;           // ToHub segments per block (2 per warp)
+constexpr uint32_t kSegsPerItem = 256;          // ToHub segments per block (8 per warp)
 
 // ---------------------------------------------------------------- build
 __global__ void k_oc_keys(const uint32_t* __restrict__ s, const uint32_t* __restrict__ d,
@@ -226,7 +226,7 @@ __device__ __forceinline__ void oc_segment(const ArgsA& a, const float* __restri
   if (lane == 0 && cnt && cnt - 1 < hlim) hv[cnt - 1] = csum;  // the segment's last run
 }
 
-__global__ void __launch_bounds__(kOcThreads) k_oc_tohub(const __grid_constant__ ArgsA a) {
+__global__ void __launch_bounds__(kOcThreads, 1) k_oc_tohub(const __grid_constant__ ArgsA a) {
   extern __shared__ __align__(16) float csh[];
   const OcItemA it = a.items[blockIdx.x];
   const uint64_t v0 = (uint64_t)it.row << kOcSrcBits;
@@ -269,7 +269,7 @@ __device__ __forceinline__ void twosum_add(float* hi, float* lo, uint32_t k, flo
   atomicAdd(lo + k, (old - (s - bb)) + (v - bb));
 }
 
-__global__ void __launch_bounds__(kOcThreads) k_oc_fromhub(const __grid_constant__ ArgsB a) {
+__global__ void __launch_bounds__(kOcThreads, 1) k_oc_fromhub(const __grid_constant__ ArgsB a) {
   extern __shared__ __align__(16) float acc[];  // hi [kDstLen], lo [kDstLen]
   float* hi = acc;
   float* lo = acc + kDstLen;
@@ -286,8 +286,18 @@ __global__ void __launch_bounds__(kOcThreads) k_oc_fromhub(const __grid_constant
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // a chunk (<= 256 entries): every lane issues its loads first, then folds
   static_assert(kChunk == 8 * 32, "eight entries per lane per chunk");
-  for (uint32_t c = it.c0 + warp; c < it.c1; c += kOcWarps) {
-    const uint64_t ch = a.chunks[c];
+  // the warp's chunks are c0 + warp + 32 t; lane l loads the descriptor of
+  // t = t0 + l for a batch of 32, handed out by shuffles; a chunk's loads are
+  // all issued before its folds
+  uint64_t batch = 0;
+  for (uint32_t t = 0;; ++t) {
+    const uint64_t c = (uint64_t)it.c0 + warp + (uint64_t)kOcWarps * t;
+    if (c >= it.c1) break;
+    if ((t & 31) == 0) {
+      const uint64_t cl = c + (uint64_t)kOcWarps * lane;
+      batch = cl < it.c1 ? a.chunks[cl] : 0ull;
+    }
+    const uint64_t ch = __shfl_sync(0xffffffffu, batch, t & 31);
     const uint64_t h0 = ch >> 32;
     const uint32_t len = (uint32_t)(ch & 0xFFFFFFFFull);
     uint32_t o[8];
@@ -456,6 +466,10 @@ nx_status build_onchip(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64
     k_oc_seg_hub<<<(unsigned)ceil_div(std::max<uint32_t>(oc.nseg, 1), 256), 256, 0, st>>>(
         oc.seg_e.as<uint64_t>(), oc.nseg, hidx.as<uint32_t>(), oc.seg_h.as<uint64_t>());
     NX_LAUNCH_CHECK();
+    // largest first (each block stages its row's 128 KB once, whatever its length)
+    std::stable_sort(items_a.begin(), items_a.end(), [&](const OcItemA& x, const OcItemA& y) {
+      return seg_e[x.s1] - seg_e[x.s0] > seg_e[y.s1] - seg_e[y.s0];
+    });
     oc.na = (uint32_t)items_a.size();
     NX_TRY(oc.items_a.alloc(std::max<size_t>(items_a.size(), 1) * sizeof(OcItemA)));
     if (!items_a.empty())
