@@ -460,10 +460,10 @@ def measure_onchip(nx, inputs, torch, scale=26, ef=22, seed=5, P=64, iters=10, r
     g.free()
     t = statistics.median(ms) / iters / 1e3
     peak, _ = load_peaks()
-    alg = 4 * m + 10 * H + 16 * n  # edge words, hub values out and in, hub offsets, c, outdeg, r, c
+    alg = 2 * m + 10 * H + 16 * n  # 16-bit edges, hub values out and in, hub offsets, c, outdeg, r, c
     out = {"workload": f"R-MAT scale {scale} ef {ef} seed {seed}, degree-ordered ids, PageRank x{iters}",
            "H": H, "H_over_m": H / m, "ms_per_iter": t * 1e3,
-           "gteps": m / t / 1e9, "bytes_per_iter": alg, "bytes_formula": "4m + 10H + 16n",
+           "gteps": m / t / 1e9, "bytes_per_iter": alg, "bytes_formula": "2m + 10H + 16n",
            "roofline_frac": alg / t / 1e9 / peak,
            "spu_ms_per_iter": statistics.median(ms_spu) / iters,
            "speedup_vs_spu": statistics.median(ms_spu) / statistics.median(ms),

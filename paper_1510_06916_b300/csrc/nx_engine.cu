@@ -912,8 +912,8 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       st->strategy = (uint32_t)strategy;
       st->ms = ms;
       st->edges_swept = g->m * iters;
-      // words, hub values written and read, hub offsets, staged c, outdeg, r, c
-      st->bytes_model = (uint64_t)iters * (4 * g->m + 10 * g->oc.H + 16 * n64);
+      // 16-bit edge entries, hub values written and read, hub offsets, staged c, outdeg, r, c
+      st->bytes_model = (uint64_t)iters * (2 * g->m + 10 * g->oc.H + 16 * n64);
       st->launches = (g->oc.na ? 2 : 1) * iters;
     }
     return NX_OK;

@@ -160,11 +160,11 @@ struct Dsss {
 // to stage in shared memory for ToHub, and destination intervals of
 // 2^kOcDstBits vertices, whose compensated accumulators fit shared memory for
 // FromHub. Edges are sorted by (source interval i, destination interval j,
-// destination, source), rows (i) outermost, and stored as one word each:
-// src_local | dst_local << 15 | (ordinal of the sub-shard (i, j) & 1) << 29.
-// A hub entry is a run of equal (i, j, destination), also cut at every
-// multiple of kOcSeg edges; a segment is a window of the edge array between
-// cuts and row starts, so no hub entry crosses a segment.
+// destination, source), rows (i) outermost. A hub entry is a run of equal
+// (i, j, destination), also cut at every multiple of kOcSeg edges; a segment
+// is a window of the edge array between cuts and row starts, so no hub entry
+// crosses a segment. ToHub needs only the source and where entries start, so
+// each edge is stored as 16 bits: src_local | (entry start) << 15.
 constexpr uint32_t kOcSrcBits = 15;
 constexpr uint32_t kOcDstBits = 14;
 constexpr uint32_t kOcSeg = 2048;
@@ -180,7 +180,7 @@ struct OnChip {
   bool built = false;
   uint32_t PA = 0, PB = 0;     // source (row) and destination (column) intervals
   uint64_t m = 0, H = 0;       // edges, hub entries
-  DevBuf ew;                   // uint32 [round_up(m, 16) + 16]
+  DevBuf ew;                   // uint16 [round_up(m, 16) + 16]
   DevBuf seg_e;                // uint64 [nseg + 1]: first edge of each segment
   DevBuf seg_h;                // uint64 [nseg]: first hub entry of each segment
   DevBuf hub_dst;              // uint16 [H]: destination offset in its column

@@ -20,7 +20,6 @@
 namespace nx {
 namespace {
 
-constexpr uint32_t kSent = 0xFFFFFFFFu;
 constexpr int kOcThreads = 1024;
 constexpr int kOcWarps = kOcThreads / 32;
 constexpr uint32_t kSrcLen = 1u << kOcSrcBits;  // source interval (ToHub)
@@ -39,24 +38,16 @@ __global__ void k_oc_keys(const uint32_t* __restrict__ s, const uint32_t* __rest
   }
 }
 
-// Sub-shard (i, j) starts.
-__global__ void k_oc_ssflag(const uint64_t* __restrict__ key, uint64_t m, uint32_t* __restrict__ f) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
-    f[e] = (e == 0 || (key[e] >> 29) != (key[e - 1] >> 29)) ? 1u : 0u;
-}
-
-// Edge words and hub-entry starts (a new (i, j, destination), or a cut every
-// kOcSeg edges).
-__global__ void k_oc_words(const uint64_t* __restrict__ key, const uint32_t* __restrict__ ssf,
-                           const uint32_t* __restrict__ ssord, uint64_t m,
-                           uint32_t* __restrict__ ew, uint32_t* __restrict__ head) {
+// Hub-entry starts (a new (i, j, destination), or a cut every kOcSeg edges)
+// and the 16-bit edge entries ToHub reads: src_local | start << 15.
+__global__ void k_oc_words(const uint64_t* __restrict__ key, uint64_t m,
+                           uint16_t* __restrict__ ew, uint32_t* __restrict__ head) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
     const uint64_t k = key[e];
-    const uint32_t par = (ssord[e] + ssf[e]) & 1u;
-    ew[e] = (uint32_t)(k & 0x1FFFFFFFull) | (par << 29);
-    head[e] = (e == 0 || (k >> 15) != (key[e - 1] >> 15) || e % kOcSeg == 0) ? 1u : 0u;
+    const bool h = e == 0 || (k >> 15) != (key[e - 1] >> 15) || e % kOcSeg == 0;
+    ew[e] = (uint16_t)((k & (kSrcLen - 1)) | (h ? 0x8000u : 0u));
+    head[e] = h ? 1u : 0u;
   }
 }
 
@@ -92,7 +83,7 @@ unsigned grid_n(uint64_t work) {
 
 // ---------------------------------------------------------------- ToHub
 struct ArgsA {
-  const uint32_t* ew;
+  const uint16_t* ew;
   const uint64_t* seg_e;
   const uint64_t* seg_h;
   const OcItemA* items;
@@ -102,37 +93,24 @@ struct ArgsA {
   uint32_t n, nseg;
 };
 
-// One 256-edge step of a segment (see oc_segment). FULL: every edge of the
-// step lies inside the segment, so no edge needs a range check.
+// One 256-edge step of a segment (see oc_segment): lane l holds the 16-bit
+// entries of edges base + 8 l .. + 7 (source offset, and bit 15 set where a
+// hub entry starts). FULL: every edge of the step lies inside the segment.
 template <bool FULL>
-__device__ __forceinline__ void oc_step(const uint4 w0, const uint4 w1, uint64_t base, uint64_t e0,
-                                        uint64_t e1, const float* __restrict__ csh,
-                                        float* __restrict__ hv, uint32_t hlim, uint32_t& ckey,
-                                        uint32_t& cnt, float& csum) {
+__device__ __forceinline__ void oc_step(const uint4 w, uint64_t base, uint64_t e0, uint64_t e1,
+                                        const float* __restrict__ csh, float* __restrict__ hv,
+                                        uint32_t hlim, uint32_t& cnt, float& csum) {
   const int lane = threadIdx.x & 31;
-  const uint32_t wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-  uint32_t key[8];
+  const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
   float val[8];
+  uint32_t hm = 0;
   const uint64_t p0 = base + (uint64_t)lane * 8;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    if (FULL) {
-      key[k] = wv[k] >> 15;
-      val[k] = csh[wv[k] & (kSrcLen - 1)];
-    } else {
-      const bool valid = p0 + k >= e0 && p0 + k < e1;
-      key[k] = valid ? (wv[k] >> 15) : kSent;
-      val[k] = valid ? csh[wv[k] & (kSrcLen - 1)] : 0.f;
-    }
-  }
-  uint32_t pk = __shfl_up_sync(0xffffffffu, key[7], 1);
-  if (lane == 0) pk = ckey;
-  uint32_t hm = 0;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const uint32_t prev = k ? key[k - 1] : pk;
-    const bool h = FULL ? (key[k] != prev) : (key[k] != kSent && key[k] != prev);
-    hm |= (h ? 1u : 0u) << k;
+    const uint32_t e = (wv[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+    const bool valid = FULL || (p0 + k >= e0 && p0 + k < e1);
+    val[k] = valid ? csh[e & (kSrcLen - 1)] : 0.f;
+    hm |= (valid ? (e >> 15) : 0u) << k;
   }
   const uint32_t hc = __popc(hm);
   uint32_t incl = hc;
@@ -175,20 +153,19 @@ __device__ __forceinline__ void oc_step(const uint4 w0, const uint4 w1, uint64_t
   }
   float prev = __shfl_up_sync(0xffffffffu, x, 1);
   if (lane == 0) prev = csum;
-  // the run that ends just before this lane's first head
-  if (nh && (hb > 0 || ckey != kSent)) {
+  // the run that ends just before this lane's first head (if a run is open)
+  if (nh && hb > 0) {
     const uint32_t idx = hb - 1;
     if (idx < hlim) hv[idx] = prev + F;
   }
   csum = __shfl_sync(0xffffffffu, x, 31);
-  ckey = __shfl_sync(0xffffffffu, key[7], 31);  // the open run's key (a later step follows a full one)
   cnt += htot;
 }
 
-// One warp, one segment: 256-edge steps (two 16-byte loads per lane, the
-// next step prefetched), source values from shared memory, runs of equal
-// destination reduced in registers and across lanes; every hub entry is
-// written once, the run open at the end of a step carried to the next step.
+// One warp, one segment: 256-edge steps (one 16-byte load per lane, the next
+// step prefetched), source values from shared memory, runs reduced in
+// registers and across lanes; every hub entry is written once, the run open
+// at the end of a step carried to the next step.
 __device__ __forceinline__ void oc_segment(const ArgsA& a, const float* __restrict__ csh,
                                            uint32_t q) {
   const int lane = threadIdx.x & 31;
@@ -197,30 +174,24 @@ __device__ __forceinline__ void oc_segment(const ArgsA& a, const float* __restri
   const uint32_t hlim = h1 > h0 ? (uint32_t)(h1 - h0) : 0u;  // entries of this segment
   float* hv = a.hub_val + h0;
   uint64_t base = e0 & ~7ull;
-  uint4 nx0 = make_uint4(0, 0, 0, 0), nx1 = nx0;
+  uint4 nx = make_uint4(0, 0, 0, 0);
   {
     const uint64_t p = base + (uint64_t)lane * 8;
-    if (p < e1) {
-      nx0 = __ldcs(reinterpret_cast<const uint4*>(a.ew + p));
-      nx1 = __ldcs(reinterpret_cast<const uint4*>(a.ew + p + 4));
-    }
+    if (p < e1) nx = __ldcs(reinterpret_cast<const uint4*>(a.ew + p));
   }
-  uint32_t ckey = kSent, cnt = 0;  // key of the open run, hub entries started so far
-  float csum = 0.f;                // the open run's partial sum
+  uint32_t cnt = 0;  // hub entries started so far (> 0: a run is open)
+  float csum = 0.f;  // the open run's partial sum
   while (base < e1) {
-    const uint4 w0 = nx0, w1 = nx1;
+    const uint4 w = nx;
     const uint64_t nbase = base + 256;
     {
       const uint64_t p = nbase + (uint64_t)lane * 8;
-      if (p < e1) {
-        nx0 = __ldcs(reinterpret_cast<const uint4*>(a.ew + p));
-        nx1 = __ldcs(reinterpret_cast<const uint4*>(a.ew + p + 4));
-      }
+      if (p < e1) nx = __ldcs(reinterpret_cast<const uint4*>(a.ew + p));
     }
     if (base >= e0 && nbase <= e1)
-      oc_step<true>(w0, w1, base, e0, e1, csh, hv, hlim, ckey, cnt, csum);
+      oc_step<true>(w, base, e0, e1, csh, hv, hlim, cnt, csum);
     else
-      oc_step<false>(w0, w1, base, e0, e1, csh, hv, hlim, ckey, cnt, csum);
+      oc_step<false>(w, base, e0, e1, csh, hv, hlim, cnt, csum);
     base = nbase;
   }
   if (lane == 0 && cnt && cnt - 1 < hlim) hv[cnt - 1] = csum;  // the segment's last run
@@ -396,28 +367,21 @@ nx_status build_onchip(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64
   oc.PB = (uint32_t)ceil_div(n, kDstLen);
   if ((uint64_t)oc.PA * oc.PB > (1ull << 26))
     return invalid("nx_build_dsss: NX_ONCHIP_HUBS supports n up to about 9.5e7 vertices");
-  const uint64_t words = round_up(m, kEdgeAlign) + kEdgeAlign;
-  NX_TRY(oc.ew.alloc(words * 4));
-  NX_CUDA(cudaMemsetAsync(oc.ew.p, 0, words * 4, st));
+  const uint64_t words = round_up(m, kEdgeAlign) + kEdgeAlign;  // 16-bit entries
+  NX_TRY(oc.ew.alloc(words * 2));
+  NX_CUDA(cudaMemsetAsync(oc.ew.p, 0, words * 2, st));
   std::vector<uint32_t> cnt((size_t)oc.PA * oc.PB, 0);
   std::vector<uint32_t> rows(oc.PA, 0);
   if (m) {
-    DevBuf key, f, ord, head, hidx, dcnt, drows, tot;
+    DevBuf key, head, hidx, dcnt, drows, tot;
     NX_TRY(key.alloc(m * 8));
     k_oc_keys<<<grid_n(m), 256, 0, st>>>(s, d, m, key.as<uint64_t>());
     NX_LAUNCH_CHECK();
     NX_TRY(radix_sort_u64(key.as<uint64_t>(), nullptr, m, 45 + std::max<uint32_t>(1, bits_for(oc.PA))));
-    NX_TRY(f.alloc(m * 4));
-    NX_TRY(ord.alloc(m * 4));
-    k_oc_ssflag<<<grid_n(m), 256, 0, st>>>(key.as<uint64_t>(), m, f.as<uint32_t>());
-    NX_LAUNCH_CHECK();
-    NX_TRY(exclusive_scan_u32(f.as<uint32_t>(), ord.as<uint32_t>(), m, nullptr));
     NX_TRY(head.alloc(m * 4));
-    k_oc_words<<<grid_n(m), 256, 0, st>>>(key.as<uint64_t>(), f.as<uint32_t>(), ord.as<uint32_t>(),
-                                          m, oc.ew.as<uint32_t>(), head.as<uint32_t>());
+    k_oc_words<<<grid_n(m), 256, 0, st>>>(key.as<uint64_t>(), m, oc.ew.as<uint16_t>(),
+                                          head.as<uint32_t>());
     NX_LAUNCH_CHECK();
-    f.release();
-    ord.release();
     NX_TRY(hidx.alloc(m * 4));
     NX_TRY(tot.alloc(4));
     NX_TRY(exclusive_scan_u32(head.as<uint32_t>(), hidx.as<uint32_t>(), m, tot.as<uint32_t>()));
@@ -570,7 +534,7 @@ nx_status onchip_iteration(nx_graph* g, const OcRun& r, cudaStream_t s) {
   NX_CUDA(cudaFuncSetAttribute(k_oc_fromhub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
   if (oc.na) {
     ArgsA a{};
-    a.ew = oc.ew.as<uint32_t>();
+    a.ew = oc.ew.as<uint16_t>();
     a.seg_e = oc.seg_e.as<uint64_t>();
     a.seg_h = oc.seg_h.as<uint64_t>();
     a.items = oc.items_a.as<OcItemA>();
