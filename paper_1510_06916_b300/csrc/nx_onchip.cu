@@ -64,11 +64,19 @@ __global__ void k_oc_hubs(const uint64_t* __restrict__ key, const uint32_t* __re
   }
 }
 
-// Edges per row (source interval).
-__global__ void k_oc_rows(const uint64_t* __restrict__ key, uint64_t m, uint32_t* __restrict__ rc) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
-    atomicAdd(rc + (key[e] >> 45), 1u);
+// First edge of each row (source interval) in the sorted keys: rs[r] = the
+// first e with key[e] >> 45 >= r (a binary search per row).
+__global__ void k_oc_row_starts(const uint64_t* __restrict__ key, uint64_t m, uint32_t PA,
+                                uint64_t* __restrict__ rs) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > PA) return;
+  uint64_t lo = 0, hi = m;
+  while (lo < hi) {
+    const uint64_t mid = lo + ((hi - lo) >> 1);
+    if ((key[mid] >> 45) < r) lo = mid + 1;
+    else hi = mid;
+  }
+  rs[r] = lo;
 }
 
 __global__ void k_oc_seg_hub(const uint64_t* __restrict__ seg_e, uint32_t nseg,
@@ -371,7 +379,7 @@ nx_status build_onchip(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64
   NX_TRY(oc.ew.alloc(words * 2));
   NX_CUDA(cudaMemsetAsync(oc.ew.p, 0, words * 2, st));
   std::vector<uint32_t> cnt((size_t)oc.PA * oc.PB, 0);
-  std::vector<uint32_t> rows(oc.PA, 0);
+  std::vector<uint64_t> row_start(oc.PA + 1, 0);
   if (m) {
     DevBuf key, head, hidx, dcnt, drows, tot;
     NX_TRY(key.alloc(m * 8));
@@ -397,21 +405,20 @@ nx_status build_onchip(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64
                                          hidx.as<uint32_t>(), m, oc.PB, oc.hub_dst.as<uint16_t>(),
                                          dcnt.as<uint32_t>());
     NX_LAUNCH_CHECK();
-    NX_TRY(drows.alloc((size_t)oc.PA * 4));
-    NX_CUDA(cudaMemsetAsync(drows.p, 0, (size_t)oc.PA * 4, st));
-    k_oc_rows<<<grid_n(m), 256, 0, st>>>(key.as<uint64_t>(), m, drows.as<uint32_t>());
+    NX_TRY(drows.alloc(((size_t)oc.PA + 1) * 8));
+    k_oc_row_starts<<<(unsigned)ceil_div(oc.PA + 1, 256), 256, 0, st>>>(key.as<uint64_t>(), m, oc.PA,
+                                                                        drows.as<uint64_t>());
     NX_LAUNCH_CHECK();
     NX_CUDA(cudaMemcpyAsync(cnt.data(), dcnt.p, cnt.size() * 4, cudaMemcpyDeviceToHost, st));
-    NX_CUDA(cudaMemcpyAsync(rows.data(), drows.p, rows.size() * 4, cudaMemcpyDeviceToHost, st));
+    NX_CUDA(cudaMemcpyAsync(row_start.data(), drows.p, row_start.size() * 8, cudaMemcpyDeviceToHost, st));
     NX_CUDA(cudaStreamSynchronize(st));
     key.release();
     head.release();
     // segments: windows between multiples of kOcSeg and row starts
     std::vector<uint64_t> seg_e;
     std::vector<OcItemA> items_a;
-    uint64_t rs = 0;
     for (uint32_t r = 0; r < oc.PA; ++r) {
-      const uint64_t re = rs + rows[r];
+      const uint64_t rs = row_start[r], re = row_start[r + 1];
       uint32_t first = (uint32_t)seg_e.size();
       for (uint64_t e = rs; e < re;) {
         seg_e.push_back(e);
@@ -420,7 +427,6 @@ nx_status build_onchip(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64
       const uint32_t last = (uint32_t)seg_e.size();
       for (uint32_t q = first; q < last; q += kSegsPerItem)
         items_a.push_back(OcItemA{r, q, std::min<uint32_t>(last, q + kSegsPerItem), 0});
-      rs = re;
     }
     oc.nseg = (uint32_t)seg_e.size();
     seg_e.push_back(m);

@@ -87,3 +87,44 @@ def test_default_workload_is_the_scale_26_graph():
     import argparse  # noqa: F401  (the parser's default is checked by name below)
     src = open(bench.__file__).read()
     assert 'ap.add_argument("--workload", default="rmat26"' in src
+
+
+def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
+    # the committed DRAM-traffic record applies only while the sweep kernel's
+    # sources hash to what was captured; any edit turns it into null
+    import hashlib
+    import json
+
+    root = tmp_path
+    (root / "profiles").mkdir()
+    src = root / "k.cu"
+    src.write_text("kernel v1")
+    h = hashlib.sha256(src.read_bytes()).hexdigest()
+    (root / "profiles" / "traffic.json").write_text(json.dumps(
+        {"rmatX": {"bytes_per_launch": 123, "sources_sha256": {"k.cu": h}}}))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.traffic_record("rmatX") == 123
+    assert bench.traffic_record("other") is None
+    src.write_text("kernel v2")
+    assert bench.traffic_record("rmatX") is None
+
+
+def test_committed_traffic_record_matches_the_current_sweep_kernel():
+    import hashlib
+    import json
+    import os
+
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    for wl in ("rmat25", "rmat26"):
+        ent = rec[wl]
+        assert ent["bytes_per_launch"] > 0
+        for f, h in ent["sources_sha256"].items():
+            assert hashlib.sha256(open(os.path.join(bench.ROOT, f), "rb").read()).hexdigest() == h, f
+
+
+def test_compact_extras_keep_scalars_and_errors():
+    out = bench.compact({"rmat22": {"gteps": 1.0, "roofline_frac": 0.2, "D": 5},
+                         "scc": {"error": "x" * 500}, "unknown": {"a": 1}, "bad": 3})
+    assert out["rmat22"] == {"gteps": 1.0, "roofline_frac": 0.2}
+    assert len(out["scc"]["error"]) == 120
+    assert out["unknown"] == {} and "bad" not in out
