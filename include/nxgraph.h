@@ -114,7 +114,9 @@ typedef struct {
 
 typedef struct {
   uint32_t iters_done;    /* sweeps performed                                   */
-  uint32_t Q;             /* resident intervals used (MPU; P for SPU, 0 for DPU) */
+  uint32_t Q;             /* resident intervals used (MPU; P for SPU and
+                             NX_DPU_ONCHIP, 0 for DPU); NX_SCC: coloring rounds;
+                             nx_run_multi: 1 if the kept CUDA graph was replayed */
   uint32_t strategy;      /* the strategy that ran (after NX_AUTO)              */
   uint32_t streamed_cols; /* shards streamed from pinned host per iteration     */
   float ms;               /* wall time of the iteration loop (CUDA events)      */
@@ -122,7 +124,9 @@ typedef struct {
   uint64_t bytes_model;   /* algorithmic device bytes of the loop: per sweep 4 B
                              per edge read (8 B weighted) + 16 n (PageRank family:
                              gather, outdeg, new values, contributions) or 12 n
-                             (BFS / WCC); DPU adds 12 B per hub entry          */
+                             (BFS / WCC / SCC); DPU adds 12 B per hub entry;
+                             NX_DPU_ONCHIP: 2 B per edge + 10 B per hub entry
+                             (H_onchip) + 16 n                                 */
   uint64_t h2d_bytes;     /* host->device bytes of the loop (streaming)         */
   uint64_t d2h_bytes;     /* device->host bytes of the loop                     */
   uint32_t launches;      /* kernels launched by the loop                       */
@@ -173,8 +177,14 @@ void nx_last_error(char* buf, size_t len);
  * component, gradients; edge gradients stay in caller edge order). Only
  * nx_dsss_export reports internal ids. nx_run_multi and
  * nx_pagerank_step_noalloc reject relabeled graphs.
+ * NX_ONCHIP_HUBS also builds the row-major structure of NX_DPU_ONCHIP (its
+ * edges sorted by source interval of 2^15 vertices, destination interval of
+ * 2^14, destination, source; one 16-bit entry per edge and one hub entry per
+ * run of equal (source interval, destination), cut every 2048 edges).
+ * NX_TILE_CAP_LOG2 / NX_TILE_EDGES_LOG2 choose the tile shape.
  * Errors: INVALID_ARG (an id >= n, P out of range, m >= 2^32, n > 2^30,
- * missing w), OOM, CUDA.
+ * missing w, tile shape out of range, unknown flag bits, NX_ONCHIP_HUBS with
+ * more than about 9.5e7 vertices), OOM, CUDA.
  */
 nx_status nx_build_dsss(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n,
                         uint32_t P, uint32_t flags, const float* w, nx_graph** out);
@@ -359,7 +369,8 @@ void nx_graph_free(nx_graph* g);
  * it and must be serialised by the caller. Runs on the stream of
  * nx_set_stream and returns when the step is complete.
  * Errors: INVALID_ARG (NULL pointers, r_in == r_out, alpha outside [0, 1),
- * too many tiles, a graph built with NX_RELABEL), CUDA.
+ * too many tiles, a graph built with NX_RELABEL, a graph whose arrays a run
+ * with a device budget moved to host memory), CUDA.
  */
 nx_status nx_pagerank_step_noalloc(const nx_graph* g, float alpha, const float* r_in,
                                    float* r_out);
