@@ -337,9 +337,10 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   EventPair ev;
   NX_TRY(ev.create());
   NX_CUDA(cudaEventRecord(ev.e0, stream()));
-  // Degrees of the input ids can be counted as the edges arrive unless the
-  // ids are renamed first (NX_RELABEL counts them after renaming).
-  const bool early_deg = !(flags & NX_RELABEL);
+  // Degrees of the input ids are counted as the edges arrive (overlapping the
+  // upload of host edges); NX_RELABEL orders the vertices by them and then
+  // permutes them to the new ids (a renamed vertex keeps its degrees).
+  const bool early_deg = true;
   DevBuf indeg, bad;
   NX_TRY(g->outdeg.alloc((uint64_t)n * 4));
   NX_TRY(indeg.alloc((uint64_t)n * 4));
@@ -413,13 +414,17 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
       so = rs.as<uint32_t>();
       dout = rd.as<uint32_t>();
     }
-    NX_TRY(relabel_edges(g, s, d, m, so, dout));
+    NX_TRY(relabel_edges(g, s, d, m, so, dout, g->outdeg.as<uint32_t>()));
     s = so;
     d = dout;
-    if (m) {  // degrees of the renamed ids
-      k_histogram<<<grid_for(m), 256, 0, stream()>>>(s, m, g->outdeg.as<uint32_t>());
-      k_histogram<<<grid_for(m), 256, 0, stream()>>>(d, m, indeg.as<uint32_t>());
-      NX_LAUNCH_CHECK();
+    {  // degrees of the renamed ids: new vertex k is caller vertex old_of_new[k]
+      DevBuf od2, id2;
+      NX_TRY(od2.alloc((uint64_t)n * 4));
+      NX_TRY(id2.alloc((uint64_t)n * 4));
+      NX_TRY(gather_u32(g->old_of_new.as<uint32_t>(), g->outdeg.p, od2.p, n));
+      NX_TRY(gather_u32(g->old_of_new.as<uint32_t>(), indeg.p, id2.p, n));
+      g->outdeg = std::move(od2);
+      indeg = std::move(id2);
     }
   }
   geo.P = P;

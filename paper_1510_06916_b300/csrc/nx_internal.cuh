@@ -306,9 +306,10 @@ nx_status onchip_iteration(nx_graph* g, const OcRun& r, cudaStream_t s);
 
 // Relabel (nx_relabel.cu). relabel_edges computes the vertex order (out-degree
 // descending, ties by caller id) into g and writes the renamed endpoints
-// (s_out / d_out may alias s / d). gather_u32: out[k] = in[idx[k]] for k < n.
+// (s_out / d_out may alias s / d) from the caller ids' out-degrees `outdeg`.
+// gather_u32: out[k] = in[idx[k]] for k < n.
 nx_status relabel_edges(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64_t m,
-                        uint32_t* s_out, uint32_t* d_out);
+                        uint32_t* s_out, uint32_t* d_out, const uint32_t* outdeg);
 nx_status gather_u32(const uint32_t* idx, const void* in, void* out, uint64_t n);
 // Vertex arrays across the ABI: caller order -> internal order (to_internal)
 // or back; a plain copy for graphs that were not relabeled. `in` and `out`

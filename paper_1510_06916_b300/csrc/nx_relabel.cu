@@ -11,12 +11,6 @@
 namespace nx {
 namespace {
 
-__global__ void k_outdeg(const uint32_t* __restrict__ s, uint64_t m, uint32_t* __restrict__ od) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
-    atomicAdd(&od[s[e]], 1u);
-}
-
 // key = (m - outdeg) << vb | v: ascending keys = descending degree, then id.
 __global__ void k_order_keys(const uint32_t* __restrict__ od, uint32_t n, uint64_t m, uint32_t vb,
                              uint64_t* __restrict__ keys) {
@@ -60,19 +54,13 @@ unsigned grid_of(uint64_t work) {
 }  // namespace
 
 nx_status relabel_edges(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64_t m,
-                        uint32_t* s_out, uint32_t* d_out) {
+                        uint32_t* s_out, uint32_t* d_out, const uint32_t* outdeg) {
   const uint32_t n = g->geo.n;
   const uint32_t vb = std::max<uint32_t>(1, bits_for(n));
   const uint32_t db = bits_for(m + 1);
-  DevBuf od, keys;
-  NX_TRY(od.alloc((uint64_t)n * 4));
+  DevBuf keys;
   NX_TRY(keys.alloc((uint64_t)n * 8));
-  NX_CUDA(cudaMemsetAsync(od.p, 0, (uint64_t)n * 4, stream()));
-  if (m) {
-    k_outdeg<<<grid_of(m), 256, 0, stream()>>>(s, m, od.as<uint32_t>());
-    NX_LAUNCH_CHECK();
-  }
-  k_order_keys<<<grid_of(n), 256, 0, stream()>>>(od.as<uint32_t>(), n, m, vb, keys.as<uint64_t>());
+  k_order_keys<<<grid_of(n), 256, 0, stream()>>>(outdeg, n, m, vb, keys.as<uint64_t>());
   NX_LAUNCH_CHECK();
   NX_TRY(radix_sort_u64(keys.as<uint64_t>(), nullptr, n, vb + db));
   NX_TRY(g->old_of_new.alloc((uint64_t)n * 4));
