@@ -155,6 +155,14 @@ typedef struct {
 /* Stream for all later calls (a cudaStream_t; NULL = legacy default stream). */
 nx_status nx_set_stream(void* stream);
 
+/* Device memory cache. The library allocates from a stream-ordered pool of its
+ * own per device that keeps freed blocks (up to half of the device's memory)
+ * for the next build or run, the way a caching allocator does. This call
+ * synchronises the device and returns every cached, unused block of the
+ * current device's pool to the driver (memory held by live graphs stays).
+ * Errors: NX_ERR_CUDA if the device cannot be synchronised. */
+nx_status nx_trim_memory(void);
+
 /* Copies the last error message of this thread into buf (always terminated). */
 void nx_last_error(char* buf, size_t len);
 

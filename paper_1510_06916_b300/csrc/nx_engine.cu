@@ -95,36 +95,67 @@ uint64_t target_block_edges(uint64_t total) {
   return std::max<uint64_t>(16384, e);
 }
 
+// Appends the items to `out` heaviest first (ties in the order they were
+// made, as a stable sort would leave them).
+void emit_heaviest_first(std::vector<std::pair<uint64_t, uint32_t>>& key,
+                         const std::vector<Item>& made, PlanOut& out) {
+  std::sort(key.begin(), key.end(), [](const auto& a, const auto& b) {
+    return a.first > b.first || (a.first == b.first && a.second < b.second);
+  });
+  out.items.reserve(out.items.size() + key.size());
+  out.cost.reserve(out.cost.size() + key.size());
+  for (const auto& k : key) {
+    out.items.push_back(made[k.second]);
+    out.cost.push_back(k.first);
+  }
+}
+
+// Items of one tile (or piece) of `cost` edges: split into k parts of about
+// `blk` edges when it is heavier than 2 blk.
+void make_items(uint32_t t, uint64_t cost, bool allow_split, uint64_t blk, uint32_t row,
+                uint32_t sx, std::vector<std::pair<uint64_t, uint32_t>>& key,
+                std::vector<Item>& made, PlanOut& out) {
+  uint32_t k = 1;
+  if (allow_split && cost > 2 * blk) k = (uint32_t)ceil_div(cost, blk);
+  for (uint32_t q = 0; q < k; ++q) {
+    Item it{};
+    it.tile = t;
+    it.nsplit = k;
+    it.slot = k > 1 ? out.slots : 0;
+    it.sub = q;
+    it.row = row;
+    it.pad = sx;
+    it.vbeg = cost * q / k;
+    it.vend = (q + 1 == k) ? ~0ull : cost * (q + 1) / k;
+    key.push_back({cost / k + 1, (uint32_t)made.size()});
+    made.push_back(it);
+  }
+  if (k > 1) out.slots += k;
+}
+
 // Tiles of columns [c0, c1), sweeping sources [i0, i1) over `ds`.
 void plan_tiles(const nx_graph* g, const std::vector<const Dsss*>& ds, uint32_t i0, uint32_t i1,
                 uint32_t c0, uint32_t c1, bool allow_split, uint64_t blk, PlanOut& out) {
   const auto& tb = g->geo.h_col_tb;
-  std::vector<std::pair<uint64_t, Item>> tmp;
-  for (uint32_t j = c0; j < c1; ++j)
-    for (uint32_t t = tb[j]; t < tb[j + 1]; ++t) {
-      uint64_t cost = 0;
-      for (const Dsss* d : ds)
-        for (uint32_t i = i0; i < i1; ++i) cost += piece_len(g, *d, i, t, j);
-      uint32_t k = 1;
-      if (allow_split && cost > 2 * blk) k = (uint32_t)ceil_div(cost, blk);
-      for (uint32_t q = 0; q < k; ++q) {
-        Item it{};
-        it.tile = t;
-        it.nsplit = k;
-        it.slot = k > 1 ? out.slots : 0;
-        it.sub = q;
-        it.vbeg = cost * q / k;
-        it.vend = (q + 1 == k) ? ~0ull : cost * (q + 1) / k;
-        tmp.push_back({cost / k + 1, it});
+  const uint32_t P = g->geo.P, t0 = tb[c0], t1 = tb[c1];
+  // edges per tile: pieces (i, t) of one column and source are consecutive
+  std::vector<uint64_t> cost((size_t)(t1 - t0), 0);
+  for (uint32_t j = c0; j < c1; ++j) {
+    const uint32_t nt = tb[j + 1] - tb[j];
+    uint64_t* cj = cost.data() + (tb[j] - t0);
+    for (const Dsss* d : ds)
+      for (uint32_t i = i0; i < i1; ++i) {
+        const uint64_t* po = d->h_piece_off.data() + piece_index(P, tb[j], nt, i, tb[j]);
+        for (uint32_t q = 0; q < nt; ++q) cj[q] += po[q + 1] - po[q];
       }
-      if (k > 1) out.slots += k;
-    }
-  std::stable_sort(tmp.begin(), tmp.end(),
-                   [](const auto& a, const auto& b) { return a.first > b.first; });
-  for (auto& p : tmp) {
-    out.items.push_back(p.second);
-    out.cost.push_back(p.first);
   }
+  std::vector<std::pair<uint64_t, uint32_t>> key;
+  std::vector<Item> made;
+  key.reserve(cost.size() + 64);
+  made.reserve(cost.size() + 64);
+  for (uint32_t t = t0; t < t1; ++t)
+    make_items(t, cost[t - t0], allow_split, blk, 0, 0, key, made, out);
+  emit_heaviest_first(key, made, out);
 }
 
 // Single pieces (i, t) of row i of DSSS number `sx` for tiles of columns
@@ -132,32 +163,14 @@ void plan_tiles(const nx_graph* g, const std::vector<const Dsss*>& ds, uint32_t 
 void plan_row(const nx_graph* g, const Dsss& d, uint32_t sx, uint32_t i, uint32_t c0, uint32_t c1,
               uint64_t blk, PlanOut& out) {
   const auto& tb = g->geo.h_col_tb;
-  std::vector<std::pair<uint64_t, Item>> tmp;
+  std::vector<std::pair<uint64_t, uint32_t>> key;
+  std::vector<Item> made;
   for (uint32_t j = c0; j < c1; ++j)
     for (uint32_t t = tb[j]; t < tb[j + 1]; ++t) {
-      uint64_t cost = piece_len(g, d, i, t, j);
-      if (!cost) continue;
-      uint32_t k = cost > 2 * blk ? (uint32_t)ceil_div(cost, blk) : 1;
-      for (uint32_t q = 0; q < k; ++q) {
-        Item it{};
-        it.tile = t;
-        it.nsplit = k;
-        it.slot = k > 1 ? out.slots : 0;
-        it.sub = q;
-        it.row = i;
-        it.pad = sx;
-        it.vbeg = cost * q / k;
-        it.vend = (q + 1 == k) ? ~0ull : cost * (q + 1) / k;
-        tmp.push_back({cost / k + 1, it});
-      }
-      if (k > 1) out.slots += k;
+      const uint64_t cost = piece_len(g, d, i, t, j);
+      if (cost) make_items(t, cost, true, blk, i, sx, key, made, out);
     }
-  std::stable_sort(tmp.begin(), tmp.end(),
-                   [](const auto& a, const auto& b) { return a.first > b.first; });
-  for (auto& p : tmp) {
-    out.items.push_back(p.second);
-    out.cost.push_back(p.first);
-  }
+  emit_heaviest_first(key, made, out);
 }
 
 // ---------------------------------------------------------------- buffers

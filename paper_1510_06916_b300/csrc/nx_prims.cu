@@ -44,34 +44,38 @@ int num_sms() {
 }
 
 // ---------------------------------------------------------------- buffers
-// The pool keeps up to kPoolKeep bytes of freed memory for reuse (graphs built
-// and run one after another reuse it); memory above that goes back to the
-// driver at the next synchronisation.
-static constexpr uint64_t kPoolKeep = 4ull << 30;
+// The pool keeps freed memory for reuse, up to half of the device's memory
+// (graphs built and run one after another reuse it instead of mapping new
+// pages: at R-MAT scale 26 a build and its first run allocate about 40 GB of
+// temporaries); memory above that goes back to the driver at the next
+// synchronisation, and nx_trim_memory() returns all of it.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
 
 static cudaError_t pool_of_current_device(cudaMemPool_t* out) {
-  static std::mutex mu;
-  static cudaMemPool_t pools[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!pools[dev]) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    size_t free_b = 0, total_b = 0;
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) return e;
     cudaMemPoolProps props = {};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = dev;
-    e = cudaMemPoolCreate(&pools[dev], &props);
+    e = cudaMemPoolCreate(&g_pools[dev], &props);
     if (e != cudaSuccess) {
-      pools[dev] = nullptr;
+      g_pools[dev] = nullptr;
       return e;
     }
-    uint64_t keep = kPoolKeep;
-    e = cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    uint64_t keep = total_b / 2;
+    e = cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
     if (e != cudaSuccess) return e;
   }
-  *out = pools[dev];
+  *out = g_pools[dev];
   return cudaSuccess;
 }
 
@@ -444,6 +448,21 @@ nx_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t n, uint32_t ke
 
 extern "C" nx_status nx_set_stream(void* s) {
   nx::g_stream = (cudaStream_t)s;
+  return NX_OK;
+}
+
+extern "C" nx_status nx_trim_memory(void) {
+  int dev = 0;
+  NX_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return NX_OK;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(nx::g_pool_mu);
+    pool = nx::g_pools[dev];
+  }
+  if (!pool) return NX_OK;
+  NX_CUDA(cudaDeviceSynchronize());  // frees still queued on streams reach the pool
+  NX_CUDA(cudaMemPoolTrimTo(pool, 0));
   return NX_OK;
 }
 

@@ -26,7 +26,7 @@ STRATEGIES = {"spu": SPU, "dpu": DPU, "mpu": MPU, "auto": AUTO,
               "src_coarse": SRC_COARSE, "src_fine": SRC_FINE, "dpu_onchip": DPU_ONCHIP}
 
 EXPORTS = [
-    "nx_set_stream", "nx_last_error", "nx_build_dsss", "nx_graph_get_info", "nx_run",
+    "nx_set_stream", "nx_trim_memory", "nx_last_error", "nx_build_dsss", "nx_graph_get_info", "nx_run",
     "nx_get_values", "nx_set_values", "nx_run_ppr_batch", "nx_adjoint_wpr", "nx_run_multi",
     "nx_graph_free", "nx_io_model", "nx_dsss_export", "nx_pagerank_step_noalloc",
     "nx_autotune", "nx_get_relabel", "nx_bfs_max_depth", "nx_set_barrier_limit",
@@ -89,6 +89,7 @@ def lib():
                                   ctypes.c_int32, ctypes.c_float)
         d = ctypes.c_double
         L.nx_set_stream.argtypes = [vp]
+        L.nx_trim_memory.argtypes = []
         L.nx_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         L.nx_last_error.restype = None
         L.nx_build_dsss.argtypes = [vp, vp, u64, u32, u32, u32, vp, ctypes.POINTER(vp)]
@@ -167,6 +168,11 @@ def set_stream(stream) -> None:
     """Stream for later calls: a torch.cuda.Stream, a raw handle, or None."""
     h = getattr(stream, "cuda_stream", stream)
     check(lib().nx_set_stream(ctypes.c_void_p(h or 0)))
+
+
+def trim_memory() -> None:
+    """Returns the library's cached, unused device memory to the driver."""
+    check(lib().nx_trim_memory())
 
 
 def set_barrier_limit(cycles: int) -> None:
