@@ -115,50 +115,81 @@ struct PieceMap {
   }
 };
 
-// Edge words and run-head flags (first edge of each (piece, destination) run).
+// Edge words, run-head bits and piece starts. A run is the edges of one
+// (piece, destination); its first edge is its head, and each head owns one hub
+// entry. Each warp takes 32 consecutive edges: hbits[w] holds their head bits
+// and hcnt[w] the number of heads; pieces (pc(e-1), pc(e)] start at edge e.
 __global__ void k_words(const uint64_t* __restrict__ keys, uint64_t m, PieceMap pm,
-                        uint32_t* __restrict__ ew, uint32_t* __restrict__ head) {
-  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-    uint32_t d, t, sl;
-    uint64_t pc = pm.piece(keys[e], &d, &t, &sl);
-    ew[e] = ((d - pm.tile_start[t]) << pm.kc.lb) | sl;
-    bool h = true;
-    if (e > 0) {
-      uint32_t d0, t0, sl0;
-      uint64_t pc0 = pm.piece(keys[e - 1], &d0, &t0, &sl0);
-      h = (pc0 != pc) || (d0 != d);
+                        uint32_t* __restrict__ ew, uint32_t* __restrict__ hbits,
+                        uint32_t* __restrict__ hcnt, uint64_t* __restrict__ piece_off) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nw = (m + 31) / 32;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += nwarps) {
+    const uint64_t e = w * 32 + lane;
+    const bool valid = e < m;
+    uint32_t d = 0, t = 0, sl = 0;
+    uint64_t pc = 0;
+    if (valid) {
+      pc = pm.piece(keys[e], &d, &t, &sl);
+      ew[e] = ((d - pm.tile_start[t]) << pm.kc.lb) | sl;
     }
-    head[e] = h ? 1u : 0u;
+    uint64_t pc0 = __shfl_up_sync(0xffffffffu, pc, 1);
+    uint32_t d0 = __shfl_up_sync(0xffffffffu, d, 1);
+    if (lane == 0 && e > 0) {  // the previous edge belongs to the previous warp's range
+      uint32_t t0, sl0;
+      pc0 = pm.piece(keys[e - 1], &d0, &t0, &sl0);
+    }
+    const bool head = valid && (e == 0 || pc0 != pc || d0 != d);
+    const uint32_t bits = __ballot_sync(0xffffffffu, head);
+    if (lane == 0) {
+      hbits[w] = bits;
+      hcnt[w] = __popc(bits);
+    }
+    if (valid) {
+      const uint64_t k0 = (e == 0) ? 0 : pc0 + 1;
+      for (uint64_t k = k0; k <= pc; ++k) piece_off[k] = e;
+    }
   }
 }
 
-// piece_off / hub_off boundaries and hub destination offsets. hidx is the
-// exclusive scan of the head flags (hub entry of each run).
-__global__ void k_bounds(const uint64_t* __restrict__ keys, uint64_t m, PieceMap pm,
-                         const uint32_t* __restrict__ hidx, const uint32_t* __restrict__ ew,
-                         uint64_t* __restrict__ piece_off, uint64_t* __restrict__ hub_off,
-                         uint16_t* __restrict__ hub_dst, uint64_t npieces, uint64_t D) {
-  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e <= m; e += stride) {
+// Pieces after the last edge's start at m.
+__global__ void k_piece_tail(const uint64_t* __restrict__ keys, uint64_t m, PieceMap pm,
+                             uint64_t* __restrict__ piece_off, uint64_t npieces) {
+  uint64_t k0 = 0;
+  if (m) {
     uint32_t d, t, sl;
-    uint64_t pc = e < m ? pm.piece(keys[e], &d, &t, &sl) : npieces;
-    uint64_t prev = 0;
-    bool first = (e == 0);
-    if (!first) {
-      uint32_t d0, t0, sl0;
-      prev = pm.piece(keys[e - 1], &d0, &t0, &sl0) + 1;
-    }
-    uint64_t h = e < m ? (uint64_t)hidx[e] : D;
-    for (uint64_t k = prev; k <= pc && k <= npieces; ++k) {
-      piece_off[k] = e;
-      hub_off[k] = h;
-    }
-    if (e < m) {
-      // hidx is the exclusive scan of the head flags: a head is where it steps
-      bool is_head = (e + 1 < m) ? (hidx[e + 1] != hidx[e]) : ((uint64_t)hidx[e] + 1 == D);
-      if (is_head) hub_dst[hidx[e]] = (uint16_t)(ew[e] >> pm.kc.lb);
-    }
+    k0 = pm.piece(keys[m - 1], &d, &t, &sl) + 1;
+  }
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t k = k0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= npieces; k += stride)
+    piece_off[k] = m;
+}
+
+// Hub entry of edge e: the heads before it (hpre = exclusive scan of hcnt).
+__device__ __forceinline__ uint64_t hub_index(const uint32_t* hbits, const uint32_t* hpre, uint64_t e) {
+  const uint64_t w = e >> 5;
+  const uint32_t lt = (1u << (e & 31)) - 1u;
+  return (uint64_t)hpre[w] + __popc(hbits[w] & lt);
+}
+
+// Destination offset (within its tile) of every hub entry.
+__global__ void k_hub_dst(const uint32_t* __restrict__ ew, const uint32_t* __restrict__ hbits,
+                          const uint32_t* __restrict__ hpre, uint64_t m, uint32_t lb,
+                          uint16_t* __restrict__ hub_dst) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+    if ((hbits[e >> 5] >> (e & 31)) & 1u) hub_dst[hub_index(hbits, hpre, e)] = (uint16_t)(ew[e] >> lb);
+}
+
+// First hub entry of every piece (D for pieces that start at m).
+__global__ void k_hub_off(const uint64_t* __restrict__ piece_off, const uint32_t* __restrict__ hbits,
+                          const uint32_t* __restrict__ hpre, uint64_t m, uint64_t D,
+                          uint64_t* __restrict__ hub_off, uint64_t npieces) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= npieces; k += stride) {
+    const uint64_t e = piece_off[k];
+    hub_off[k] = e >= m ? D : hub_index(hbits, hpre, e);
   }
 }
 
@@ -211,7 +242,7 @@ nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geom
     k_make_keys<<<grid_for(m), 256, 0, stream()>>>(s, d, m, kc, keys.as<uint64_t>(),
                                                    wn ? idx.as<uint32_t>() : nullptr);
     NX_LAUNCH_CHECK();
-    NX_TRY(radix_sort_u64(keys.as<uint64_t>(), wn ? idx.as<uint32_t>() : nullptr, m, key_bits));
+    NX_TRY(radix_sort_u64(keys, wn ? &idx : nullptr, m, key_bits));
   }
   const uint64_t mpad = round_up(m, kEdgeAlign) + kEdgeAlign;
   NX_TRY(out.ew.alloc(mpad * sizeof(uint32_t)));
@@ -219,14 +250,17 @@ nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geom
   NX_TRY(out.piece_off.alloc((npieces + 1) * sizeof(uint64_t)));
   NX_TRY(out.hub_off.alloc((npieces + 1) * sizeof(uint64_t)));
   PieceMap pm{kc, tile_of, geo.tile_start.as<uint32_t>(), geo.col_tb.as<uint32_t>()};
-  DevBuf head, dtot;
-  NX_TRY(head.alloc(std::max<uint64_t>(m, 1) * sizeof(uint32_t)));
+  const uint64_t nw = (m + 31) / 32;
+  DevBuf hbits, hcnt, dtot;
+  NX_TRY(hbits.alloc(std::max<uint64_t>(nw, 1) * sizeof(uint32_t)));
+  NX_TRY(hcnt.alloc(std::max<uint64_t>(nw, 1) * sizeof(uint32_t)));
   NX_TRY(dtot.alloc(sizeof(uint32_t)));
   if (m) {
     k_words<<<grid_for(m), 256, 0, stream()>>>(keys.as<uint64_t>(), m, pm, out.ew.as<uint32_t>(),
-                                               head.as<uint32_t>());
+                                               hbits.as<uint32_t>(), hcnt.as<uint32_t>(),
+                                               out.piece_off.as<uint64_t>());
     NX_LAUNCH_CHECK();
-    NX_TRY(exclusive_scan_u32(head.as<uint32_t>(), head.as<uint32_t>(), m, dtot.as<uint32_t>()));
+    NX_TRY(exclusive_scan_u32(hcnt.as<uint32_t>(), hcnt.as<uint32_t>(), nw, dtot.as<uint32_t>()));
     uint32_t D32 = 0;
     NX_CUDA(cudaMemcpyAsync(&D32, dtot.p, sizeof D32, cudaMemcpyDeviceToHost, stream()));
     NX_CUDA(cudaStreamSynchronize(stream()));
@@ -234,11 +268,19 @@ nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geom
   } else {
     out.D = 0;
   }
+  k_piece_tail<<<grid_for(npieces + 1), 256, 0, stream()>>>(keys.as<uint64_t>(), m, pm,
+                                                           out.piece_off.as<uint64_t>(), npieces);
+  NX_LAUNCH_CHECK();
   NX_TRY(out.hub_dst.alloc(std::max<uint64_t>(out.D, 1) * sizeof(uint16_t)));
-  k_bounds<<<grid_for(m + 1), 256, 0, stream()>>>(
-      keys.as<uint64_t>(), m, pm, head.as<uint32_t>(), out.ew.as<uint32_t>(),
-      out.piece_off.as<uint64_t>(), out.hub_off.as<uint64_t>(), out.hub_dst.as<uint16_t>(),
-      npieces, out.D);
+  if (m) {
+    k_hub_dst<<<grid_for(m), 256, 0, stream()>>>(out.ew.as<uint32_t>(), hbits.as<uint32_t>(),
+                                                 hcnt.as<uint32_t>(), m, geo.lb,
+                                                 out.hub_dst.as<uint16_t>());
+    NX_LAUNCH_CHECK();
+  }
+  k_hub_off<<<grid_for(npieces + 1), 256, 0, stream()>>>(
+      out.piece_off.as<uint64_t>(), hbits.as<uint32_t>(), hcnt.as<uint32_t>(), m, out.D,
+      out.hub_off.as<uint64_t>(), npieces);
   NX_LAUNCH_CHECK();
   if (wn) {
     NX_TRY(out.wt.alloc(mpad * sizeof(float)));

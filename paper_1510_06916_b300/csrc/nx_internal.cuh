@@ -122,8 +122,10 @@ constexpr uint64_t kEdgeAlign = 16;
 nx_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* total);
 nx_status exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* total);
 // LSD radix sort of 64-bit keys over bits [0, key_bits), stable, with an
-// optional uint32 payload. keys/vals are sorted in place (scratch internal).
-nx_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t n, uint32_t key_bits);
+// optional uint32 payload. On return keys/vals hold the sorted data, possibly
+// in buffers swapped in from the sort's scratch (at least n elements), so
+// pointers taken from them before the call are stale.
+nx_status radix_sort_u64(DevBuf& keys, DevBuf* vals, uint64_t n, uint32_t key_bits);
 // Smallest shared-memory carveout that keeps the occupancy of kernel `fn`
 // (`threads` per block, `smem` dynamic bytes); the rest of L1 caches loads.
 nx_status prefer_l1(const void* fn, int threads, size_t smem);

@@ -385,7 +385,7 @@ nx_status build_onchip(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64
     NX_TRY(key.alloc(m * 8));
     k_oc_keys<<<grid_n(m), 256, 0, st>>>(s, d, m, key.as<uint64_t>());
     NX_LAUNCH_CHECK();
-    NX_TRY(radix_sort_u64(key.as<uint64_t>(), nullptr, m, 45 + std::max<uint32_t>(1, bits_for(oc.PA))));
+    NX_TRY(radix_sort_u64(key, nullptr, m, 45 + std::max<uint32_t>(1, bits_for(oc.PA))));
     NX_TRY(head.alloc(m * 4));
     k_oc_words<<<grid_n(m), 256, 0, st>>>(key.as<uint64_t>(), m, oc.ew.as<uint16_t>(),
                                           head.as<uint32_t>());

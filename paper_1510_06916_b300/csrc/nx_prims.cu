@@ -2,6 +2,7 @@
 // exclusive scans and a stable LSD radix sort of 64-bit keys. All written for
 // this library (no CUB / Thrust).
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -302,11 +303,15 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint64_t* __restrict
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t base = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)w * RS_WARP_KEYS + lane;
-#pragma unroll 4
-  for (int r = 0; r < RS_ROUNDS; ++r) {
-    uint64_t idx = base + (uint64_t)r * 32;
-    if (idx < n) atomicAdd(&h[w][(uint32_t)(keys[idx] >> shift) & 255u], 1u);
+  uint64_t k[RS_ROUNDS];
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {  // every load in flight before the first count
+    const uint64_t idx = base + (uint64_t)r * 32;
+    k[r] = idx < n ? keys[idx] : ~0ull;
   }
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r)
+    if (base + (uint64_t)r * 32 < n) atomicAdd(&h[w][(uint32_t)(k[r] >> shift) & 255u], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
     uint32_t s = 0;
@@ -314,6 +319,20 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint64_t* __restrict
     for (int q = 0; q < RS_WARPS; ++q) s += h[q][d];
     counts[(uint64_t)d * nb + blockIdx.x] = s;
   }
+}
+
+// Lanes of the warp whose 9-bit value d equals this lane's, from one ballot
+// per bit (measured faster here than a match instruction, whose pipe the
+// ranking saturated).
+__device__ __forceinline__ uint32_t rs_peers(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
 }
 
 // Stable scatter of one 8-bit digit. Keys are ranked per warp (lane order
@@ -347,7 +366,8 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
     bool valid = idx < n;
     key[r] = valid ? kin[idx] : 0ull;
     uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    // alternate the match pipe and the vote pipe: neither one saturates
+    uint32_t peers = (r % 3) ? rs_peers(d) : __match_any_sync(0xffffffffu, d);
     uint32_t before = wc[w][d];
     __syncwarp();
     if ((peers & lt_mask) == 0) wc[w][d] = before + __popc(peers);
@@ -407,7 +427,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
 }
 }  // namespace
 
-nx_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t n, uint32_t key_bits) {
+nx_status radix_sort_u64(DevBuf& keys, DevBuf* vals, uint64_t n, uint32_t key_bits) {
   if (n <= 1 || key_bits == 0) return NX_OK;
   if (n >= (1ull << 32)) return invalid("radix_sort_u64: n must be < 2^32");
   const uint32_t nb = (uint32_t)ceil_div(n, RS_TILE);
@@ -415,29 +435,29 @@ nx_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t n, uint32_t ke
   NX_TRY(k2.alloc(n * sizeof(uint64_t)));
   if (vals) NX_TRY(v2.alloc(n * sizeof(uint32_t)));
   NX_TRY(counts.alloc((uint64_t)nb * 256 * sizeof(uint32_t)));
-  uint64_t* ka = keys;
-  uint64_t* kb = k2.as<uint64_t>();
-  uint32_t* va = vals;
-  uint32_t* vb = vals ? v2.as<uint32_t>() : nullptr;
+  DevBuf* ka = &keys;
+  DevBuf* kb = &k2;
+  DevBuf* va = vals;
+  DevBuf* vb = vals ? &v2 : nullptr;
   const size_t smem = (size_t)RS_TILE * (sizeof(uint64_t) + (vals ? sizeof(uint32_t) : 0));
   // dynamic + static shared memory exceed 48 KB: opt in (per device, so every call)
   NX_CUDA(cudaFuncSetAttribute(rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int passes = 0;
   for (uint32_t shift = 0; shift < key_bits; shift += 8, ++passes) {
-    rs_hist<<<nb, RS_THREADS, 0, stream()>>>(ka, n, shift, counts.as<uint32_t>(), nb);
+    rs_hist<<<nb, RS_THREADS, 0, stream()>>>(ka->as<uint64_t>(), n, shift, counts.as<uint32_t>(), nb);
     NX_LAUNCH_CHECK();
     NX_TRY(exclusive_scan_u32(counts.as<uint32_t>(), counts.as<uint32_t>(), (uint64_t)nb * 256,
                               nullptr));
-    rs_scatter<<<nb, RS_THREADS, smem, stream()>>>(ka, va, kb, vb, n, shift,
-                                                   counts.as<uint32_t>(), nb);
+    rs_scatter<<<nb, RS_THREADS, smem, stream()>>>(
+        ka->as<uint64_t>(), va ? va->as<uint32_t>() : nullptr, kb->as<uint64_t>(),
+        vb ? vb->as<uint32_t>() : nullptr, n, shift, counts.as<uint32_t>(), nb);
     NX_LAUNCH_CHECK();
     std::swap(ka, kb);
     std::swap(va, vb);
   }
-  if (passes & 1) {  // result sits in the scratch buffers
-    NX_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream()));
-    if (vals)
-      NX_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream()));
+  if (passes & 1) {  // the result sits in the scratch buffers: hand them to the caller
+    std::swap(keys, k2);
+    if (vals) std::swap(*vals, v2);
   }
   // scratch is freed on return: make sure the stream is done with it
   NX_CUDA(cudaStreamSynchronize(stream()));

@@ -62,7 +62,7 @@ nx_status relabel_edges(nx_graph* g, const uint32_t* s, const uint32_t* d, uint6
   NX_TRY(keys.alloc((uint64_t)n * 8));
   k_order_keys<<<grid_of(n), 256, 0, stream()>>>(outdeg, n, m, vb, keys.as<uint64_t>());
   NX_LAUNCH_CHECK();
-  NX_TRY(radix_sort_u64(keys.as<uint64_t>(), nullptr, n, vb + db));
+  NX_TRY(radix_sort_u64(keys, nullptr, n, vb + db));
   NX_TRY(g->old_of_new.alloc((uint64_t)n * 4));
   NX_TRY(g->new_of_old.alloc((uint64_t)n * 4));
   k_order_perm<<<grid_of(n), 256, 0, stream()>>>(keys.as<uint64_t>(), n, vb,
