@@ -290,7 +290,7 @@ nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geom
       NX_LAUNCH_CHECK();
     }
   }
-  out.h_piece_off.resize(npieces + 1);
+  NX_TRY(out.h_piece_off.resize(npieces + 1));
   NX_CUDA(cudaMemcpyAsync(out.h_piece_off.data(), out.piece_off.p, (npieces + 1) * sizeof(uint64_t),
                           cudaMemcpyDeviceToHost, stream()));
   NX_CUDA(cudaStreamSynchronize(stream()));

@@ -95,18 +95,34 @@ uint64_t target_block_edges(uint64_t total) {
   return std::max<uint64_t>(16384, e);
 }
 
-// Appends the items to `out` heaviest first (ties in the order they were
-// made, as a stable sort would leave them).
-void emit_heaviest_first(std::vector<std::pair<uint64_t, uint32_t>>& key,
+// Appends the items to `out` heaviest first: a counting sort on the cost
+// rounded down to 8 steps per octave (ties and near-ties in the order they
+// were made), linear in the item count.
+void emit_heaviest_first(const std::vector<std::pair<uint64_t, uint32_t>>& key,
                          const std::vector<Item>& made, PlanOut& out) {
-  std::sort(key.begin(), key.end(), [](const auto& a, const auto& b) {
-    return a.first > b.first || (a.first == b.first && a.second < b.second);
-  });
-  out.items.reserve(out.items.size() + key.size());
-  out.cost.reserve(out.cost.size() + key.size());
-  for (const auto& k : key) {
-    out.items.push_back(made[k.second]);
-    out.cost.push_back(k.first);
+  auto bucket = [](uint64_t c) -> uint32_t {  // c >= 1
+    const uint32_t e = 63u - (uint32_t)__builtin_clzll(c);
+    const uint32_t frac = e >= 3 ? (uint32_t)(c >> (e - 3)) & 7u : (uint32_t)(c << (3 - e)) & 7u;
+    return e * 8 + frac;
+  };
+  constexpr uint32_t kBuckets = 64 * 8;
+  std::vector<uint32_t> start(kBuckets + 1, 0);
+  for (const auto& k : key) ++start[kBuckets - 1 - bucket(k.first)];
+  uint32_t acc = 0;
+  for (uint32_t b = 0; b <= kBuckets; ++b) {
+    const uint32_t c = start[b];
+    start[b] = acc;
+    acc += c;
+  }
+  std::vector<uint32_t> order(key.size());
+  for (uint32_t q = 0; q < (uint32_t)key.size(); ++q)
+    order[start[kBuckets - 1 - bucket(key[q].first)]++] = q;
+  const size_t base = out.items.size();
+  out.items.resize(base + key.size());
+  out.cost.resize(base + key.size());
+  for (size_t q = 0; q < order.size(); ++q) {
+    out.items[base + q] = made[key[order[q]].second];
+    out.cost[base + q] = key[order[q]].first;
   }
 }
 
@@ -211,15 +227,15 @@ nx_status prepare(nx_graph* g) {
   return NX_OK;
 }
 
-nx_status upload_items(nx_graph*, const PlanOut& plan, nx_graph::Plan& dst) {
+nx_status upload_items(nx_graph*, PlanOut& plan, nx_graph::Plan& dst) {
   NX_TRY(dst.items.alloc(std::max<size_t>(plan.items.size(), 1) * sizeof(Item)));
   if (!plan.items.empty())
     NX_CUDA(cudaMemcpyAsync(dst.items.p, plan.items.data(), plan.items.size() * sizeof(Item),
                             cudaMemcpyHostToDevice, stream()));
   NX_CUDA(cudaStreamSynchronize(stream()));  // plan.items is a host temporary
   dst.slots = plan.slots;
-  dst.h_cost = plan.cost;
-  dst.h_items = plan.items;
+  dst.h_cost = std::move(plan.cost);
+  dst.h_items = std::move(plan.items);
   return NX_OK;
 }
 
@@ -1297,7 +1313,7 @@ nx_status probe_impl(nx_graph* g, uint32_t sweeps, float* ms_per_sweep) {
       off.push_back((uint32_t)plan.items.size());
     }
     NX_TRY(upload_items(g, plan, *slot));
-    slot->na = (uint32_t)plan.items.size();
+    slot->na = (uint32_t)slot->h_items.size();
     slot->off = off;
   }
   NX_TRY(ensure_split(g, slot->slots));
@@ -1392,7 +1408,7 @@ nx_status tr_plan(nx_graph* g, nx_graph::Plan** out) {
     std::vector<const Dsss*> ds{&g->tr};
     plan_tiles(g, ds, 0, g->geo.P, 0, g->geo.P, true, target_block_edges(g->m), plan);
     NX_TRY(upload_items(g, plan, *slot));
-    slot->na = (uint32_t)plan.items.size();
+    slot->na = (uint32_t)slot->h_items.size();
   }
   NX_TRY(ensure_split(g, slot->slots));
   *out = slot.get();
@@ -1415,7 +1431,7 @@ nx_status scc_impl(nx_graph* g, uint32_t max_sweeps, nx_run_stats* st) {
     std::vector<const Dsss*> ds{&g->fwd};
     plan_tiles(g, ds, 0, P, 0, P, true, target_block_edges(g->m), plan);
     NX_TRY(upload_items(g, plan, *fslot));
-    fslot->na = (uint32_t)plan.items.size();
+    fslot->na = (uint32_t)fslot->h_items.size();
   }
   NX_TRY(ensure_split(g, fslot->slots));
   nx_graph::Plan* tpl = nullptr;
@@ -1732,7 +1748,7 @@ nx_status multi_impl(nx_graph** gs, uint32_t count, nx_program prog, float alpha
       PlanOut plan;
       plan_tiles(g, ds, 0, g->geo.P, 0, g->geo.P, true, target_block_edges(g->m * ds.size()), plan);
       NX_TRY(upload_items(g, plan, *slot));
-      slot->na = (uint32_t)plan.items.size();
+      slot->na = (uint32_t)slot->h_items.size();
     }
     NX_TRY(ensure_split(g, slot->slots));
     SweepArgs a = base_args(g, prog, p, nullptr);

@@ -88,6 +88,45 @@ struct PinnedBuf {
   template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Pinned host blocks from a process-wide cache: a freed block is kept (up to
+// 512 MB in all) for the next request of about its size, so a graph built
+// after another one reuses pinned pages instead of pinning and zeroing new ones.
+void* pinned_take(size_t bytes, size_t* got);
+void pinned_give(void* p, size_t bytes);
+
+// Host array in a cached pinned block (device-to-host copies into it run at
+// full speed); resize() leaves the contents undefined.
+template <class T> struct PinnedArray {
+  T* p = nullptr;
+  size_t n = 0, cap = 0;  // cap: bytes of the block
+  PinnedArray() = default;
+  PinnedArray(const PinnedArray&) = delete;
+  PinnedArray& operator=(const PinnedArray&) = delete;
+  ~PinnedArray() { release(); }
+  void release() {
+    if (p) pinned_give(p, cap);
+    p = nullptr;
+    n = cap = 0;
+  }
+  nx_status resize(size_t count) {
+    if (count * sizeof(T) > cap) {
+      release();
+      size_t got = 0;
+      p = static_cast<T*>(pinned_take(count * sizeof(T), &got));
+      if (!p) return NX_ERR_OOM;
+      cap = got;
+    }
+    n = count;
+    return NX_OK;
+  }
+  T& operator[](size_t i) { return p[i]; }
+  const T& operator[](size_t i) const { return p[i]; }
+  T* data() { return p; }
+  const T* data() const { return p; }
+  size_t size() const { return n; }
+  bool empty() const { return n == 0; }
+};
+
 // Two timing events, destroyed on every exit path.
 struct EventPair {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -143,7 +182,7 @@ struct Dsss {
   DevBuf hub_off;    // uint64 [npieces+1]: hub entries before each piece
   DevBuf hub_dst;    // uint16 [D]: destination offset in its tile of each hub entry
   uint64_t D = 0;
-  std::vector<uint64_t> h_piece_off;
+  PinnedArray<uint64_t> h_piece_off;  // host copy of piece_off
   // Residency under a device budget: words [0, dev_words) of the edge array
   // are on the device; the pinned host image h_ew holds words
   // [h_ew_first, words) (h_ew_first <= dev_words, so together they hold every

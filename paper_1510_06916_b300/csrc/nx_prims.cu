@@ -117,6 +117,50 @@ nx_status DevBuf::alloc(size_t n) {
   bytes = n;
   return NX_OK;
 }
+static std::mutex g_pinned_mu;
+static std::vector<std::pair<void*, size_t>> g_pinned_free;  // cached blocks
+static size_t g_pinned_cached = 0;
+constexpr size_t kPinnedCacheMax = 512ull << 20;
+
+void* pinned_take(size_t bytes, size_t* got) {
+  bytes = std::max<size_t>(bytes, 64);
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    for (size_t q = 0; q < g_pinned_free.size(); ++q) {
+      const auto blk = g_pinned_free[q];
+      if (blk.second >= bytes && blk.second <= 2 * bytes) {
+        g_pinned_free.erase(g_pinned_free.begin() + q);
+        g_pinned_cached -= blk.second;
+        *got = blk.second;
+        return blk.first;
+      }
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    char buf[160];
+    snprintf(buf, sizeof buf, "pinned host allocation of %zu bytes failed", bytes);
+    set_error(buf);
+    return nullptr;
+  }
+  *got = bytes;
+  return p;
+}
+
+void pinned_give(void* p, size_t bytes) {
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    if (g_pinned_cached + bytes <= kPinnedCacheMax) {
+      g_pinned_free.push_back({p, bytes});
+      g_pinned_cached += bytes;
+      return;
+    }
+  }
+  cudaFreeHost(p);
+}
+
 void PinnedBuf::release() {
   if (p) cudaFreeHost(p);
   p = nullptr;

@@ -11,20 +11,31 @@
 namespace nx {
 namespace {
 
-// key = (m - outdeg) << vb | v: ascending keys = descending degree, then id.
-__global__ void k_order_keys(const uint32_t* __restrict__ od, uint32_t n, uint64_t m, uint32_t vb,
-                             uint64_t* __restrict__ keys) {
+__global__ void k_max_u32(const uint32_t* __restrict__ a, uint32_t n, uint32_t* __restrict__ out) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint32_t mx = 0;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-    keys[v] = ((m - od[v]) << vb) | v;
+    mx = max(mx, a[v]);
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
 }
 
-__global__ void k_order_perm(const uint64_t* __restrict__ keys, uint32_t n, uint32_t vb,
+// key = max_deg - outdeg (ascending keys = descending degree), value = v: the
+// stable sort leaves equal degrees in id order.
+__global__ void k_order_keys(const uint32_t* __restrict__ od, uint32_t n, uint32_t max_deg,
+                             uint64_t* __restrict__ keys, uint32_t* __restrict__ ids) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    keys[v] = max_deg - od[v];
+    ids[v] = (uint32_t)v;
+  }
+}
+
+__global__ void k_order_perm(const uint32_t* __restrict__ ids, uint32_t n,
                              uint32_t* __restrict__ old_of_new, uint32_t* __restrict__ new_of_old) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t mask = (1ull << vb) - 1;
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-    const uint32_t old = (uint32_t)(keys[k] & mask);
+    const uint32_t old = ids[k];
     old_of_new[k] = old;
     new_of_old[old] = (uint32_t)k;
   }
@@ -56,17 +67,23 @@ unsigned grid_of(uint64_t work) {
 nx_status relabel_edges(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64_t m,
                         uint32_t* s_out, uint32_t* d_out, const uint32_t* outdeg) {
   const uint32_t n = g->geo.n;
-  const uint32_t vb = std::max<uint32_t>(1, bits_for(n));
-  const uint32_t db = bits_for(m + 1);
-  DevBuf keys;
-  NX_TRY(keys.alloc((uint64_t)n * 8));
-  k_order_keys<<<grid_of(n), 256, 0, stream()>>>(outdeg, n, m, vb, keys.as<uint64_t>());
+  DevBuf keys, ids, mx;
+  NX_TRY(mx.alloc(4));
+  NX_CUDA(cudaMemsetAsync(mx.p, 0, 4, stream()));
+  k_max_u32<<<grid_of(n), 256, 0, stream()>>>(outdeg, n, mx.as<uint32_t>());
   NX_LAUNCH_CHECK();
-  NX_TRY(radix_sort_u64(keys, nullptr, n, vb + db));
+  uint32_t max_deg = 0;
+  NX_CUDA(cudaMemcpyAsync(&max_deg, mx.p, 4, cudaMemcpyDeviceToHost, stream()));
+  NX_CUDA(cudaStreamSynchronize(stream()));
+  NX_TRY(keys.alloc((uint64_t)n * 8));
+  NX_TRY(ids.alloc((uint64_t)n * 4));
+  k_order_keys<<<grid_of(n), 256, 0, stream()>>>(outdeg, n, max_deg, keys.as<uint64_t>(),
+                                                 ids.as<uint32_t>());
+  NX_LAUNCH_CHECK();
+  NX_TRY(radix_sort_u64(keys, &ids, n, bits_for((uint64_t)max_deg + 1)));
   NX_TRY(g->old_of_new.alloc((uint64_t)n * 4));
   NX_TRY(g->new_of_old.alloc((uint64_t)n * 4));
-  k_order_perm<<<grid_of(n), 256, 0, stream()>>>(keys.as<uint64_t>(), n, vb,
-                                                 g->old_of_new.as<uint32_t>(),
+  k_order_perm<<<grid_of(n), 256, 0, stream()>>>(ids.as<uint32_t>(), n, g->old_of_new.as<uint32_t>(),
                                                  g->new_of_old.as<uint32_t>());
   NX_LAUNCH_CHECK();
   if (m) {
