@@ -89,12 +89,14 @@ struct KeyCodec {
   }
 };
 
+// rename (nullable): internal id of each input id, applied on the fly.
 __global__ void k_make_keys(const uint32_t* __restrict__ s, const uint32_t* __restrict__ d,
-                            uint64_t m, KeyCodec kc, uint64_t* __restrict__ keys,
-                            uint32_t* __restrict__ idx) {
+                            uint64_t m, KeyCodec kc, const uint32_t* __restrict__ rename,
+                            uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
   uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-    keys[e] = kc.encode(s[e], d[e]);
+    const uint32_t a = s[e], b = d[e];
+    keys[e] = rename ? kc.encode(rename[a], rename[b]) : kc.encode(a, b);
     if (idx) idx[e] = (uint32_t)e;
   }
 }
@@ -228,8 +230,10 @@ unsigned grid_for(uint64_t work, unsigned threads = 256) {
 
 // Builds one DSSS from (s, d) over the geometry; wn (nullable) are the
 // normalised weights in input order.
+// rename (nullable): applied to s and d while the keys are made.
 nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geometry& geo,
-                    const uint32_t* tile_of, const float* wn, Dsss& out) {
+                    const uint32_t* tile_of, const float* wn, Dsss& out,
+                    const uint32_t* rename = nullptr) {
   out.m = m;
   const uint64_t npieces = (uint64_t)geo.P * geo.ntiles;
   KeyCodec kc{geo.P, geo.L, geo.lb};
@@ -239,7 +243,7 @@ nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geom
   NX_TRY(keys.alloc(std::max<uint64_t>(m, 1) * sizeof(uint64_t)));
   if (wn) NX_TRY(idx.alloc(std::max<uint64_t>(m, 1) * sizeof(uint32_t)));
   if (m) {
-    k_make_keys<<<grid_for(m), 256, 0, stream()>>>(s, d, m, kc, keys.as<uint64_t>(),
+    k_make_keys<<<grid_for(m), 256, 0, stream()>>>(s, d, m, kc, rename, keys.as<uint64_t>(),
                                                    wn ? idx.as<uint32_t>() : nullptr);
     NX_LAUNCH_CHECK();
     NX_TRY(radix_sort_u64(keys, wn ? &idx : nullptr, m, key_bits));
@@ -447,7 +451,12 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   Geometry& geo = g->geo;
   geo.n = n;
   DevBuf rs, rd;
-  if (flags & NX_RELABEL) {  // degree-ordered ids; host inputs are renamed in their device copies
+  // With nothing but the forward DSSS to build, the keys apply the new ids
+  // themselves and the renamed endpoint arrays are never written.
+  const bool rename_in_keys = (flags & NX_RELABEL) && !want_t && !want_w && !(flags & NX_ONCHIP_HUBS);
+  if ((flags & NX_RELABEL) && rename_in_keys) {
+    NX_TRY(relabel_edges(g, s, d, m, nullptr, nullptr, g->outdeg.as<uint32_t>()));
+  } else if (flags & NX_RELABEL) {  // host inputs are renamed in their device copies
     uint32_t* so = ds.as<uint32_t>();
     uint32_t* dout = dd.as<uint32_t>();
     if (on_dev) {
@@ -459,6 +468,8 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
     NX_TRY(relabel_edges(g, s, d, m, so, dout, g->outdeg.as<uint32_t>()));
     s = so;
     d = dout;
+  }
+  if (flags & NX_RELABEL) {
     {  // degrees of the renamed ids: new vertex k is caller vertex old_of_new[k]
       DevBuf od2, id2;
       NX_TRY(od2.alloc((uint64_t)n * 4));
@@ -497,7 +508,8 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
     NX_CUDA(cudaStreamSynchronize(stream()));
     g->has_w = true;
   }
-  NX_TRY(build_one(s, d, m, geo, tile_of.as<uint32_t>(), want_w ? wn.as<float>() : nullptr, g->fwd));
+  NX_TRY(build_one(s, d, m, geo, tile_of.as<uint32_t>(), want_w ? wn.as<float>() : nullptr, g->fwd,
+                   rename_in_keys ? g->new_of_old.as<uint32_t>() : nullptr));
   if (flags & NX_ONCHIP_HUBS) NX_TRY(build_onchip(g, s, d, m));
   if (want_t) {
     NX_TRY(build_one(d, s, m, geo, tile_of.as<uint32_t>(), want_w ? wn.as<float>() : nullptr,

@@ -346,8 +346,9 @@ struct OcRun {
 nx_status onchip_iteration(nx_graph* g, const OcRun& r, cudaStream_t s);
 
 // Relabel (nx_relabel.cu). relabel_edges computes the vertex order (out-degree
-// descending, ties by caller id) into g and writes the renamed endpoints
-// (s_out / d_out may alias s / d) from the caller ids' out-degrees `outdeg`.
+// descending, ties by caller id) into g from the caller ids' out-degrees
+// `outdeg` and, when s_out is not NULL, writes the renamed endpoints (s_out /
+// d_out may alias s / d).
 // gather_u32: out[k] = in[idx[k]] for k < n.
 nx_status relabel_edges(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64_t m,
                         uint32_t* s_out, uint32_t* d_out, const uint32_t* outdeg);

@@ -86,7 +86,7 @@ nx_status relabel_edges(nx_graph* g, const uint32_t* s, const uint32_t* d, uint6
   k_order_perm<<<grid_of(n), 256, 0, stream()>>>(ids.as<uint32_t>(), n, g->old_of_new.as<uint32_t>(),
                                                  g->new_of_old.as<uint32_t>());
   NX_LAUNCH_CHECK();
-  if (m) {
+  if (m && s_out) {
     k_rename<<<grid_of(m), 256, 0, stream()>>>(g->new_of_old.as<uint32_t>(), s, d, m, s_out, d_out);
     NX_LAUNCH_CHECK();
   }
