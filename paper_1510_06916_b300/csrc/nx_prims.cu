@@ -332,18 +332,25 @@ nx_status prefer_l1(const void* fn, int threads, size_t smem) {
 }
 
 // ---------------------------------------------------------------- radix sort
+// Stable LSD radix sort in passes of at most 9 bits: per pass one kernel
+// counts each tile's digits, a scan turns the counts into the first output
+// slot of every (digit, tile), and one kernel ranks and scatters each tile.
 namespace {
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ROUNDS = 16;                     // keys per lane
 constexpr int RS_WARP_KEYS = 32 * RS_ROUNDS;      // 512
 constexpr int RS_TILE = RS_WARPS * RS_WARP_KEYS;  // 4096
+constexpr uint32_t RS_MAX_BITS = 9;
 
+// counts[d * nb + tile] = keys of the tile whose digit (key >> shift) & mask is d.
+template <int BITS>
 __global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint64_t* __restrict__ keys, uint64_t n,
-                                                      uint32_t shift, uint32_t* __restrict__ counts,
-                                                      uint32_t nb) {
-  __shared__ uint32_t h[RS_WARPS][256];
-  for (int k = threadIdx.x; k < RS_WARPS * 256; k += RS_THREADS) (&h[0][0])[k] = 0;
+                                                      uint32_t shift, uint32_t mask,
+                                                      uint32_t* __restrict__ counts, uint32_t nb) {
+  constexpr int NB = 1 << BITS;
+  __shared__ uint32_t h[RS_WARPS][NB];
+  for (int k = threadIdx.x; k < RS_WARPS * NB; k += RS_THREADS) (&h[0][0])[k] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t base = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)w * RS_WARP_KEYS + lane;
@@ -355,9 +362,9 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint64_t* __restrict
   }
 #pragma unroll
   for (int r = 0; r < RS_ROUNDS; ++r)
-    if (base + (uint64_t)r * 32 < n) atomicAdd(&h[w][(uint32_t)(k[r] >> shift) & 255u], 1u);
+    if (base + (uint64_t)r * 32 < n) atomicAdd(&h[w][(uint32_t)(k[r] >> shift) & mask], 1u);
   __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+  for (uint32_t d = threadIdx.x; d <= mask; d += RS_THREADS) {
     uint32_t s = 0;
 #pragma unroll
     for (int q = 0; q < RS_WARPS; ++q) s += h[q][d];
@@ -365,13 +372,13 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint64_t* __restrict
   }
 }
 
-// Lanes of the warp whose 9-bit value d equals this lane's, from one ballot
-// per bit (measured faster here than a match instruction, whose pipe the
-// ranking saturated).
+// Lanes of the warp whose NBITS-bit value d equals this lane's, from one
+// ballot per bit.
+template <int NBITS>
 __device__ __forceinline__ uint32_t rs_peers(uint32_t d) {
   uint32_t peers = 0xffffffffu;
 #pragma unroll
-  for (int b = 0; b < 9; ++b) {
+  for (int b = 0; b < NBITS; ++b) {
     const bool bit = (d >> b) & 1u;
     const uint32_t bal = __ballot_sync(0xffffffffu, bit);
     peers &= bit ? bal : ~bal;
@@ -379,23 +386,27 @@ __device__ __forceinline__ uint32_t rs_peers(uint32_t d) {
   return peers;
 }
 
-// Stable scatter of one 8-bit digit. Keys are ranked per warp (lane order
-// within a round, rounds in order, warps in order = input order), placed in
-// shared memory in digit order, and written out from there so that
+// Stable scatter of one digit of at most BITS bits. Keys are ranked per warp
+// (lane order within a round, rounds in order, warps in order = input order),
+// placed in shared memory in digit order, and written out from there so that
 // consecutive threads store consecutive addresses of one digit's run.
 // Dynamic shared memory: RS_TILE keys (+ RS_TILE values when vin != nullptr).
+template <int BITS>
 __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, uint64_t n, uint32_t shift, const uint32_t* __restrict__ offs,
-    uint32_t nb) {
+    uint32_t* __restrict__ vout, uint64_t n, uint32_t shift, uint32_t mask,
+    const uint32_t* __restrict__ offs, uint32_t nb) {
+  constexpr int NB = 1 << BITS;
+  constexpr int PER = NB / RS_THREADS > 0 ? NB / RS_THREADS : 1;  // digits per thread
+  static_assert(NB <= RS_THREADS * PER, "digit tables");
   extern __shared__ __align__(16) unsigned char rs_smem[];
   uint64_t* sk = reinterpret_cast<uint64_t*>(rs_smem);       // [RS_TILE]
   uint32_t* sv = reinterpret_cast<uint32_t*>(sk + RS_TILE);  // [RS_TILE] (values)
-  __shared__ uint32_t wc[RS_WARPS][257];
-  __shared__ uint32_t dstart[256];  // first local slot of each digit
-  __shared__ uint32_t gbase[256];   // first global slot of this block's run of each digit
+  __shared__ uint32_t wc[RS_WARPS][NB + 1];
+  __shared__ uint32_t dstart[NB];  // first local slot of each digit
+  __shared__ uint32_t gbase[NB];   // first global slot of this block's run of each digit
   __shared__ uint32_t wsum[RS_WARPS];
-  for (int k = threadIdx.x; k < RS_WARPS * 257; k += RS_THREADS) (&wc[0][0])[k] = 0;
+  for (int k = threadIdx.x; k < RS_WARPS * (NB + 1); k += RS_THREADS) (&wc[0][0])[k] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -409,9 +420,10 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
     uint64_t idx = base + (uint64_t)r * 32;
     bool valid = idx < n;
     key[r] = valid ? kin[idx] : 0ull;
-    uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
-    // alternate the match pipe and the vote pipe: neither one saturates
-    uint32_t peers = (r % 3) ? rs_peers(d) : __match_any_sync(0xffffffffu, d);
+    uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & mask) : (uint32_t)NB;
+    // the match pipe for one round in three, one ballot per bit otherwise:
+    // either alone saturates its pipe
+    uint32_t peers = (r % 3) ? rs_peers<BITS + 1>(d) : __match_any_sync(0xffffffffu, d);
     uint32_t before = wc[w][d];
     __syncwarp();
     if ((peers & lt_mask) == 0) wc[w][d] = before + __popc(peers);
@@ -420,15 +432,21 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
   }
   __syncthreads();
   // per digit: block total, then per-warp starts inside the digit's local run
-  uint32_t tot = 0;
-  if (threadIdx.x < 256) {
-    const int d = threadIdx.x;
+  uint32_t tot[PER];
+  uint32_t tsum = 0;
 #pragma unroll
-    for (int q = 0; q < RS_WARPS; ++q) tot += wc[q][d];
-    gbase[d] = offs[(uint64_t)d * nb + blockIdx.x];
+  for (int q = 0; q < PER; ++q) {
+    const uint32_t d = threadIdx.x * PER + q;
+    tot[q] = 0;
+    if (d < (uint32_t)NB) {
+#pragma unroll
+      for (int v = 0; v < RS_WARPS; ++v) tot[q] += wc[v][d];
+      gbase[d] = d <= mask ? offs[(uint64_t)d * nb + blockIdx.x] : 0u;
+    }
+    tsum += tot[q];
   }
-  // exclusive scan of the 256 digit totals (one per thread)
-  uint32_t x = tot;
+  // exclusive scan of the per-thread sums (digits in thread order)
+  uint32_t x = tsum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -438,15 +456,18 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
   __syncthreads();
   uint32_t pre = 0;
   for (int q = 0; q < w; ++q) pre += wsum[q];
-  if (threadIdx.x < 256) {
-    const int d = threadIdx.x;
-    uint32_t st = pre + x - tot;
-    dstart[d] = st;
+  uint32_t st = pre + x - tsum;
 #pragma unroll
-    for (int q = 0; q < RS_WARPS; ++q) {
-      const uint32_t t = wc[q][d];
-      wc[q][d] = st;
-      st += t;
+  for (int q = 0; q < PER; ++q) {
+    const uint32_t d = threadIdx.x * PER + q;
+    if (d < (uint32_t)NB) {
+      dstart[d] = st;
+#pragma unroll
+      for (int v = 0; v < RS_WARPS; ++v) {
+        const uint32_t t = wc[v][d];
+        wc[v][d] = st;
+        st += t;
+      }
     }
   }
   __syncthreads();
@@ -454,7 +475,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
   for (int r = 0; r < RS_ROUNDS; ++r) {
     uint64_t idx = base + (uint64_t)r * 32;
     if (idx < n) {
-      const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+      const uint32_t d = (uint32_t)(key[r] >> shift) & mask;
       const uint32_t lp = wc[w][d] + rank[r];
       sk[lp] = key[r];
       if (vin) sv[lp] = vin[idx];
@@ -463,7 +484,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < cnt; i += RS_THREADS) {
     const uint64_t k = sk[i];
-    const uint32_t d = (uint32_t)(k >> shift) & 255u;
+    const uint32_t d = (uint32_t)(k >> shift) & mask;
     const uint32_t pos = gbase[d] + (i - dstart[d]);
     kout[pos] = k;
     if (vin) vout[pos] = sv[i];
@@ -474,32 +495,51 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
 nx_status radix_sort_u64(DevBuf& keys, DevBuf* vals, uint64_t n, uint32_t key_bits) {
   if (n <= 1 || key_bits == 0) return NX_OK;
   if (n >= (1ull << 32)) return invalid("radix_sort_u64: n must be < 2^32");
+  key_bits = std::min<uint32_t>(key_bits, 64);
   const uint32_t nb = (uint32_t)ceil_div(n, RS_TILE);
+  // passes of at most 9 bits, as even as possible (52 bits: 9,9,9,9,8,8)
+  const uint32_t npass = (key_bits + RS_MAX_BITS - 1) / RS_MAX_BITS;
   DevBuf k2, v2, counts;
   NX_TRY(k2.alloc(n * sizeof(uint64_t)));
   if (vals) NX_TRY(v2.alloc(n * sizeof(uint32_t)));
-  NX_TRY(counts.alloc((uint64_t)nb * 256 * sizeof(uint32_t)));
+  NX_TRY(counts.alloc((uint64_t)nb * (1u << RS_MAX_BITS) * sizeof(uint32_t)));
   DevBuf* ka = &keys;
   DevBuf* kb = &k2;
   DevBuf* va = vals;
   DevBuf* vb = vals ? &v2 : nullptr;
   const size_t smem = (size_t)RS_TILE * (sizeof(uint64_t) + (vals ? sizeof(uint32_t) : 0));
   // dynamic + static shared memory exceed 48 KB: opt in (per device, so every call)
-  NX_CUDA(cudaFuncSetAttribute(rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int passes = 0;
-  for (uint32_t shift = 0; shift < key_bits; shift += 8, ++passes) {
-    rs_hist<<<nb, RS_THREADS, 0, stream()>>>(ka->as<uint64_t>(), n, shift, counts.as<uint32_t>(), nb);
+  NX_CUDA(cudaFuncSetAttribute(rs_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  NX_CUDA(cudaFuncSetAttribute(rs_scatter<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  uint32_t shift = 0;
+  for (uint32_t p = 0; p < npass; ++p) {
+    const uint32_t width = key_bits / npass + (p < key_bits % npass ? 1u : 0u);
+    const uint32_t mask = (1u << width) - 1u;
+    const uint64_t nc = (uint64_t)nb << width;
+    if (width > 8) {
+      rs_hist<9><<<nb, RS_THREADS, 0, stream()>>>(ka->as<uint64_t>(), n, shift, mask,
+                                                  counts.as<uint32_t>(), nb);
+    } else {
+      rs_hist<8><<<nb, RS_THREADS, 0, stream()>>>(ka->as<uint64_t>(), n, shift, mask,
+                                                  counts.as<uint32_t>(), nb);
+    }
     NX_LAUNCH_CHECK();
-    NX_TRY(exclusive_scan_u32(counts.as<uint32_t>(), counts.as<uint32_t>(), (uint64_t)nb * 256,
-                              nullptr));
-    rs_scatter<<<nb, RS_THREADS, smem, stream()>>>(
-        ka->as<uint64_t>(), va ? va->as<uint32_t>() : nullptr, kb->as<uint64_t>(),
-        vb ? vb->as<uint32_t>() : nullptr, n, shift, counts.as<uint32_t>(), nb);
+    NX_TRY(exclusive_scan_u32(counts.as<uint32_t>(), counts.as<uint32_t>(), nc, nullptr));
+    if (width > 8) {
+      rs_scatter<9><<<nb, RS_THREADS, smem, stream()>>>(
+          ka->as<uint64_t>(), va ? va->as<uint32_t>() : nullptr, kb->as<uint64_t>(),
+          vb ? vb->as<uint32_t>() : nullptr, n, shift, mask, counts.as<uint32_t>(), nb);
+    } else {
+      rs_scatter<8><<<nb, RS_THREADS, smem, stream()>>>(
+          ka->as<uint64_t>(), va ? va->as<uint32_t>() : nullptr, kb->as<uint64_t>(),
+          vb ? vb->as<uint32_t>() : nullptr, n, shift, mask, counts.as<uint32_t>(), nb);
+    }
     NX_LAUNCH_CHECK();
     std::swap(ka, kb);
     std::swap(va, vb);
+    shift += width;
   }
-  if (passes & 1) {  // the result sits in the scratch buffers: hand them to the caller
+  if (npass & 1) {  // the result sits in the scratch buffers: hand them to the caller
     std::swap(keys, k2);
     if (vals) std::swap(*vals, v2);
   }
