@@ -66,6 +66,8 @@ def _load():
         lib.orc_pr_iterate.argtypes = [vp, dbl, u32, vp, i32, vp, vp]
         lib.orc_pr_release.argtypes = [vp]
         lib.orc_pr_release.restype = None
+        lib.orc_set_threads.argtypes = [i32]
+        lib.orc_set_threads.restype = None
         lib.orc_wpr_adjoint.argtypes = [u32, u64, vp, vp, vp, dbl, u32, u32, vp, vp, vp, vp,
                                         vp, vp]
         for f in (lib.orc_pagerank, lib.orc_bfs, lib.orc_wcc, lib.orc_scc, lib.orc_wpr_adjoint,
@@ -76,9 +78,10 @@ def _load():
 
 
 def set_threads(k: int | None) -> None:
-    """Bound the OpenMP threads the oracle uses (None: library default)."""
+    """Bound the OpenMP threads the oracle uses from now on (None: no change)."""
     if k is not None:
         os.environ["OMP_NUM_THREADS"] = str(k)
+        _load().orc_set_threads(int(k))
 
 
 def _u32(a):

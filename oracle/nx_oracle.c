@@ -36,6 +36,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_INF 0xFFFFFFFFu
 
@@ -432,4 +435,14 @@ int orc_wpr_adjoint(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t*
   free(y);
   csr_free(&out);
   return 0;
+}
+
+/* Threads of the parallel loops from now on (k >= 1); the results do not
+ * depend on it: every vertex's sum is taken by one thread in edge order. */
+void orc_set_threads(int k) {
+#ifdef _OPENMP
+  if (k >= 1) omp_set_num_threads(k);
+#else
+  (void)k;
+#endif
 }
