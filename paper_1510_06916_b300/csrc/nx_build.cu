@@ -387,7 +387,17 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   // upload of host edges); NX_RELABEL orders the vertices by them and then
   // permutes them to the new ids (a renamed vertex keeps its degrees).
   const bool early_deg = true;
-  DevBuf indeg, bad;
+  DevBuf indeg, bad, od_new;
+  // The value and contribution arrays every run gathers from, and the
+  // out-degrees in new ids, are allocated before the build's temporaries
+  // (about 40 GB at R-MAT scale 26) pass through the device pool: carved out
+  // of the memory those leave behind, the same arrays made the scale-26
+  // PageRank sweep 1.5% slower (6.37 vs 6.28 ms, measured on one GPU).
+  for (int k = 0; k < 2; ++k) {
+    NX_TRY(g->val[k].alloc((uint64_t)n * 4));
+    NX_TRY(g->aux[k].alloc((uint64_t)n * 4));
+  }
+  if (flags & NX_RELABEL) NX_TRY(od_new.alloc((uint64_t)n * 4));
   NX_TRY(g->outdeg.alloc((uint64_t)n * 4));
   NX_TRY(indeg.alloc((uint64_t)n * 4));
   NX_TRY(bad.alloc(4));
@@ -471,8 +481,7 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   }
   if (flags & NX_RELABEL) {
     {  // degrees of the renamed ids: new vertex k is caller vertex old_of_new[k]
-      DevBuf od2, id2;
-      NX_TRY(od2.alloc((uint64_t)n * 4));
+      DevBuf od2 = std::move(od_new), id2;
       NX_TRY(id2.alloc((uint64_t)n * 4));
       NX_TRY(gather_u32(g->old_of_new.as<uint32_t>(), g->outdeg.p, od2.p, n));
       NX_TRY(gather_u32(g->old_of_new.as<uint32_t>(), indeg.p, id2.p, n));
