@@ -833,10 +833,11 @@ def _ragged_graph():
     return n, s[keep], d[keep]
 
 
+@pytest.mark.parametrize("transpose", [True, False])  # False: new ids applied while making keys
 @pytest.mark.parametrize("P", [1, 4, 7])
-def test_relabel_order_and_layout(P):
+def test_relabel_order_and_layout(P, transpose):
     n, s, d = _ragged_graph()
-    g = nx.Graph(s, d, n, P, transpose=True, relabel=True)
+    g = nx.Graph(s, d, n, P, transpose=transpose, relabel=True)
     old_of_new = g.relabel_map()
     assert (np.sort(old_of_new) == np.arange(n)).all()  # a permutation
     od = np.bincount(s, minlength=n)[old_of_new]
@@ -850,9 +851,29 @@ def test_relabel_order_and_layout(P):
     gs, gd, goff = g.export()
     assert (goff == off).all()
     assert (gs == ns[order]).all() and (gd == nd[order]).all()
-    order_t, _ = oracle.dsss_order(n, P, nd, ns)
-    ts, td, _ = g.export(transpose=True)
-    assert (ts == ns[order_t]).all() and (td == nd[order_t]).all()
+    if transpose:
+        order_t, _ = oracle.dsss_order(n, P, nd, ns)
+        ts, td, _ = g.export(transpose=True)
+        assert (ts == ns[order_t]).all() and (td == nd[order_t]).all()
+    g.run("pr", 20)
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"relabel P={P} PR")
+
+
+def test_trim_memory_keeps_graphs_and_later_builds_correct():
+    n = 1 << 14
+    s, d, _ = rmat(14, 16, 9)
+    g = nx.Graph(s, d, n, 8, relabel=True)
+    g.run("pr", 10)
+    ref = oracle.pagerank(n, s, d, 0.85, 10)
+    assert_pr_close(g.values(), ref, "before trim")
+    nx.trim_memory()  # cached blocks back to the driver; the live graph keeps its own
+    g.run("pr", 10)
+    assert_pr_close(g.values(), ref, "after trim")
+    g.free()
+    nx.trim_memory()
+    g2 = nx.Graph(s, d, n, 8, relabel=True)
+    g2.run("pr", 10)
+    assert_pr_close(g2.values(), ref, "new graph after trim")
 
 
 @pytest.mark.parametrize("P", [3, 16])

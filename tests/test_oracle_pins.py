@@ -122,6 +122,21 @@ def test_prepared_problem_is_the_same_arithmetic(weighted):
     pp.close()
 
 
+def test_thread_count_does_not_change_the_oracle():
+    # every vertex's sum is taken by one thread in edge order, so one thread
+    # and all of them give the same bits (the CPU baseline times both)
+    s, d, _ = inputs.rmat_edges(12, 16 << 12, 11)
+    n = 1 << 12
+    pp = oracle.PreparedPageRank(n, s, d)
+    oracle.set_threads(1)
+    try:
+        one = pp.iterate(ALPHA, 5)
+    finally:
+        oracle.set_threads(os.cpu_count() or 1)
+    assert (pp.iterate(ALPHA, 5) == one).all()
+    pp.close()
+
+
 def test_pagerank_dangling_term_matters():
     # A plausible mistake (dropping the dangling mass) breaks the sum-to-one pin:
     # a 2-vertex path 0 -> 1 with 1 dangling.
