@@ -105,11 +105,10 @@ typedef struct {
   const float* teleport;  /* PPR/WPR teleport vector [n], or NULL = uniform 1/n */
   int32_t teleport_is_device;
   int32_t use_graph;      /* reserved, set to 0                                  */
-  uint32_t band_intervals;/* SPU: source intervals per launch (0 = automatic: one
-                             launch, or, when the gathered value array exceeds
-                             128 MB and P >= 32, bands whose values fit in 128
-                             MB); accumulators carry between bands in device
-                             memory                                              */
+  uint32_t band_intervals;/* SPU: source intervals per launch (0 = all P in one
+                             launch); with fewer, the sweep runs one launch per
+                             band of source intervals and the accumulators carry
+                             between bands in device memory                     */
 } nx_params;
 
 typedef struct {

@@ -1069,17 +1069,15 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     NX_TRY(move_to_device(const_cast<Dsss*>(d)->h_piece_pin, const_cast<Dsss*>(d)->piece_off));
     NX_TRY(move_to_device(const_cast<Dsss*>(d)->h_hub_off, const_cast<Dsss*>(d)->hub_off));
   }
-  // SPU bands: launches over groups of source intervals whose gathered values
-  // fit in L2 together (the value array of the whole graph may not)
+  // SPU bands (on request): launches over groups of source intervals, the
+  // tile accumulators carried between them. One launch over all sources is
+  // the default: at R-MAT scale 26 (268 MB of values, beyond L2) it beat two
+  // 128 MB bands by 7.4% with degree-ordered ids (5.82 vs 6.28 ms per sweep at
+  // P = 64, 5.70 vs 6.15 at P = 32) and by 2.4% with the generator's ids: the
+  // most-read values stay in L2 either way, and a band pays for the carried
+  // accumulators and a second pass over every tile.
   uint32_t band = P;
-  if (strat == NX_SPU && !streaming) {
-    // Measured at R-MAT scale 26 (268 MB of values): two bands gain 2-3% at P = 32 and 64
-    // (short pieces), and lose 2-10% at P = 16 and 8; smaller bands lose at every P.
-    const uint64_t kBandBytes = 128ull << 20;  // about the L2
-    if (p.band_intervals) band = std::min<uint32_t>(p.band_intervals, P);
-    else if ((uint64_t)n * 4 > kBandBytes && P >= 32)
-      band = (uint32_t)std::max<uint64_t>(1, kBandBytes / ((uint64_t)L * 4));
-  }
+  if (strat == NX_SPU && !streaming && p.band_intervals) band = std::min<uint32_t>(p.band_intervals, P);
   const uint32_t nbands = (uint32_t)ceil_div(P, band);
 
   // plan (cached: the graph never changes)
@@ -1284,37 +1282,21 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
 // Times the PageRank sweep's loads and gathers alone (PK_PROBE) with the
 // launches an SPU PageRank run would make: the same plan (bands included).
 nx_status probe_impl(nx_graph* g, uint32_t sweeps, float* ms_per_sweep) {
-  const uint32_t n = g->geo.n, P = g->geo.P, L = g->geo.L;
+  const uint32_t n = g->geo.n, P = g->geo.P;
   NX_TRY(ensure_resident(g));
   NX_TRY(prepare(g));
   NX_TRY(ensure(g->aux[0], (size_t)n * 4));
   NX_TRY(ensure(g->aux[1], (size_t)n * 4));
-  uint32_t band = P;
-  const uint64_t kBandBytes = 128ull << 20;  // the rule of the SPU run
-  if ((uint64_t)n * 4 > kBandBytes && P >= 32)
-    band = (uint32_t)std::max<uint64_t>(1, kBandBytes / ((uint64_t)L * 4));
-  const uint32_t nbands = (uint32_t)ceil_div(P, band);
-  const int key = (((int)NX_SPU * 16 + 1) * 4096) * 2048 + (int)(nbands > 1 ? band : 0);
+  // one launch over all sources, as the SPU run's default
+  const int key = (((int)NX_SPU * 16 + 1) * 4096) * 2048;
   auto& slot = g->plans[key];
   if (!slot) {
     slot.reset(new nx_graph::Plan());
     PlanOut plan;
     std::vector<const Dsss*> ds{&g->fwd};
-    std::vector<uint32_t> off;
-    const uint64_t blk = target_block_edges(g->m);
-    if (nbands == 1) {
-      plan_tiles(g, ds, 0, P, 0, P, true, blk, plan);
-    } else {
-      for (uint32_t i0 = 0; i0 < P; i0 += band) {
-        off.push_back((uint32_t)plan.items.size());
-        plan_tiles(g, ds, i0, std::min(P, i0 + band), 0, P, true,
-                   std::max<uint64_t>(blk / nbands, 4096), plan);
-      }
-      off.push_back((uint32_t)plan.items.size());
-    }
+    plan_tiles(g, ds, 0, P, 0, P, true, target_block_edges(g->m), plan);
     NX_TRY(upload_items(g, plan, *slot));
     slot->na = (uint32_t)slot->h_items.size();
-    slot->off = off;
   }
   NX_TRY(ensure_split(g, slot->slots));
   nx_params p{};
@@ -1327,19 +1309,7 @@ nx_status probe_impl(nx_graph* g, uint32_t sweeps, float* ms_per_sweep) {
   EventPair ev;
   NX_TRY(ev.create());
   NX_CUDA(cudaEventRecord(ev.e0, stream()));
-  for (uint32_t q = 0; q < sweeps; ++q) {
-    if (nbands == 1) {
-      NX_TRY(launch_sweep(PK_PROBE, a, slot->na, stream()));
-    } else {
-      for (uint32_t b = 0; b < nbands; ++b) {
-        SweepArgs ab = a;
-        ab.items = a.items + slot->off[b];
-        ab.src_lo = b * band;
-        ab.src_hi = std::min(P, (b + 1) * band);
-        NX_TRY(launch_sweep(PK_PROBE, ab, slot->off[b + 1] - slot->off[b], stream()));
-      }
-    }
-  }
+  for (uint32_t q = 0; q < sweeps; ++q) NX_TRY(launch_sweep(PK_PROBE, a, slot->na, stream()));
   NX_CUDA(cudaEventRecord(ev.e1, stream()));
   float ms = 0.f;
   NX_TRY(ev.elapsed(&ms));

@@ -859,6 +859,19 @@ def test_relabel_order_and_layout(P, transpose):
     assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"relabel P={P} PR")
 
 
+def test_gather_probe_times_and_leaves_the_run_alone():
+    n = 1 << 15
+    s, d, _ = rmat(15, 16, 13)
+    g = nx.Graph(s, d, n, 8, relabel=True)
+    g.run("pr", 10)
+    r = g.values().copy()
+    ms = g.gather_probe(sweeps=3)
+    assert ms > 0.0
+    assert (g.values() == r).all()  # the probe writes nothing the run owns
+    g.run("pr", 10)
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 10), "PR after the probe")
+
+
 def test_trim_memory_keeps_graphs_and_later_builds_correct():
     n = 1 << 14
     s, d, _ = rmat(14, 16, 9)
