@@ -307,8 +307,16 @@ nx_status build_geometry(nx_graph* g, const uint32_t* deg_a, const uint32_t* deg
                          uint64_t m_bal, uint32_t edges_log2, DevBuf& tile_of) {
   Geometry& geo = g->geo;
   const uint32_t n = geo.n;
+  // E_tile: about m / (8 x SMs), within [2^14, 2^20]. The vertex cap bounds
+  // most tiles; E_tile cuts the heavy ones (and gives small graphs enough
+  // tiles), and the planner splits what is still heavy over several blocks.
+  // The upper bound was 2^16: lifting it made the R-MAT scale-26 PageRank
+  // sweep (P = 64, E_tile 2^20) 4% faster (5.58 vs 5.81 ms) and DPU sweeps
+  // 15-30% faster at scales 22-24; the staged MPU columns want smaller tiles
+  // (scale 22, P = 16, Q = 8: 15.5 / 16.2 / 20.1 ms at 2^16 / 2^17 / 2^18),
+  // which m / (8 x SMs) still gives there (2^17 with the transpose).
   uint64_t E = m_bal / ((uint64_t)num_sms() * 8);
-  E = std::max<uint64_t>(16384, std::min<uint64_t>(E, 65536));
+  E = std::max<uint64_t>(16384, std::min<uint64_t>(E, 1ull << 20));
   if (edges_log2) E = 1ull << edges_log2;
   DevBuf pre, flag;
   NX_TRY(pre.alloc((uint64_t)n * sizeof(uint64_t)));
