@@ -125,7 +125,8 @@ def test_256_graphs_one_launch():
     for gi, sc in enumerate(scales):
         n = 1 << sc
         s, d, _ = inputs.rmat_edges(sc, 16 << sc, inputs.multigraph_seed(gi))
-        graphs.append(nx.Graph(s, d, n, max(1, min(16, n >> 12)), transpose=True))
+        # the tile shape the benchmark's persistent launch uses (E_tile = 2^16)
+        graphs.append(nx.Graph(s, d, n, max(1, min(16, n >> 12)), transpose=True, tile_edges_log2=16))
         data.append((n, s, d))
     nx.run_multi(graphs, "pr", 20)
     worst_l1 = worst_rel = 0.0

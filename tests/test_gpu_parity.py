@@ -596,13 +596,14 @@ def test_autograd_function():
 
 # ------------------------------------------------------------------ many graphs
 
-def test_run_multi_uneven_graphs():
+@pytest.mark.parametrize("edges_log2", [0, 16])  # the default tile shape and the batching one
+def test_run_multi_uneven_graphs(edges_log2):
     scales = inputs.multigraph_scales(12, lo=6, hi=12)
     graphs, edges = [], []
     for gi, sc in enumerate(scales):
         n = 1 << sc
         s, d, _ = inputs.rmat_edges(sc, 16 << sc, inputs.multigraph_seed(gi))
-        graphs.append(nx.Graph(s, d, n, 1 + gi % 5, transpose=True))
+        graphs.append(nx.Graph(s, d, n, 1 + gi % 5, transpose=True, tile_edges_log2=edges_log2))
         edges.append((n, s, d))
     st = nx.run_multi(graphs, "pr", 20)
     assert st["iters_done"] == 20 and st["launches"] == 1
