@@ -684,8 +684,19 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
   if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
+// Blocks per SM the register budget is set for: five (48 registers) where the
+// program fits without spilling -- PageRank's sweep ran 4.3% faster at R-MAT
+// scale 26 (5.38 vs 5.62 ms) and BFS / WCC 1-3% faster with the fifth block's
+// gathers in flight -- and four (64 registers) for the programs that carry a
+// weight or a second gathered value per edge (weighted PageRank, the adjoint,
+// the r/outdeg gather), which spilled and ran 17-19% slower at five.
 template <int K>
-__global__ void __launch_bounds__(kThreads) k_sweep(const __grid_constant__ SweepArgs a) {
+constexpr int sweep_min_blocks() {
+  return (K == PK_WPR || K == PK_ADJ || K == PK_PRD) ? 4 : 5;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads, sweep_min_blocks<K>()) k_sweep(const __grid_constant__ SweepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Item it;
   if (a.items) {
