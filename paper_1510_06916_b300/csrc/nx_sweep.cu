@@ -754,8 +754,13 @@ __device__ __forceinline__ bool grid_barrier(MultiSync* sy, unsigned nblocks, lo
   return s_ok != 0;
 }
 
+// The persistent kernel's register budget is set for five blocks per SM
+// (48 registers; the programs spill a little there, but the extra warps win:
+// 256 R-MAT graphs, PageRank x20 16.9 vs 19.7 ms at three blocks, BFS / WCC
+// x40 9.0 / 17.1 vs 12.2 / 22.7 ms; six blocks lost on PageRank), and for
+// three for weighted PageRank, which spills badly below 80 registers.
 template <int K>
-__global__ void __launch_bounds__(kThreads) k_multi(const SweepArgs* __restrict__ args,
+__global__ void __launch_bounds__(kThreads, K == PK_WPR ? 3 : 5) k_multi(const SweepArgs* __restrict__ args,
                                                     const MItem* __restrict__ items,
                                                     uint32_t nitems, uint32_t iters,
                                                     uint32_t* __restrict__ ctr, MultiSync* sy,
