@@ -863,7 +863,7 @@ const void* sweep_fn(ProgKind kind) {
 // Function attributes of a sweep kernel for `smem` bytes of dynamic shared
 // memory: the opt-in limit when dynamic + static shared memory pass the 48 KB
 // default (per device), and the smallest shared-memory carveout that still
-// holds the blocks an SM can run (registers limit them to four), so the rest
+// holds the blocks an SM can run (the registers allow four or five), so the rest
 // of the unified L1 caches the random source gathers. The driver's own choice
 // reserved more: PageRank ran 0-6% slower with it (R-MAT scales 22-26,
 // P = 8-64).
