@@ -182,14 +182,20 @@ struct EdgeRegs {
   float4 f[N / 4];
 };
 
+// Edge words of a step; prefetched one step ahead. The weights of weighted
+// programs are loaded when their step is processed (not prefetched): without
+// the second set of weight registers the weighted sweeps fit five blocks per
+// SM, 2-3% faster than four blocks with prefetched weights.
 template <class PG>
 __device__ __forceinline__ void load_step(EdgeRegs<kEPL>& r, const uint32_t* __restrict__ ew,
                                           const float* __restrict__ wt, uint64_t idx) {
 #pragma unroll
-  for (int k = 0; k < kEPL / 4; ++k) {
-    r.q[k] = ld_stream(ew + idx + 4 * k);
-    if (PG::weighted) r.f[k] = ld_stream_f(wt + idx + 4 * k);
-  }
+  for (int k = 0; k < kEPL / 4; ++k) r.q[k] = ld_stream(ew + idx + 4 * k);
+}
+__device__ __forceinline__ void load_weights(EdgeRegs<kEPL>& r, const float* __restrict__ wt,
+                                             uint64_t idx) {
+#pragma unroll
+  for (int k = 0; k < kEPL / 4; ++k) r.f[k] = ld_stream_f(wt + idx + 4 * k);
 }
 
 // One warp step: the kStep edge words in `cur` start at edge index `base`;
@@ -306,7 +312,11 @@ __device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
     if (p < b) load_step<PG>(nxt, ew, wt, p - ew_lo);
   }
   while (base < b) {
-    const EdgeRegs<kEPL> cur = nxt;
+    EdgeRegs<kEPL> cur = nxt;
+    if (PG::weighted) {
+      const uint64_t p = base + (uint64_t)lane * kEPL;
+      if (p < b) load_weights(cur, wt, p - ew_lo);
+    }
     const uint64_t nbase = base + (uint64_t)kWarps * kStep;
     {  // prefetch the warp's next step
       const uint64_t pn = nbase + (uint64_t)lane * kEPL;
@@ -418,9 +428,14 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, const Item& it, u
     if (e < ep.b) load_step<PG>(nxt, a.src[sx].ew, a.src[sx].wt, e - a.ew_lo[sx]);
   }
   while (q < stot) {
-    const EdgeRegs<kEPL> cur = nxt;
+    EdgeRegs<kEPL> cur = nxt;
     const FlatEnt ec = ep;
     const uint64_t bc = base;
+    if (PG::weighted) {
+      const uint32_t sxc = (ec.cum >> 24) & 1u;
+      const uint64_t e = bc + (uint64_t)lane * kEPL;
+      if (e < ec.b) load_weights(cur, a.src[sxc].wt, e - a.ew_lo[sxc]);
+    }
     const uint32_t qn = q + kWarps;
     if (qn < stot) {  // prefetch the warp's next step, possibly in a later piece
       while ((tab[p + 1].cum & kCum) <= qn) ++p;
@@ -684,15 +699,14 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, Item it, unsigned
   if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
-// Blocks per SM the register budget is set for: five (48 registers) where the
-// program fits without spilling -- PageRank's sweep ran 4.3% faster at R-MAT
-// scale 26 (5.38 vs 5.62 ms) and BFS / WCC 1-3% faster with the fifth block's
-// gathers in flight -- and four (64 registers) for the programs that carry a
-// weight or a second gathered value per edge (weighted PageRank, the adjoint,
-// the r/outdeg gather), which spilled and ran 17-19% slower at five.
+// Blocks per SM the register budget is set for: five (48 registers) --
+// PageRank's sweep ran 4.3% faster at R-MAT scale 26 (5.38 vs 5.62 ms), BFS /
+// WCC 1-3% faster and the weighted programs 2-3% faster with the fifth
+// block's gathers in flight -- and four (64 registers) for the r/outdeg
+// gather, which carries a second gathered value per edge.
 template <int K>
 constexpr int sweep_min_blocks() {
-  return (K == PK_WPR || K == PK_ADJ || K == PK_PRD) ? 4 : 5;
+  return K == PK_PRD ? 4 : 5;
 }
 
 template <int K>
