@@ -294,7 +294,6 @@ __device__ __forceinline__ void sweep_range(const uint32_t* __restrict__ ew,
                                             const uint32_t* __restrict__ od) {
   using V = typename PG::V;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t smask = (1u << lb) - 1u;
   const uint64_t a0 = a & ~(uint64_t)(kEPL - 1);
   const uint32_t nsteps = (uint32_t)((b - a0 + kStep - 1) / kStep);
   const uint32_t k0 = (uint32_t)((warp - (int)rot) & (kWarps - 1));
