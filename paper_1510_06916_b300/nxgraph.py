@@ -368,7 +368,8 @@ def autotune(src, dst, n, candidates=(8, 16, 32, 64), program="pr", iters=10, ca
     return int(best.value), ms.tolist()
 
 
-def autotune_shape(src, dst, n, shapes, program="pr", iters=10, cache=None, transpose=False):
+def autotune_shape(src, dst, n, shapes, program="pr", iters=10, cache=None, transpose=False,
+                   relabel=False):
     """Fastest of `shapes` [(P, tile_cap_log2, tile_edges_log2), ...] (0 = default).
     Returns (index, ms_per_iter list); ms are -1 when served from the cache."""
     if isinstance(src, np.ndarray):
@@ -379,7 +380,7 @@ def autotune_shape(src, dst, n, shapes, program="pr", iters=10, cache=None, tran
     cand = (NxShape * len(shapes))(*[NxShape(int(p), int(c), int(e), 0) for p, c, e in shapes])
     ms = np.empty(len(shapes), dtype=np.float32)
     best = ctypes.c_uint32()
-    flags = (DEV_PTRS if sd else HOST_PTRS) | (WITH_TRANSPOSE if transpose else 0)
+    flags = (DEV_PTRS if sd else HOST_PTRS) | (WITH_TRANSPOSE if transpose else 0) | (RELABEL if relabel else 0)
     check(lib().nx_autotune_shape(sp, dp, len(src), n, flags, None,
                                   PROGRAMS.get(program, program), cand, len(shapes), iters,
                                   ctypes.byref(best), ms.ctypes.data,
