@@ -572,9 +572,8 @@ def measure_sweep(nx, inputs, torch, w, steps, warmup, world=1, local=0, clocks=
     torch.cuda.empty_cache()
     # Roofline of the sweep kernel: algorithmic bytes of one sweep (one
     # PageRank iteration), 4m (source offsets) + 4D (destination ids) + 12n
-    # (read c, write r, read outdeg), over the sweep's kernel time. A sweep is
-    # one launch, or one launch per band of source intervals when the value
-    # array exceeds 128 MB and P >= 32 (the bands share the sweep's bytes).
+    # (read c, write r, read outdeg), over the sweep's kernel time (one launch
+    # per sweep).
     sweeps = steps * iters
     D = info["D"]
     alg = 4 * m + 4 * D + 12 * n
