@@ -174,21 +174,25 @@ def oracle_cores():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
-def cpu_oracle_sample(w, prepared, target_s=10.0, max_iters=20):
-    """Times the oracle's PageRank iteration loop alone on the full graph:
-    one iteration first, then enough more for about `target_s` seconds."""
-    m = w["ef"] << w["scale"]
+def cpu_oracle_step(w, prepared):
+    """Times the oracle's iteration loop alone on the full graph for one step
+    of the workload (its PageRank iterations from r = 1/n); returns GTEPS, the
+    threads used, the seconds and the FP64 ranks."""
+    m, iters = w["ef"] << w["scale"], w["iters"]
     t0 = time.perf_counter()
-    prepared.iterate(0.85, 1)
-    dt1 = time.perf_counter() - t0
-    k = int(max(0, min(max_iters - 1, target_s / max(dt1, 1e-3) - 1)))
-    dtk = 0.0
-    if k:
-        t0 = time.perf_counter()
-        prepared.iterate(0.85, k)
-        dtk = time.perf_counter() - t0
-    iters, dt = 1 + k, dt1 + dtk
-    return m * iters / dt / 1e9, oracle_cores(), dt, iters
+    ref = prepared.iterate(0.85, iters)
+    dt = time.perf_counter() - t0
+    return m * iters / dt / 1e9, oracle_cores(), dt, ref
+
+
+def pr_parity(gpu, ref):
+    """L1 over the vector and the largest per-vertex relative error (vertices
+    with a non-zero reference) of FP32 ranks against the FP64 oracle."""
+    import numpy as np
+    d = np.abs(gpu.astype(np.float64) - ref)
+    nz = ref != 0
+    return {"l1": float(d.sum()), "max_rel": float((d[nz] / np.abs(ref[nz])).max()) if nz.any() else 0.0,
+            "tolerance": {"l1": 1e-6, "max_rel": 1e-4}}
 
 
 def cpu_oracle_single_thread(w, prepared, cores):
@@ -564,6 +568,7 @@ def measure_sweep(nx, inputs, torch, w, steps, warmup, world=1, local=0, clocks=
     clock_rec = clk.stop() if clk else None
     ms = ev0.elapsed_time(ev1)
     ms_max = barrier_max(ms, world)
+    ranks = g.values()  # the last timed run's ranks (caller ids), for the parity check
     # the sweep's loads and gathers alone (no reduction): the practical
     # ceiling of a sweep that gathers one 4-byte value per edge
     g.gather_probe(3)
@@ -586,6 +591,7 @@ def measure_sweep(nx, inputs, torch, w, steps, warmup, world=1, local=0, clocks=
                "ceiling_frac_of_peak": alg / (probe_ms / 1e3) / 1e9 / peak,
                "sweep_over_ceiling": probe_ms / (t_sweep * 1e3)}
     return {
+        "ranks": ranks,
         "gather_ceiling": ceiling,
         "value": aggregate_gteps(m, iters, steps, world, ms_max), "ms_max": ms_max,
         "ms_per_step": ms_max / steps, "launches": launches, "clocks": clock_rec,
@@ -740,21 +746,25 @@ def main():
         torch.cuda.empty_cache()
 
     cpu = None
+    parity = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
             prepared = prepare_oracle(w, host_edges)
-            v, cores, dt, k = cpu_oracle_sample(w, prepared)
+            v, cores, dt, ref = cpu_oracle_step(w, prepared)
+            parity = pr_parity(head["ranks"], ref)
+            del ref
             v1, dt1 = cpu_oracle_single_thread(w, prepared, cores)
             prepared.close()
             cpu = {"value": v, "unit": "GTEPS", "cores": cores, "kind": "oracle",
-                   "sample": f"{k} PageRank iteration(s) of the full graph, iteration loop only "
-                             f"(CSR built before the clock), {dt:.1f} s",
+                   "sample": f"one step of the workload ({w['iters']} PageRank iterations of the full "
+                             f"graph), iteration loop only (CSR built before the clock), {dt:.1f} s",
                    "single_thread": {"value": v1, "unit": "GTEPS", "cores": 1,
                                      "sample": f"1 PageRank iteration of the full graph, {dt1:.1f} s"}}
         except Exception as e:  # pragma: no cover
             cpu = {"value": None, "unit": "GTEPS", "cores": None, "kind": "oracle",
                    "sample": f"failed: {e}"}
     host_edges = None
+    head.pop("ranks", None)
 
     extras = None
     if not args.no_extras:
@@ -778,6 +788,7 @@ def main():
             "graph": head["graph"],
             "roofline": roof,
             "cpu_baseline": cpu,
+            "parity": parity,
             "e2e": e2e,
             "gpu_launches": head["launches"],
             "clocks": head["clocks"],
