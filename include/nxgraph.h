@@ -67,7 +67,9 @@ typedef enum {
                   combines them per destination interval                           */
   NX_MPU = 2,  /* Algorithm 7: Q intervals resident from the budget; the (P-Q)^2
                   sub-shards among the others go through hubs                      */
-  NX_AUTO = 3, /* SPU when the budget holds all intervals, else MPU              */
+  NX_AUTO = 3, /* the fastest the graph and budget allow: NX_DPU_ONCHIP for PR /
+                  PPR on a graph built with NX_ONCHIP_HUBS and no budget, else
+                  SPU when the budget holds all intervals, else MPU             */
   /* Exp 1 / Table IV ablation (PR and PPR only; needs NX_WITH_TRANSPOSE; budget
      0): the same sub-shards read in source order from the transpose DSSS, each
      edge pushing its contribution to the destination with an atomic add.      */

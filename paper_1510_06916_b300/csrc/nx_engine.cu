@@ -839,7 +839,13 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   if (push && !g->has_tr)
     return invalid("nx_run: the source-sorted ablation reads the transpose DSSS (NX_WITH_TRANSPOSE)");
   if (push && budget) return invalid("nx_run: the source-sorted ablation takes no budget");
-  const bool onchip = (strategy == NX_DPU_ONCHIP);
+  // NX_AUTO picks the fastest strategy the graph and the budget allow (the
+  // paper's adaptive choice, Section III-B3): for PageRank on a graph built
+  // with NX_ONCHIP_HUBS and no budget, the on-chip double-phase update (1.4x
+  // the SPU sweep at R-MAT scale 26); otherwise SPU when the budget holds
+  // every interval, else MPU (below).
+  const bool onchip = (strategy == NX_DPU_ONCHIP) ||
+                      (strategy == NX_AUTO && !budget && g->oc.built && (prog == NX_PR || prog == NX_PPR));
   if (onchip && prog != NX_PR && prog != NX_PPR)
     return invalid("nx_run: NX_DPU_ONCHIP runs PR and PPR only");
   if (onchip && !g->oc.built)
@@ -938,7 +944,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       memset(st, 0, sizeof *st);
       st->iters_done = iters;
       st->Q = P;
-      st->strategy = (uint32_t)strategy;
+      st->strategy = (uint32_t)NX_DPU_ONCHIP;
       st->ms = ms;
       st->edges_swept = g->m * iters;
       // 16-bit edge entries, hub values written and read, hub offsets, staged c, outdeg, r, c

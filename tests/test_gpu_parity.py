@@ -119,6 +119,16 @@ def test_dpu_onchip_matches_oracle(scale, ef, seed, P):
     g.run("ppr", 15, "dpu_onchip", teleport=t)
     ref = oracle.personalized_pagerank(n, s, d, t, 0.85, 15)
     assert_pr_close(g.values(), ref, f"onchip PPR scale {scale}")
+    # AUTO takes the on-chip update for PageRank on this graph, and SPU on the
+    # same graph under a budget or for BFS
+    st = g.run("pr", 20, "auto")
+    assert st["strategy"] == nx.DPU_ONCHIP
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"onchip AUTO PR scale {scale}")
+    st = g.run("pr", 20, "auto", budget=1 << 40)
+    assert st["strategy"] == nx.SPU
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 20), f"AUTO with a budget, scale {scale}")
+    st = g.run("bfs", 1000, "auto")
+    assert st["strategy"] == nx.SPU
     g.free()
 
 
