@@ -95,7 +95,8 @@ typedef enum {
 /* Tile shape (below the interval level; nx_autotune_shape searches it):
  * destination tiles of at most 2^k vertices (8 <= k <= 13; default 2^11), and
  * a tile also ends where its in-edges pass a multiple of 2^e (10 <= e <= 20;
- * default m / (8 x SMs) clamped to [2^14, 2^16]). 0 = the default.          */
+ * default m / (8 x SMs) clamped to [2^14, 2^20], m doubled with the
+ * transpose). 0 = the default.                                               */
 #define NX_TILE_CAP_LOG2(k) ((uint32_t)(k) << 8)
 #define NX_TILE_EDGES_LOG2(e) ((uint32_t)(e) << 12)
 
@@ -307,7 +308,9 @@ nx_status nx_adjoint_wpr(nx_graph* g, const float* grad_r, uint32_t adj_terms, f
  * Runs `program` on `count` independent graphs in one persistent kernel per
  * call (blocks pull (graph, tile) work items from a counter and meet at a
  * grid barrier after every iteration), the whole iteration loop captured in a
- * CUDA graph. The executable graph is kept (a few per process) and replayed
+ * CUDA graph. The launch has parallelism across graphs, so graphs built for it
+ * with larger tiles (NX_TILE_EDGES_LOG2(16)) run faster here (256 R-MAT graphs
+ * of scales 10..18: 1.6x) and slower when swept alone. The executable graph is kept (a few per process) and replayed
  * by a later call with the same graphs, program, iteration count, damping and
  * barrier limit whose graphs have not reallocated any buffer since
  * (stats->Q is then 1, else 0); nx_graph_free of a member drops it. Each
