@@ -313,8 +313,9 @@ nx_status nx_adjoint_wpr(nx_graph* g, const float* grad_r, uint32_t adj_terms, f
  * of scales 10..18: 1.4x) and slower when swept alone. The executable graph
  * is kept (a few per process) and replayed by a later call with the same
  * graphs, program, iteration count, damping and barrier limit whose graphs
- * have not reallocated any buffer since (stats->Q is then 1, else 0); nx_graph_free of a member drops it. Each
- * graph keeps its own values (read them with nx_get_values). BFS uses root 0.
+ * have not reallocated any buffer since (stats->Q is then 1, else 0);
+ * nx_graph_free of a member drops it. Each graph keeps its own values (read
+ * them with nx_get_values). BFS uses root 0.
  * Errors: INVALID_ARG (NULL or repeated graphs, PPR, WCC on a graph without
  * transpose, WPR without weights, a graph built with NX_RELABEL), TIMEOUT (a
  * grid barrier waited longer than its limit, see nx_set_barrier_limit; the
