@@ -477,6 +477,37 @@ def measure_autotune(nx, inputs, torch, scale=22, seed=2):
     return out
 
 
+def measure_rmat26_programs(nx, inputs, torch, budget=6 * 10**9):
+    """The scale-26 configuration's other runs: BFS from vertex 0 and WCC under
+    SPU in HBM, and PageRank x10 / BFS / WCC under MPU with a 6 GB device
+    budget (the edge words beyond it stream from pinned host memory)."""
+    w = WORKLOADS["rmat26"]
+    n, m = 1 << w["scale"], w["ef"] << w["scale"]
+    src, dst, _ = inputs.rmat_edges_device(w["scale"], m, w["seed"])
+    g = nx.Graph(src, dst, n, w["P"], transpose=True, relabel=True)
+    del src, dst
+    torch.cuda.empty_cache()
+    out = {"workload": workload_name(w, "rmat26") + ", with transpose", "budget_bytes": budget}
+
+    def rec(st):
+        return {"ms": st["ms"], "sweeps": st["iters_done"], "edges_swept": st["edges_swept"],
+                "gteps_swept": st["edges_swept"] / (st["ms"] / 1e3) / 1e9 if st["ms"] else None,
+                "host_to_device_bytes": st["h2d_bytes"], "streamed_cols": st["streamed_cols"]}
+
+    for prog, it in (("bfs", 1000), ("wcc", 1000)):
+        g.run(prog, it, "spu")
+        out[f"spu_{prog}"] = rec(g.run(prog, it, "spu"))
+    for prog, it in (("pr", w["iters"]), ("bfs", 1000), ("wcc", 1000)):
+        g.run(prog, it, "mpu", budget=budget)
+        out[f"mpu6gb_{prog}"] = rec(g.run(prog, it, "mpu", budget=budget))
+        out[f"mpu6gb_{prog}"]["device_bytes"] = g.info()["device_bytes"]
+    g.free()
+    torch.cuda.empty_cache()
+    for k in ("spu_bfs", "spu_wcc", "mpu6gb_pr", "mpu6gb_bfs", "mpu6gb_wcc"):
+        out[k + "_ms"] = out[k]["ms"]
+    return out
+
+
 def measure_onchip(nx, inputs, torch, scale=26, ef=22, seed=5, P=64, iters=10, runs=5):
     """PageRank under NX_DPU_ONCHIP (Algorithm 6 with shared-memory intervals)
     on the scale-26 graph, beside the SPU sweep on the same graph."""
@@ -645,6 +676,7 @@ def compact(extras):
         "adjoint": ("adjoint_gteps", "forward_gteps", "adjoint_over_forward"),
         "multi_graph": ("gteps", "multi_ms", "separate_runs_kernel_ms"),
         "autotune": ("best_P", "best_tile_cap", "best_tile_edges", "scale26"),
+        "rmat26_programs": ("spu_bfs_ms", "spu_wcc_ms", "mpu6gb_pr_ms", "mpu6gb_bfs_ms", "mpu6gb_wcc_ms"),
         "strategies": ("spu_pr_ms", "dpu_pr_ms", "mpu_pr_ms", "dpu_over_spu_pr",
                        "src_coarse_over_spu_pr", "src_fine_over_spu_pr"),
         "relabel": ("relabel_over_ids",),
@@ -804,7 +836,8 @@ def main():
 EXTRAS = {"rmat22": measure_rmat22, "ppr_batch": measure_ppr_batch, "adjoint": measure_adjoint,
           "multi_graph": measure_multi, "autotune": measure_autotune,
           "strategies": measure_strategies, "budget_sweep": measure_budget_sweep,
-          "relabel": measure_relabel, "scc": measure_scc, "dpu_onchip": measure_onchip}
+          "relabel": measure_relabel, "scc": measure_scc, "dpu_onchip": measure_onchip,
+          "rmat26_programs": measure_rmat26_programs}
 
 
 if __name__ == "__main__":

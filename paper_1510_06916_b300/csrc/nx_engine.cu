@@ -149,9 +149,11 @@ void make_items(uint32_t t, uint64_t cost, bool allow_split, uint64_t blk, uint3
   if (k > 1) out.slots += k;
 }
 
-// Tiles of columns [c0, c1), sweeping sources [i0, i1) over `ds`.
+// Tiles of columns [c0, c1) (those in [tlo, thi) only), sweeping sources
+// [i0, i1) over `ds`.
 void plan_tiles(const nx_graph* g, const std::vector<const Dsss*>& ds, uint32_t i0, uint32_t i1,
-                uint32_t c0, uint32_t c1, bool allow_split, uint64_t blk, PlanOut& out) {
+                uint32_t c0, uint32_t c1, bool allow_split, uint64_t blk, PlanOut& out,
+                uint32_t tlo = 0, uint32_t thi = 0xFFFFFFFFu) {
   const auto& tb = g->geo.h_col_tb;
   const uint32_t P = g->geo.P, t0 = tb[c0], t1 = tb[c1];
   // edges per tile: pieces (i, t) of one column and source are consecutive
@@ -169,7 +171,7 @@ void plan_tiles(const nx_graph* g, const std::vector<const Dsss*>& ds, uint32_t 
   std::vector<Item> made;
   key.reserve(cost.size() + 64);
   made.reserve(cost.size() + 64);
-  for (uint32_t t = t0; t < t1; ++t)
+  for (uint32_t t = std::max(t0, tlo); t < std::min(t1, thi); ++t)
     make_items(t, cost[t - t0], allow_split, blk, 0, 0, key, made, out);
   emit_heaviest_first(key, made, out);
 }
@@ -508,11 +510,16 @@ constexpr uint64_t kStreamChunkWords = 16ull << 20;
 
 struct StreamBand {
   uint32_t j, i0, i1;     // column and its source intervals [i0, i1)
+  uint32_t t0, t1;        // its tiles [t0, t1) (the whole column unless a sub-shard is split)
   uint64_t e0[2], e1[2];  // word range of each DSSS (aligned, padded)
-  bool first, last;       // first / last band of the column
+  bool first, last;       // the band starts / ends the source range of its tiles
 };
 
-// Bands of the streamed columns [Jc, P) (deterministic: plans are cached).
+// Bands of the streamed columns [Jc, P) (deterministic: plans are cached):
+// consecutive source intervals of a column up to kStreamChunkWords words; a
+// single sub-shard above that is cut into ranges of its tiles (its pieces
+// (i, t) are consecutive), so the staging buffers stay about that size
+// however skewed the graph (degree-ordered ids put most edges in SS_00).
 std::vector<StreamBand> stream_bands(const nx_graph* g, const std::vector<const Dsss*>& ds,
                                      uint32_t Jc) {
   const uint32_t P = g->geo.P;
@@ -521,35 +528,49 @@ std::vector<StreamBand> stream_bands(const nx_graph* g, const std::vector<const 
   for (uint32_t j = Jc; j < P; ++j) {
     const uint32_t nt = tb[j + 1] - tb[j];
     if (nt == 0) continue;  // empty trailing interval: no tiles
-    // start of SS_ij in DSSS s (i = P: the column's end)
-    auto at = [&](size_t sx, uint32_t i) {
-      const Dsss& d = *ds[sx];
-      return i < P ? d.h_piece_off[piece_index(P, tb[j], nt, i, tb[j])]
-                   : d.h_piece_off[(uint64_t)P * tb[j + 1]];
+    // start of piece (i, t) in DSSS s; (i, tb[j + 1]) is the end of SS_ij and
+    // (P, tb[j]) the column's end
+    auto at = [&](size_t sx, uint32_t i, uint32_t t) {
+      return ds[sx]->h_piece_off[piece_index(P, tb[j], nt, i, t)];
     };
-    uint32_t i0 = 0;
-    const size_t before = out.size();
-    while (i0 < P) {
-      uint32_t i1 = i0 + 1;
-      while (i1 < P) {
-        uint64_t w = 0;
-        for (size_t sx = 0; sx < ds.size(); ++sx) w += at(sx, i1 + 1) - at(sx, i0);
-        if (w > kStreamChunkWords) break;
-        ++i1;
-      }
+    auto words = [&](uint32_t ia, uint32_t ta, uint32_t ib, uint32_t tb_) {
+      uint64_t w = 0;
+      for (size_t sx = 0; sx < ds.size(); ++sx) w += at(sx, ib, tb_) - at(sx, ia, ta);
+      return w;
+    };
+    auto push = [&](uint32_t i0, uint32_t i1, uint32_t t0, uint32_t t1, uint32_t ta, uint32_t ie,
+                    uint32_t te) {
       StreamBand b{};
       b.j = j;
       b.i0 = i0;
       b.i1 = i1;
+      b.t0 = t0;
+      b.t1 = t1;
       for (size_t sx = 0; sx < ds.size(); ++sx) {
-        b.e0[sx] = at(sx, i0) & ~(kEdgeAlign - 1);
-        b.e1[sx] = round_up(at(sx, i1), kEdgeAlign) + kEdgeAlign;
+        b.e0[sx] = at(sx, i0, ta) & ~(kEdgeAlign - 1);
+        b.e1[sx] = round_up(at(sx, ie, te), kEdgeAlign) + kEdgeAlign;
       }
+      b.first = (i0 == 0);
+      b.last = (i1 == P);
       out.push_back(b);
+    };
+    uint32_t i0 = 0;
+    while (i0 < P) {
+      uint32_t i1 = i0 + 1;
+      while (i1 < P && words(i0, tb[j], i1 + 1, tb[j]) <= kStreamChunkWords) ++i1;
+      if (i1 == i0 + 1 && words(i0, tb[j], i0 + 1, tb[j]) > kStreamChunkWords) {
+        // one sub-shard above the chunk: ranges of its tiles
+        for (uint32_t t = tb[j]; t < tb[j + 1];) {
+          uint32_t te = t + 1;
+          while (te < tb[j + 1] && words(i0, t, i0, te + 1) <= kStreamChunkWords) ++te;
+          push(i0, i0 + 1, t, te, t, i0, te);
+          t = te;
+        }
+      } else {
+        push(i0, i1, tb[j], tb[j + 1], tb[j], i1, tb[j]);
+      }
       i0 = i1;
     }
-    out[before].first = true;
-    out.back().last = true;
   }
   return out;
 }
@@ -1112,7 +1133,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
       plan_tiles(g, c.ds, 0, P, 0, c.Jc, true, blk, plan);
       for (const StreamBand& bd : bands) {
         launch_off.push_back((uint32_t)plan.items.size());
-        plan_tiles(g, c.ds, bd.i0, bd.i1, bd.j, bd.j + 1, true, blk, plan);
+        plan_tiles(g, c.ds, bd.i0, bd.i1, bd.j, bd.j + 1, true, blk, plan, bd.t0, bd.t1);
       }
       launch_off.push_back((uint32_t)plan.items.size());  // launch_off[0]: resident item count
     } else if (!staged) {  // DPU, intervals resident: ToHub items (all rows), then FromHub tiles

@@ -481,15 +481,44 @@ def test_spu_streams_shards_from_host(frac):
     assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
 
 
-def _budget_slack(info, nds):
+def test_streamed_sub_shard_above_a_chunk_is_cut_by_tiles():
+    # Degree-ordered ids put most edges in SS_00: at scale 21, P = 2, it holds
+    # far more than one 64 MB staging chunk (16 M words), so the streamed band
+    # is cut into ranges of its tiles. Results are unchanged and the staging
+    # buffers stay within the stated slack.
+    scale = 21
+    n = 1 << scale
+    s, d, _ = rmat(scale, 16, 14)
+    m = len(s)
+    g = nx.Graph(s, d, n, 2, transpose=True, relabel=True)
+    budget = 2 * n * 4 + (1 << 20)
+    st = g.run("pr", 10, "spu", budget=budget)
+    assert st["streamed_cols"] == 2
+    assert_pr_close(g.values(), oracle.pagerank(n, s, d, 0.85, 10), "PR, split sub-shard")
+    info = g.info()
+    assert info["device_bytes"] <= budget + _budget_slack(info, 1, True), info
+    # every word crosses the link once per iteration, plus the alignment of each band
+    assert 4 * m - (1 << 20) <= st["h2d_bytes"] / 10 <= 4 * m + 4096 * 128, (st["h2d_bytes"] / 10, m)
+    g.run("bfs", 1000, "spu", budget=budget, root=0)
+    assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 0)).all()
+    st = g.run("wcc", 1000, "spu", budget=budget)
+    assert st["streamed_cols"] == 2
+    assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+    info = g.info()
+    assert info["device_bytes"] <= budget + _budget_slack(info, 2, True), info
+    g.free()
+
+
+def _budget_slack(info, nds, relabeled=False):
     """Device bytes outside a budget's accounting (intervals 2 n B_a + resident
-    edge words): out-degrees and PageRank contributions (12 n), piece and hub
+    edge words): out-degrees and PageRank contributions (12 n), the id maps of
+    degree-ordered ids (8 n), piece and hub
     offsets of the DSSS the run reads (16 B per piece each), tile tables, the
-    accumulators of one streamed column (4 L), two staging buffers (at most
-    64 MB per DSSS each while no streamed sub-shard is larger), and 256 MB for
+    accumulators of one streamed column (4 L), two staging buffers (a band
+    holds at most 64 MB of words, down to single tiles), and 256 MB for
     plans, split-tile slots and scalars."""
     n, P, nt, L = info["n"], info["P"], info["ntiles"], info["L"]
-    return (12 * n + 16 * (P * nt + 1) * nds + 8 * (nt + P + 2) + 4 * L
+    return (12 * n + (8 * n if relabeled else 0) + 16 * (P * nt + 1) * nds + 8 * (nt + P + 2) + 4 * L
             + 2 * nds * (64 << 20) + (256 << 20))
 
 
