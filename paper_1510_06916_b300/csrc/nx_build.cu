@@ -28,19 +28,18 @@ namespace {
 // per vertex of shared memory.
 constexpr uint32_t kTileMaxCap = 2048;
 
-__global__ void k_check_ids(const uint32_t* __restrict__ a, uint64_t m, uint32_t n,
-                            uint32_t* __restrict__ bad) {
+// Degree histogram of ids a[0..m) into h[0..n); ids >= n are counted nowhere
+// and raise *bad (the build reads it before anything indexes by an id).
+__global__ void k_check_count(const uint32_t* __restrict__ a, uint64_t m, uint32_t n,
+                              uint32_t* __restrict__ h, uint32_t* __restrict__ bad) {
   uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   bool any = false;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
-    any |= a[e] >= n;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const uint32_t v = a[e];
+    if (v < n) atomicAdd(&h[v], 1u);
+    else any = true;
+  }
   if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
-}
-
-__global__ void k_histogram(const uint32_t* __restrict__ a, uint64_t m, uint32_t* __restrict__ h) {
-  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
-    atomicAdd(&h[a[e]], 1u);
 }
 
 __global__ void k_deg_sum(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
@@ -72,6 +71,16 @@ __global__ void k_tile_ids(const uint32_t* __restrict__ flag, uint32_t* __restri
   }
 }
 
+// vt[v] = tile of v << 32 | v's offset in its tile.
+__global__ void k_vertex_tiles(const uint32_t* __restrict__ tid, const uint32_t* __restrict__ tile_start,
+                               uint32_t n, uint64_t* __restrict__ vt) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const uint32_t t = tid[v];
+    vt[v] = ((uint64_t)t << 32) | (uint32_t)(v - tile_start[t]);
+  }
+}
+
 struct KeyCodec {
   uint32_t P, L, lb;
   __host__ __device__ uint64_t encode(uint32_t s, uint32_t d) const {
@@ -89,68 +98,117 @@ struct KeyCodec {
   }
 };
 
-// rename (nullable): internal id of each input id, applied on the fly.
+// rename (nullable): internal id of each input id, applied on the fly. Ids
+// >= n (rejected by the build before the keys are used) read no map entry.
 __global__ void k_make_keys(const uint32_t* __restrict__ s, const uint32_t* __restrict__ d,
-                            uint64_t m, KeyCodec kc, const uint32_t* __restrict__ rename,
+                            uint64_t m, uint32_t n, KeyCodec kc, const uint32_t* __restrict__ rename,
                             uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
   uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-    const uint32_t a = s[e], b = d[e];
+    uint32_t a = s[e], b = d[e];
+    a = a < n ? a : 0u;
+    b = b < n ? b : 0u;
     keys[e] = rename ? kc.encode(rename[a], rename[b]) : kc.encode(a, b);
     if (idx) idx[e] = (uint32_t)e;
   }
 }
 
+// Piece and destination of a key. vt[v] = (tile of v) << 32 | (v's offset in
+// its tile), so a key costs one lookup that depends on it.
 struct PieceMap {
   KeyCodec kc;
-  const uint32_t* tile_of;     // [n]
-  const uint32_t* tile_start;  // [ntiles+1]
-  const uint32_t* col_tb;      // [P+1]
-  __device__ uint64_t piece(uint64_t key, uint32_t* d_out, uint32_t* t_out, uint32_t* sl) const {
-    uint32_t i, j, d;
-    kc.decode(key, &i, &j, &d, sl);
-    uint32_t t = tile_of[d];
-    uint32_t tb = col_tb[j], nt = col_tb[j + 1] - tb;
-    *d_out = d;
-    *t_out = t;
-    return piece_index(kc.P, tb, nt, i, t);
+  const uint64_t* vt;      // [n]
+  const uint32_t* col_tb;  // [P+1]
+  struct Dec {
+    uint32_t i, j, d, sl;
+  };
+  __device__ Dec decode(uint64_t key) const {
+    Dec x;
+    kc.decode(key, &x.i, &x.j, &x.d, &x.sl);
+    return x;
+  }
+  // piece of a decoded key whose vt entry is `v`; *off: offset in the tile
+  __device__ uint64_t piece(const Dec& x, uint64_t v, uint32_t* off) const {
+    const uint32_t t = (uint32_t)(v >> 32);
+    const uint32_t tb = col_tb[x.j], nt = col_tb[x.j + 1] - tb;
+    *off = (uint32_t)v;
+    return piece_index(kc.P, tb, nt, x.i, t);
+  }
+  __device__ uint64_t piece(uint64_t key, uint32_t* d) const {
+    const Dec x = decode(key);
+    uint32_t off;
+    *d = x.d;
+    return piece(x, vt[x.d], &off);
   }
 };
 
 // Edge words, run-head bits and piece starts. A run is the edges of one
 // (piece, destination); its first edge is its head, and each head owns one hub
-// entry. Each warp takes 32 consecutive edges: hbits[w] holds their head bits
+// entry. Edges go in groups of 32 (w = e / 32): hbits[w] holds their head bits
 // and hcnt[w] the number of heads; pieces (pc(e-1), pc(e)] start at edge e.
+// Each warp takes kWordGroups consecutive groups per iteration and issues
+// their key loads, then their vertex lookups, together: the key -> vertex
+// chain is latency-bound, so the groups overlap their waits.
+constexpr int kWordGroups = 4;
 __global__ void k_words(const uint64_t* __restrict__ keys, uint64_t m, PieceMap pm,
                         uint32_t* __restrict__ ew, uint32_t* __restrict__ hbits,
                         uint32_t* __restrict__ hcnt, uint64_t* __restrict__ piece_off) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nw = (m + 31) / 32;
+  const uint64_t ng = (nw + kWordGroups - 1) / kWordGroups;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += nwarps) {
-    const uint64_t e = w * 32 + lane;
-    const bool valid = e < m;
-    uint32_t d = 0, t = 0, sl = 0;
-    uint64_t pc = 0;
-    if (valid) {
-      pc = pm.piece(keys[e], &d, &t, &sl);
-      ew[e] = ((d - pm.tile_start[t]) << pm.kc.lb) | sl;
+  for (uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nwarps) {
+    const uint64_t e0 = g * kWordGroups * 32;
+    uint64_t key[kWordGroups];
+#pragma unroll
+    for (int q = 0; q < kWordGroups; ++q) {
+      const uint64_t e = e0 + q * 32 + lane;
+      key[q] = e < m ? keys[e] : 0ull;
     }
-    uint64_t pc0 = __shfl_up_sync(0xffffffffu, pc, 1);
-    uint32_t d0 = __shfl_up_sync(0xffffffffu, d, 1);
-    if (lane == 0 && e > 0) {  // the previous edge belongs to the previous warp's range
-      uint32_t t0, sl0;
-      pc0 = pm.piece(keys[e - 1], &d0, &t0, &sl0);
+    // the edge before the first group belongs to the previous iteration's range
+    const uint64_t kprev = (lane == 0 && e0 > 0) ? keys[e0 - 1] : 0ull;
+    PieceMap::Dec x[kWordGroups];
+    uint64_t v[kWordGroups];
+#pragma unroll
+    for (int q = 0; q < kWordGroups; ++q) {
+      x[q] = pm.decode(key[q]);
+      v[q] = (e0 + q * 32 + lane < m) ? pm.vt[x[q].d] : 0ull;
     }
-    const bool head = valid && (e == 0 || pc0 != pc || d0 != d);
-    const uint32_t bits = __ballot_sync(0xffffffffu, head);
-    if (lane == 0) {
-      hbits[w] = bits;
-      hcnt[w] = __popc(bits);
-    }
-    if (valid) {
-      const uint64_t k0 = (e == 0) ? 0 : pc0 + 1;
-      for (uint64_t k = k0; k <= pc; ++k) piece_off[k] = e;
+    const PieceMap::Dec xp = pm.decode(kprev);
+    const uint64_t vp = (lane == 0 && e0 > 0) ? pm.vt[xp.d] : 0ull;
+    uint32_t offp;
+    uint64_t pc_last = pm.piece(xp, vp, &offp);  // the previous edge's piece (lane 0)
+    uint32_t d_last = xp.d;
+#pragma unroll
+    for (int q = 0; q < kWordGroups; ++q) {
+      const uint64_t w = g * kWordGroups + q;
+      const uint64_t e = e0 + q * 32 + lane;
+      const bool valid = e < m;
+      uint32_t off = 0;
+      uint64_t pc = 0;
+      if (valid) {
+        pc = pm.piece(x[q], v[q], &off);
+        ew[e] = (off << pm.kc.lb) | x[q].sl;
+      }
+      const uint32_t d = valid ? x[q].d : 0u;
+      uint64_t pc0 = __shfl_up_sync(0xffffffffu, pc, 1);
+      uint32_t d0 = __shfl_up_sync(0xffffffffu, d, 1);
+      if (lane == 0) {
+        pc0 = pc_last;
+        d0 = d_last;
+      }
+      pc_last = __shfl_sync(0xffffffffu, pc, 31);  // lane 31 precedes the next group's lane 0
+      d_last = __shfl_sync(0xffffffffu, d, 31);
+      const bool head = valid && (e == 0 || pc0 != pc || d0 != d);
+      const uint32_t bits = __ballot_sync(0xffffffffu, head);
+      if (lane == 0 && w < nw) {
+        hbits[w] = bits;
+        hcnt[w] = __popc(bits);
+      }
+      if (valid) {
+        const uint64_t k0 = (e == 0) ? 0 : pc0 + 1;
+        for (uint64_t k = k0; k <= pc; ++k) piece_off[k] = e;
+      }
     }
   }
 }
@@ -160,8 +218,8 @@ __global__ void k_piece_tail(const uint64_t* __restrict__ keys, uint64_t m, Piec
                              uint64_t* __restrict__ piece_off, uint64_t npieces) {
   uint64_t k0 = 0;
   if (m) {
-    uint32_t d, t, sl;
-    k0 = pm.piece(keys[m - 1], &d, &t, &sl) + 1;
+    uint32_t d;
+    k0 = pm.piece(keys[m - 1], &d) + 1;
   }
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t k = k0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= npieces; k += stride)
@@ -231,29 +289,36 @@ unsigned grid_for(uint64_t work, unsigned threads = 256) {
 // Builds one DSSS from (s, d) over the geometry; wn (nullable) are the
 // normalised weights in input order.
 // rename (nullable): applied to s and d while the keys are made.
+// sorted (nullable): the keys of (s, d), already sorted (taken over; no
+// weights).
 nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geometry& geo,
-                    const uint32_t* tile_of, const float* wn, Dsss& out,
-                    const uint32_t* rename = nullptr) {
+                    const uint64_t* vt, const float* wn, Dsss& out,
+                    const uint32_t* rename = nullptr, DevBuf* sorted = nullptr) {
   out.m = m;
   const uint64_t npieces = (uint64_t)geo.P * geo.ntiles;
   KeyCodec kc{geo.P, geo.L, geo.lb};
   const uint32_t key_bits = bits_for((uint64_t)geo.P * geo.P) + 2 * geo.lb;
   if (key_bits > 64) return invalid("DSSS key does not fit 64 bits (n too large for P)");
   DevBuf keys, idx;
-  NX_TRY(keys.alloc(std::max<uint64_t>(m, 1) * sizeof(uint64_t)));
-  if (wn) NX_TRY(idx.alloc(std::max<uint64_t>(m, 1) * sizeof(uint32_t)));
-  if (m) {
-    k_make_keys<<<grid_for(m), 256, 0, stream()>>>(s, d, m, kc, rename, keys.as<uint64_t>(),
-                                                   wn ? idx.as<uint32_t>() : nullptr);
-    NX_LAUNCH_CHECK();
-    NX_TRY(radix_sort_u64(keys, wn ? &idx : nullptr, m, key_bits));
+  if (sorted && sorted->p) {
+    if (wn) return invalid("build_one: presorted keys carry no weights");
+    keys = std::move(*sorted);
+  } else {
+    NX_TRY(keys.alloc(std::max<uint64_t>(m, 1) * sizeof(uint64_t)));
+    if (wn) NX_TRY(idx.alloc(std::max<uint64_t>(m, 1) * sizeof(uint32_t)));
+    if (m) {
+      k_make_keys<<<grid_for(m), 256, 0, stream()>>>(s, d, m, geo.n, kc, rename, keys.as<uint64_t>(),
+                                                     wn ? idx.as<uint32_t>() : nullptr);
+      NX_LAUNCH_CHECK();
+      NX_TRY(radix_sort_u64(keys, wn ? &idx : nullptr, m, key_bits));
+    }
   }
   const uint64_t mpad = round_up(m, kEdgeAlign) + kEdgeAlign;
   NX_TRY(out.ew.alloc(mpad * sizeof(uint32_t)));
   NX_CUDA(cudaMemsetAsync(out.ew.p, 0, mpad * sizeof(uint32_t), stream()));
   NX_TRY(out.piece_off.alloc((npieces + 1) * sizeof(uint64_t)));
   NX_TRY(out.hub_off.alloc((npieces + 1) * sizeof(uint64_t)));
-  PieceMap pm{kc, tile_of, geo.tile_start.as<uint32_t>(), geo.col_tb.as<uint32_t>()};
+  PieceMap pm{kc, vt, geo.col_tb.as<uint32_t>()};
   const uint64_t nw = (m + 31) / 32;
   DevBuf hbits, hcnt, dtot;
   NX_TRY(hbits.alloc(std::max<uint64_t>(nw, 1) * sizeof(uint32_t)));
@@ -303,8 +368,9 @@ nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geom
   return NX_OK;
 }
 
+// vt: the tile of every vertex and its offset in the tile (k_vertex_tiles).
 nx_status build_geometry(nx_graph* g, const uint32_t* deg_a, const uint32_t* deg_b,
-                         uint64_t m_bal, uint32_t edges_log2, DevBuf& tile_of) {
+                         uint64_t m_bal, uint32_t edges_log2, DevBuf& vt) {
   Geometry& geo = g->geo;
   const uint32_t n = geo.n;
   // E_tile: about m / (8 x SMs), within [2^14, 2^20]. The vertex cap bounds
@@ -318,7 +384,7 @@ nx_status build_geometry(nx_graph* g, const uint32_t* deg_a, const uint32_t* deg
   uint64_t E = m_bal / ((uint64_t)num_sms() * 8);
   E = std::max<uint64_t>(16384, std::min<uint64_t>(E, 1ull << 20));
   if (edges_log2) E = 1ull << edges_log2;
-  DevBuf pre, flag;
+  DevBuf pre, flag, tile_of;
   NX_TRY(pre.alloc((uint64_t)n * sizeof(uint64_t)));
   NX_TRY(flag.alloc((uint64_t)n * sizeof(uint32_t)));
   NX_TRY(tile_of.alloc((uint64_t)n * sizeof(uint32_t)));
@@ -341,6 +407,10 @@ nx_status build_geometry(nx_graph* g, const uint32_t* deg_a, const uint32_t* deg
   NX_LAUNCH_CHECK();
   NX_CUDA(cudaMemcpyAsync(geo.tile_start.as<uint32_t>() + ntiles, &geo.n, sizeof(uint32_t),
                           cudaMemcpyHostToDevice, stream()));
+  NX_TRY(vt.alloc((uint64_t)n * sizeof(uint64_t)));
+  k_vertex_tiles<<<grid_for(n), 256, 0, stream()>>>(tile_of.as<uint32_t>(), geo.tile_start.as<uint32_t>(),
+                                                    n, vt.as<uint64_t>());
+  NX_LAUNCH_CHECK();
   geo.h_tile_start.resize((size_t)ntiles + 1);
   NX_CUDA(cudaMemcpyAsync(geo.h_tile_start.data(), geo.tile_start.p,
                           ((uint64_t)ntiles + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost,
@@ -383,6 +453,89 @@ struct Upload {
   }
 };
 
+// Host edges without weights: the src chunks cross the link first, then the
+// dst chunks, on a side stream. The out-degrees are complete once src has
+// landed, so NX_RELABEL's order is computed while dst arrives; each dst
+// chunk's keys (forward, and transpose when asked) are made in the new ids and
+// sorted as it lands, and only the merge of the sorted chunks is left once the
+// last chunk is in. The keys are the same as build_one's, so is their order.
+nx_status upload_and_sort(nx_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t m,
+                          uint32_t n, uint32_t P, bool relabel, bool want_t, uint32_t* hs,
+                          uint32_t* hd, uint32_t* indeg, uint32_t* bad, DevBuf* sorted) {
+  const uint32_t L = (uint32_t)ceil_div(n, P), lb = bits_for(L);
+  const KeyCodec kc{P, L, lb};
+  const uint32_t key_bits = bits_for((uint64_t)P * P) + 2 * lb;
+  if (key_bits > 64) return invalid("DSSS key does not fit 64 bits (n too large for P)");
+  constexpr uint64_t kChunks = 8;
+  const uint64_t chunk = round_up(ceil_div(m, kChunks), 1024);
+  const int nc = (int)ceil_div(m, chunk);
+  Upload up;
+  NX_TRY(up.init(2 * nc));
+  NX_CUDA(cudaEventRecord(up.ready, stream()));  // the buffers exist in stream order
+  NX_CUDA(cudaStreamWaitEvent(up.side, up.ready, 0));
+  auto range = [&](int c, uint64_t* e0, uint64_t* len) {
+    *e0 = (uint64_t)c * chunk;
+    *len = std::min<uint64_t>(chunk, m - *e0);
+  };
+  // Copies from pinned memory are queued at once (the host returns at once,
+  // the link never waits for the relabel step); from pageable memory the host
+  // thread stages each copy itself, so each chunk's copy is issued just before
+  // its work, which then runs while the host stages the next chunk.
+  auto pinned = [](const void* p) {
+    cudaPointerAttributes at{};
+    return cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost;
+  };
+  const bool queue_all = pinned(src) && pinned(dst);
+  cudaGetLastError();  // a failed attribute query leaves no error behind
+  auto copy = [&](int c, bool second) -> nx_status {
+    uint64_t a0, n0;
+    range(c, &a0, &n0);
+    NX_CUDA(cudaMemcpyAsync((second ? hd : hs) + a0, (second ? dst : src) + a0, n0 * 4,
+                            cudaMemcpyHostToDevice, up.side));
+    NX_CUDA(cudaEventRecord(up.copied[(second ? nc : 0) + c], up.side));
+    return NX_OK;
+  };
+  if (queue_all)
+    for (int c = 0; c < 2 * nc; ++c) NX_TRY(copy(c % nc, c >= nc));
+  uint64_t e0, len;
+  for (int c = 0; c < nc; ++c) {
+    range(c, &e0, &len);
+    if (!queue_all) NX_TRY(copy(c, false));
+    NX_CUDA(cudaStreamWaitEvent(stream(), up.copied[c], 0));
+    k_check_count<<<grid_for(len), 256, 0, stream()>>>(hs + e0, len, n, g->outdeg.as<uint32_t>(), bad);
+    NX_LAUNCH_CHECK();
+  }
+  if (relabel) NX_TRY(relabel_edges(g, nullptr, nullptr, 0, nullptr, nullptr, g->outdeg.as<uint32_t>()));
+  const uint32_t* ren = relabel ? g->new_of_old.as<uint32_t>() : nullptr;
+  const int nk = want_t ? 2 : 1;
+  for (int k = 0; k < nk; ++k) NX_TRY(sorted[k].alloc(m * sizeof(uint64_t)));
+  DevBuf scratch, counts;
+  NX_TRY(scratch.alloc(chunk * sizeof(uint64_t)));
+  NX_TRY(counts.alloc(radix_sort_count_words(chunk) * sizeof(uint32_t)));
+  std::vector<uint64_t> bounds{0};
+  for (int c = 0; c < nc; ++c) {
+    range(c, &e0, &len);
+    if (!queue_all) NX_TRY(copy(c, true));
+    NX_CUDA(cudaStreamWaitEvent(stream(), up.copied[nc + c], 0));
+    k_check_count<<<grid_for(len), 256, 0, stream()>>>(hd + e0, len, n, indeg, bad);
+    NX_LAUNCH_CHECK();
+    for (int k = 0; k < nk; ++k) {
+      uint64_t* kk = sorted[k].as<uint64_t>() + e0;
+      k_make_keys<<<grid_for(len), 256, 0, stream()>>>(k ? hd + e0 : hs + e0, k ? hs + e0 : hd + e0,
+                                                       len, n, kc, ren, kk, nullptr);
+      NX_LAUNCH_CHECK();
+      bool in_b = false;
+      NX_TRY(radix_sort_u64_raw(kk, scratch.as<uint64_t>(), nullptr, nullptr, counts.as<uint32_t>(),
+                                len, key_bits, &in_b));
+      if (in_b)
+        NX_CUDA(cudaMemcpyAsync(kk, scratch.p, len * sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream()));
+    }
+    bounds.push_back(e0 + len);
+  }
+  for (int k = 0; k < nk; ++k) NX_TRY(merge_runs_u64(sorted[k], bounds));  // synchronises
+  return NX_OK;
+}
+
 nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t P,
                      uint32_t flags, const float* w, nx_graph* g) {
   const bool on_dev = flags & NX_DEV_PTRS;
@@ -391,10 +544,10 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   EventPair ev;
   NX_TRY(ev.create());
   NX_CUDA(cudaEventRecord(ev.e0, stream()));
+  g->geo.n = n;  // relabel_edges reads it, during the upload of host edges too
   // Degrees of the input ids are counted as the edges arrive (overlapping the
   // upload of host edges); NX_RELABEL orders the vertices by them and then
   // permutes them to the new ids (a renamed vertex keeps its degrees).
-  const bool early_deg = true;
   DevBuf indeg, bad, od_new;
   // The value and contribution arrays every run gathers from, and the
   // out-degrees in new ids, are allocated before the build's temporaries
@@ -414,20 +567,20 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   NX_CUDA(cudaMemsetAsync(bad.p, 0, 4, stream()));
   // per range of edges: ids < n, and the degree histograms
   auto scan_edges = [&](const uint32_t* s0, const uint32_t* d0, uint64_t len) -> nx_status {
-    k_check_ids<<<grid_for(len), 256, 0, stream()>>>(s0, len, n, bad.as<uint32_t>());
-    k_check_ids<<<grid_for(len), 256, 0, stream()>>>(d0, len, n, bad.as<uint32_t>());
-    if (early_deg) {
-      k_histogram<<<grid_for(len), 256, 0, stream()>>>(s0, len, g->outdeg.as<uint32_t>());
-      k_histogram<<<grid_for(len), 256, 0, stream()>>>(d0, len, indeg.as<uint32_t>());
-    }
+    k_check_count<<<grid_for(len), 256, 0, stream()>>>(s0, len, n, g->outdeg.as<uint32_t>(),
+                                                       bad.as<uint32_t>());
+    k_check_count<<<grid_for(len), 256, 0, stream()>>>(d0, len, n, indeg.as<uint32_t>(),
+                                                       bad.as<uint32_t>());
     NX_LAUNCH_CHECK();
     return NX_OK;
   };
   // device copies of host inputs, uploaded in chunks on a side stream so the
   // checks and histograms of one chunk overlap the copy of the next
   DevBuf ds, dd, dw;
+  DevBuf sorted[2];  // forward / transpose keys sorted while the host edges arrive
   const uint32_t *s = src, *d = dst;
   const float* wp = w;
+  const bool presorted = !on_dev && m && !want_w;
   if (!on_dev) {
     NX_TRY(ds.alloc(std::max<uint64_t>(m, 1) * 4));
     NX_TRY(dd.alloc(std::max<uint64_t>(m, 1) * 4));
@@ -435,7 +588,10 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
     s = ds.as<uint32_t>();
     d = dd.as<uint32_t>();
     if (want_w) wp = dw.as<float>();
-    if (m) {
+    if (presorted) {
+      NX_TRY(upload_and_sort(g, src, dst, m, n, P, (flags & NX_RELABEL) != 0, want_t, ds.as<uint32_t>(),
+                             dd.as<uint32_t>(), indeg.as<uint32_t>(), bad.as<uint32_t>(), sorted));
+    } else if (m) {
       constexpr int kChunks = 8;
       Upload up;
       NX_TRY(up.init(kChunks));
@@ -472,7 +628,11 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   // With nothing but the forward DSSS to build, the keys apply the new ids
   // themselves and the renamed endpoint arrays are never written.
   const bool rename_in_keys = (flags & NX_RELABEL) && !want_t && !want_w && !(flags & NX_ONCHIP_HUBS);
-  if ((flags & NX_RELABEL) && rename_in_keys) {
+  if ((flags & NX_RELABEL) && presorted) {
+    // the order exists and the keys carry the new ids; only the on-chip
+    // structure reads the endpoint arrays, in the new ids
+    if (flags & NX_ONCHIP_HUBS) NX_TRY(rename_edges(g, ds.as<uint32_t>(), dd.as<uint32_t>(), m));
+  } else if ((flags & NX_RELABEL) && rename_in_keys) {
     NX_TRY(relabel_edges(g, s, d, m, nullptr, nullptr, g->outdeg.as<uint32_t>()));
   } else if (flags & NX_RELABEL) {  // host inputs are renamed in their device copies
     uint32_t* so = ds.as<uint32_t>();
@@ -503,9 +663,9 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   const uint32_t cap_log2 = (flags >> 8) & 0xFu, edges_log2 = (flags >> 12) & 0x1Fu;
   const uint64_t cap = cap_log2 ? (1ull << cap_log2) : kTileMaxCap;
   geo.tile_max = (uint32_t)std::min<uint64_t>(cap, 1ull << (32 - geo.lb));
-  DevBuf tile_of;
+  DevBuf vt;
   NX_TRY(build_geometry(g, indeg.as<uint32_t>(), want_t ? g->outdeg.as<uint32_t>() : nullptr,
-                        want_t ? 2 * m : m, edges_log2, tile_of));
+                        want_t ? 2 * m : m, edges_log2, vt));
   indeg.release();
   // weights: W_u in FP64, normalised weights in input order
   DevBuf wn;
@@ -525,12 +685,12 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
     NX_CUDA(cudaStreamSynchronize(stream()));
     g->has_w = true;
   }
-  NX_TRY(build_one(s, d, m, geo, tile_of.as<uint32_t>(), want_w ? wn.as<float>() : nullptr, g->fwd,
-                   rename_in_keys ? g->new_of_old.as<uint32_t>() : nullptr));
+  NX_TRY(build_one(s, d, m, geo, vt.as<uint64_t>(), want_w ? wn.as<float>() : nullptr, g->fwd,
+                   rename_in_keys ? g->new_of_old.as<uint32_t>() : nullptr, &sorted[0]));
   if (flags & NX_ONCHIP_HUBS) NX_TRY(build_onchip(g, s, d, m));
   if (want_t) {
-    NX_TRY(build_one(d, s, m, geo, tile_of.as<uint32_t>(), want_w ? wn.as<float>() : nullptr,
-                     g->tr));
+    NX_TRY(build_one(d, s, m, geo, vt.as<uint64_t>(), want_w ? wn.as<float>() : nullptr,
+                     g->tr, nullptr, &sorted[1]));
     g->has_tr = true;
   }
   if (want_w) {  // caller-order endpoints for the edge gradients

@@ -165,6 +165,16 @@ nx_status exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint
 // in buffers swapped in from the sort's scratch (at least n elements), so
 // pointers taken from them before the call are stale.
 nx_status radix_sort_u64(DevBuf& keys, DevBuf* vals, uint64_t n, uint32_t key_bits);
+// The same on caller buffers, stream-ordered, no allocation: keys a[0..n)
+// (payload va, nullable) with scratch b (vb) of n elements and `counts` of
+// radix_sort_count_words(n) words; *in_b tells whether the result ended in b.
+nx_status radix_sort_u64_raw(uint64_t* a, uint64_t* b, uint32_t* va, uint32_t* vb, uint32_t* counts,
+                             uint64_t n, uint32_t key_bits, bool* in_b);
+uint64_t radix_sort_count_words(uint64_t n);
+// Stable merge (ties: the earlier run first) of the sorted runs
+// keys[bounds[r], bounds[r + 1]) into one sorted sequence, pairwise by merge
+// path; keys may be swapped with the scratch buffer as in radix_sort_u64.
+nx_status merge_runs_u64(DevBuf& keys, const std::vector<uint64_t>& bounds);
 // Smallest shared-memory carveout that keeps the occupancy of kernel `fn`
 // (`threads` per block, `smem` dynamic bytes); the rest of L1 caches loads.
 nx_status prefer_l1(const void* fn, int threads, size_t smem);
@@ -353,6 +363,8 @@ nx_status onchip_iteration(nx_graph* g, const OcRun& r, cudaStream_t s);
 nx_status relabel_edges(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64_t m,
                         uint32_t* s_out, uint32_t* d_out, const uint32_t* outdeg);
 nx_status gather_u32(const uint32_t* idx, const void* in, void* out, uint64_t n);
+// Endpoints renamed to the new ids of g in place (caller ids -> internal ids).
+nx_status rename_edges(const nx_graph* g, uint32_t* s, uint32_t* d, uint64_t m);
 // Vertex arrays across the ABI: caller order -> internal order (to_internal)
 // or back; a plain copy for graphs that were not relabeled. `in` and `out`
 // are device pointers and must not alias.

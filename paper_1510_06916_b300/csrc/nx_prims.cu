@@ -492,59 +492,178 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(
 }
 }  // namespace
 
-nx_status radix_sort_u64(DevBuf& keys, DevBuf* vals, uint64_t n, uint32_t key_bits) {
+uint64_t radix_sort_count_words(uint64_t n) {
+  return ceil_div(std::max<uint64_t>(n, 1), RS_TILE) << RS_MAX_BITS;
+}
+
+nx_status radix_sort_u64_raw(uint64_t* a, uint64_t* b, uint32_t* va, uint32_t* vb, uint32_t* counts,
+                             uint64_t n, uint32_t key_bits, bool* in_b) {
+  *in_b = false;
   if (n <= 1 || key_bits == 0) return NX_OK;
   if (n >= (1ull << 32)) return invalid("radix_sort_u64: n must be < 2^32");
   key_bits = std::min<uint32_t>(key_bits, 64);
   const uint32_t nb = (uint32_t)ceil_div(n, RS_TILE);
   // passes of at most 9 bits, as even as possible (52 bits: 9,9,9,9,8,8)
   const uint32_t npass = (key_bits + RS_MAX_BITS - 1) / RS_MAX_BITS;
-  DevBuf k2, v2, counts;
-  NX_TRY(k2.alloc(n * sizeof(uint64_t)));
-  if (vals) NX_TRY(v2.alloc(n * sizeof(uint32_t)));
-  NX_TRY(counts.alloc((uint64_t)nb * (1u << RS_MAX_BITS) * sizeof(uint32_t)));
-  DevBuf* ka = &keys;
-  DevBuf* kb = &k2;
-  DevBuf* va = vals;
-  DevBuf* vb = vals ? &v2 : nullptr;
-  const size_t smem = (size_t)RS_TILE * (sizeof(uint64_t) + (vals ? sizeof(uint32_t) : 0));
+  const size_t smem = (size_t)RS_TILE * (sizeof(uint64_t) + (va ? sizeof(uint32_t) : 0));
   // dynamic + static shared memory exceed 48 KB: opt in (per device, so every call)
   NX_CUDA(cudaFuncSetAttribute(rs_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   NX_CUDA(cudaFuncSetAttribute(rs_scatter<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  uint64_t* ka = a;
+  uint64_t* kb = b;
+  uint32_t* vx = va;
+  uint32_t* vy = vb;
   uint32_t shift = 0;
   for (uint32_t p = 0; p < npass; ++p) {
     const uint32_t width = key_bits / npass + (p < key_bits % npass ? 1u : 0u);
     const uint32_t mask = (1u << width) - 1u;
     const uint64_t nc = (uint64_t)nb << width;
     if (width > 8) {
-      rs_hist<9><<<nb, RS_THREADS, 0, stream()>>>(ka->as<uint64_t>(), n, shift, mask,
-                                                  counts.as<uint32_t>(), nb);
+      rs_hist<9><<<nb, RS_THREADS, 0, stream()>>>(ka, n, shift, mask, counts, nb);
     } else {
-      rs_hist<8><<<nb, RS_THREADS, 0, stream()>>>(ka->as<uint64_t>(), n, shift, mask,
-                                                  counts.as<uint32_t>(), nb);
+      rs_hist<8><<<nb, RS_THREADS, 0, stream()>>>(ka, n, shift, mask, counts, nb);
     }
     NX_LAUNCH_CHECK();
-    NX_TRY(exclusive_scan_u32(counts.as<uint32_t>(), counts.as<uint32_t>(), nc, nullptr));
+    NX_TRY(exclusive_scan_u32(counts, counts, nc, nullptr));
     if (width > 8) {
-      rs_scatter<9><<<nb, RS_THREADS, smem, stream()>>>(
-          ka->as<uint64_t>(), va ? va->as<uint32_t>() : nullptr, kb->as<uint64_t>(),
-          vb ? vb->as<uint32_t>() : nullptr, n, shift, mask, counts.as<uint32_t>(), nb);
+      rs_scatter<9><<<nb, RS_THREADS, smem, stream()>>>(ka, vx, kb, vy, n, shift, mask, counts, nb);
     } else {
-      rs_scatter<8><<<nb, RS_THREADS, smem, stream()>>>(
-          ka->as<uint64_t>(), va ? va->as<uint32_t>() : nullptr, kb->as<uint64_t>(),
-          vb ? vb->as<uint32_t>() : nullptr, n, shift, mask, counts.as<uint32_t>(), nb);
+      rs_scatter<8><<<nb, RS_THREADS, smem, stream()>>>(ka, vx, kb, vy, n, shift, mask, counts, nb);
     }
     NX_LAUNCH_CHECK();
     std::swap(ka, kb);
-    std::swap(va, vb);
+    std::swap(vx, vy);
     shift += width;
   }
-  if (npass & 1) {  // the result sits in the scratch buffers: hand them to the caller
+  *in_b = (npass & 1) != 0;
+  return NX_OK;
+}
+
+nx_status radix_sort_u64(DevBuf& keys, DevBuf* vals, uint64_t n, uint32_t key_bits) {
+  if (n <= 1 || key_bits == 0) return NX_OK;
+  DevBuf k2, v2, counts;
+  NX_TRY(k2.alloc(n * sizeof(uint64_t)));
+  if (vals) NX_TRY(v2.alloc(n * sizeof(uint32_t)));
+  NX_TRY(counts.alloc(radix_sort_count_words(n) * sizeof(uint32_t)));
+  bool in_b = false;
+  NX_TRY(radix_sort_u64_raw(keys.as<uint64_t>(), k2.as<uint64_t>(), vals ? vals->as<uint32_t>() : nullptr,
+                            vals ? v2.as<uint32_t>() : nullptr, counts.as<uint32_t>(), n, key_bits,
+                            &in_b));
+  if (in_b) {  // the result sits in the scratch buffers: hand them to the caller
     std::swap(keys, k2);
     if (vals) std::swap(*vals, v2);
   }
   // scratch is freed on return: make sure the stream is done with it
   NX_CUDA(cudaStreamSynchronize(stream()));
+  return NX_OK;
+}
+
+// ---------------------------------------------------------------- merge
+// Stable merge of two sorted runs (ties: the first run's keys first) by merge
+// path: a partition pass finds, for every output tile of MG_TILE keys, how
+// many of its predecessors come from the first run (a binary search along the
+// tile's cross diagonal); each block then stages its tile's inputs in shared
+// memory, each thread finds its own split there and merges MG_ITEMS keys, and
+// the block writes the tile out in order.
+constexpr int MG_THREADS = 256;
+constexpr int MG_ITEMS = 8;
+constexpr int MG_TILE = MG_THREADS * MG_ITEMS;  // 2048
+
+// Keys of `a` among the first `diag` outputs.
+template <class I>
+__device__ __forceinline__ I merge_split(const uint64_t* a, I na, const uint64_t* b, I nb, I diag) {
+  I lo = diag > nb ? diag - nb : 0, hi = diag < na ? diag : na;
+  while (lo < hi) {
+    const I mid = (lo + hi) >> 1;
+    if (a[mid] <= b[diag - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_merge_part(const uint64_t* __restrict__ a, uint64_t na, const uint64_t* __restrict__ b,
+                             uint64_t nb, uint64_t ntiles, uint64_t* __restrict__ split) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += stride)
+    split[t] = merge_split<uint64_t>(a, na, b, nb, std::min<uint64_t>(t * MG_TILE, na + nb));
+}
+
+__global__ void __launch_bounds__(MG_THREADS) k_merge(const uint64_t* __restrict__ a, uint64_t na,
+                                                      const uint64_t* __restrict__ b, uint64_t nb,
+                                                      const uint64_t* __restrict__ split,
+                                                      uint64_t* __restrict__ out) {
+  __shared__ uint64_t sm[MG_TILE];
+  const uint64_t k0 = (uint64_t)blockIdx.x * MG_TILE;
+  const uint64_t k1 = std::min<uint64_t>(k0 + MG_TILE, na + nb);
+  const uint64_t a0 = split[blockIdx.x], a1 = split[blockIdx.x + 1];
+  const uint64_t b0 = k0 - a0, b1 = k1 - a1;
+  const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0), cnt = la + lb;
+  for (uint32_t x = threadIdx.x; x < la; x += MG_THREADS) sm[x] = a[a0 + x];
+  for (uint32_t x = threadIdx.x; x < lb; x += MG_THREADS) sm[la + x] = b[b0 + x];
+  __syncthreads();
+  const uint32_t diag = std::min<uint32_t>(threadIdx.x * MG_ITEMS, cnt);
+  uint32_t i = merge_split<uint32_t>(sm, la, sm + la, lb, diag), j = diag - i;
+  uint64_t v[MG_ITEMS];
+#pragma unroll
+  for (int q = 0; q < MG_ITEMS; ++q) {
+    const bool take_a = i < la && (j >= lb || sm[i] <= sm[la + j]);
+    const bool any = i < la || j < lb;
+    v[q] = any ? (take_a ? sm[i] : sm[la + j]) : 0ull;
+    i += (any && take_a) ? 1u : 0u;
+    j += (any && !take_a) ? 1u : 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < MG_ITEMS; ++q)
+    if (diag + q < cnt) sm[diag + q] = v[q];
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < cnt; x += MG_THREADS) out[k0 + x] = sm[x];
+}
+
+nx_status merge_u64(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb, uint64_t* out,
+                    uint64_t* split) {
+  const uint64_t total = na + nb;
+  if (!total) return NX_OK;
+  const uint64_t ntiles = ceil_div(total, MG_TILE);
+  if (ntiles >= (1ull << 31)) return invalid("merge_u64: too many keys");
+  k_merge_part<<<(unsigned)std::min<uint64_t>(ceil_div(ntiles + 1, 256), (uint64_t)num_sms() * 16), 256, 0,
+                 stream()>>>(a, na, b, nb, ntiles, split);
+  NX_LAUNCH_CHECK();
+  k_merge<<<(unsigned)ntiles, MG_THREADS, 0, stream()>>>(a, na, b, nb, split, out);
+  NX_LAUNCH_CHECK();
+  return NX_OK;
+}
+
+uint64_t merge_split_words(uint64_t n) { return ceil_div(std::max<uint64_t>(n, 1), MG_TILE) + 2; }
+
+nx_status merge_runs_u64(DevBuf& keys, const std::vector<uint64_t>& bounds) {
+  if (bounds.size() <= 2) return NX_OK;  // one run (or none)
+  const uint64_t n = bounds.back();
+  DevBuf tmp, split;
+  NX_TRY(tmp.alloc(std::max<uint64_t>(n, 1) * sizeof(uint64_t)));
+  NX_TRY(split.alloc(merge_split_words(n) * sizeof(uint64_t)));
+  std::vector<uint64_t> bd = bounds;
+  DevBuf* src = &keys;
+  DevBuf* dst = &tmp;
+  while (bd.size() > 2) {  // pairs of adjacent runs; an odd last run is copied
+    std::vector<uint64_t> nbd{0};
+    for (size_t r = 0; r + 1 < bd.size(); r += 2) {
+      const uint64_t x0 = bd[r], x1 = bd[r + 1];
+      const uint64_t x2 = (r + 2 < bd.size()) ? bd[r + 2] : x1;
+      if (x2 > x1) {
+        NX_TRY(merge_u64(src->as<uint64_t>() + x0, x1 - x0, src->as<uint64_t>() + x1, x2 - x1,
+                         dst->as<uint64_t>() + x0, split.as<uint64_t>()));
+      } else if (x1 > x0) {
+        NX_CUDA(cudaMemcpyAsync(dst->as<uint64_t>() + x0, src->as<uint64_t>() + x0, (x1 - x0) * 8,
+                                cudaMemcpyDeviceToDevice, stream()));
+      }
+      nbd.push_back(x2);
+    }
+    bd.swap(nbd);
+    std::swap(src, dst);
+  }
+  if (src != &keys) std::swap(keys, tmp);
+  NX_CUDA(cudaStreamSynchronize(stream()));  // tmp and split are freed on return
   return NX_OK;
 }
 

@@ -67,6 +67,7 @@ unsigned grid_of(uint64_t work) {
 nx_status relabel_edges(nx_graph* g, const uint32_t* s, const uint32_t* d, uint64_t m,
                         uint32_t* s_out, uint32_t* d_out, const uint32_t* outdeg) {
   const uint32_t n = g->geo.n;
+  if (n == 0) return invalid("relabel_edges: the graph's n is not set");
   DevBuf keys, ids, mx;
   NX_TRY(mx.alloc(4));
   NX_CUDA(cudaMemsetAsync(mx.p, 0, 4, stream()));
@@ -92,6 +93,13 @@ nx_status relabel_edges(nx_graph* g, const uint32_t* s, const uint32_t* d, uint6
   }
   NX_CUDA(cudaStreamSynchronize(stream()));  // od and keys are freed on return
   g->relabeled = true;
+  return NX_OK;
+}
+
+nx_status rename_edges(const nx_graph* g, uint32_t* s, uint32_t* d, uint64_t m) {
+  if (!m) return NX_OK;
+  k_rename<<<grid_of(m), 256, 0, stream()>>>(g->new_of_old.as<uint32_t>(), s, d, m, s, d);
+  NX_LAUNCH_CHECK();
   return NX_OK;
 }
 

@@ -1003,3 +1003,60 @@ def test_relabel_rejected_where_unsupported():
     plain = nx.Graph(s, d, n, 4)
     with pytest.raises(nx.NxError):
         plain.relabel_map()
+
+
+@pytest.mark.parametrize("m", [8200, 100_000])  # 5 (odd) and 8 sorted chunks to merge
+@pytest.mark.parametrize("kind", ["pageable", "pinned", "device"])
+def test_host_upload_sorts_while_edges_arrive(kind, m):
+    # Host edges without weights are sorted chunk by chunk as they land and the
+    # sorted chunks merged; the DSSS (both directions, degree-ordered ids and
+    # the on-chip structure) must equal the oracle's for every input kind.
+    import torch
+
+    n = 3001
+    rng = np.random.default_rng(m)
+    s = (rng.zipf(1.7, m) % n).astype(np.uint32)  # skewed, with duplicate edges
+    d = rng.integers(0, n, m).astype(np.uint32)
+    if kind == "pageable":
+        a, b = s, d
+    else:
+        a = torch.from_numpy(s.view(np.int32))
+        b = torch.from_numpy(d.view(np.int32))
+        a, b = (a.pin_memory(), b.pin_memory()) if kind == "pinned" else (a.cuda(), b.cuda())
+    for relabel in (False, True):
+        g = nx.Graph(a, b, n, 5, transpose=True, relabel=relabel, onchip=True)
+        if relabel:
+            old_of_new = g.relabel_map()
+            new_of_old = np.empty(n, np.uint32)
+            new_of_old[old_of_new] = np.arange(n, dtype=np.uint32)
+            ns, nd = new_of_old[s], new_of_old[d]
+        else:
+            ns, nd = s, d
+        order, off = oracle.dsss_order(n, 5, ns, nd)
+        gs, gd, goff = g.export()
+        assert (goff == off).all()
+        assert (gs == ns[order]).all() and (gd == nd[order]).all()
+        order_t, off_t = oracle.dsss_order(n, 5, nd, ns)
+        ts, td, toff = g.export(transpose=True)
+        assert (toff == off_t).all()
+        assert (ts == ns[order_t]).all() and (td == nd[order_t]).all()
+        assert g.info()["H_onchip"] == _onchip_hub_count(ns, nd)
+        ref = oracle.pagerank(n, s, d, 0.85, 10)
+        g.run("pr", 10)
+        assert_pr_close(g.values(), ref, f"{kind} relabel={relabel} PR")
+        g.run("pr", 10, "dpu_onchip")
+        assert_pr_close(g.values(), ref, f"{kind} relabel={relabel} on-chip PR")
+        g.run("wcc", 1000)
+        assert (g.values(dtype=np.uint32) == oracle.wcc(n, s, d)).all()
+        g.free()
+    # an id far beyond n is rejected, whatever the path
+    bad = s.copy()
+    bad[m // 2] = 0xFFFFFFF0
+    if kind == "pageable":
+        a = bad
+    else:
+        a = torch.from_numpy(bad.view(np.int32))
+        a = a.pin_memory() if kind == "pinned" else a.cuda()
+    with pytest.raises(nx.NxError) as e:
+        nx.Graph(a, b, n, 5, transpose=True, relabel=True)
+    assert e.value.code == nx.NX_ERR_INVALID_ARG
