@@ -563,11 +563,16 @@ nx_status radix_sort_u64(DevBuf& keys, DevBuf* vals, uint64_t n, uint32_t key_bi
 // path: a partition pass finds, for every output tile of MG_TILE keys, how
 // many of its predecessors come from the first run (a binary search along the
 // tile's cross diagonal); each block then stages its tile's inputs in shared
-// memory, each thread finds its own split there and merges MG_ITEMS keys, and
-// the block writes the tile out in order.
+// memory, each thread finds its own split there and merges MG_ITEMS keys
+// (keeping the two candidate keys in registers, so one shared load per key),
+// and the block writes the tile out in order. Shared memory holds one spare
+// slot per 16 keys, so the threads' strided stores of their MG_ITEMS results
+// (and the warps' linear reads) hit 16 distinct 8-byte bank pairs.
 constexpr int MG_THREADS = 256;
 constexpr int MG_ITEMS = 8;
 constexpr int MG_TILE = MG_THREADS * MG_ITEMS;  // 2048
+
+__device__ __forceinline__ uint32_t mg_pad(uint32_t x) { return x + (x >> 4); }
 
 // Keys of `a` among the first `diag` outputs.
 template <class I>
@@ -592,32 +597,48 @@ __global__ void __launch_bounds__(MG_THREADS) k_merge(const uint64_t* __restrict
                                                       const uint64_t* __restrict__ b, uint64_t nb,
                                                       const uint64_t* __restrict__ split,
                                                       uint64_t* __restrict__ out) {
-  __shared__ uint64_t sm[MG_TILE];
+  __shared__ uint64_t sm[MG_TILE + MG_TILE / 16];
   const uint64_t k0 = (uint64_t)blockIdx.x * MG_TILE;
   const uint64_t k1 = std::min<uint64_t>(k0 + MG_TILE, na + nb);
   const uint64_t a0 = split[blockIdx.x], a1 = split[blockIdx.x + 1];
   const uint64_t b0 = k0 - a0, b1 = k1 - a1;
   const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0), cnt = la + lb;
-  for (uint32_t x = threadIdx.x; x < la; x += MG_THREADS) sm[x] = a[a0 + x];
-  for (uint32_t x = threadIdx.x; x < lb; x += MG_THREADS) sm[la + x] = b[b0 + x];
+  for (uint32_t x = threadIdx.x; x < la; x += MG_THREADS) sm[mg_pad(x)] = a[a0 + x];
+  for (uint32_t x = threadIdx.x; x < lb; x += MG_THREADS) sm[mg_pad(la + x)] = b[b0 + x];
   __syncthreads();
   const uint32_t diag = std::min<uint32_t>(threadIdx.x * MG_ITEMS, cnt);
-  uint32_t i = merge_split<uint32_t>(sm, la, sm + la, lb, diag), j = diag - i;
+  uint32_t i, j;
+  {  // this thread's split: binary search along its diagonal
+    uint32_t lo = diag > lb ? diag - lb : 0, hi = diag < la ? diag : la;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (sm[mg_pad(mid)] <= sm[mg_pad(la + diag - 1 - mid)]) lo = mid + 1;
+      else hi = mid;
+    }
+    i = lo;
+    j = diag - lo;
+  }
+  uint64_t va = i < la ? sm[mg_pad(i)] : 0ull, vb = j < lb ? sm[mg_pad(la + j)] : 0ull;
   uint64_t v[MG_ITEMS];
 #pragma unroll
   for (int q = 0; q < MG_ITEMS; ++q) {
-    const bool take_a = i < la && (j >= lb || sm[i] <= sm[la + j]);
-    const bool any = i < la || j < lb;
-    v[q] = any ? (take_a ? sm[i] : sm[la + j]) : 0ull;
-    i += (any && take_a) ? 1u : 0u;
-    j += (any && !take_a) ? 1u : 0u;
+    const bool take_a = i < la && (j >= lb || va <= vb);
+    v[q] = take_a ? va : vb;
+    i += take_a ? 1u : 0u;
+    j += take_a ? 0u : 1u;
+    // the next key of the run just taken (one shared load)
+    const uint32_t nx = take_a ? i : la + j;
+    const bool more = take_a ? i < la : j < lb;
+    const uint64_t y = more ? sm[mg_pad(nx)] : 0ull;
+    va = take_a ? y : va;
+    vb = take_a ? vb : y;
   }
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < MG_ITEMS; ++q)
-    if (diag + q < cnt) sm[diag + q] = v[q];
+    if (diag + q < cnt) sm[mg_pad(diag + q)] = v[q];
   __syncthreads();
-  for (uint32_t x = threadIdx.x; x < cnt; x += MG_THREADS) out[k0 + x] = sm[x];
+  for (uint32_t x = threadIdx.x; x < cnt; x += MG_THREADS) out[k0 + x] = sm[mg_pad(x)];
 }
 
 nx_status merge_u64(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb, uint64_t* out,
