@@ -99,17 +99,48 @@ struct KeyCodec {
 };
 
 // rename (nullable): internal id of each input id, applied on the fly. Ids
-// >= n (rejected by the build before the keys are used) read no map entry.
+// >= n read no map entry and raise *bad (nullable) instead; the build rejects
+// them before the keys are used.
 __global__ void k_make_keys(const uint32_t* __restrict__ s, const uint32_t* __restrict__ d,
                             uint64_t m, uint32_t n, KeyCodec kc, const uint32_t* __restrict__ rename,
-                            uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+                            uint64_t* __restrict__ keys, uint32_t* __restrict__ idx,
+                            uint32_t* __restrict__ bad) {
   uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  bool any = false;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
     uint32_t a = s[e], b = d[e];
+    any |= (a >= n) || (b >= n);
     a = a < n ? a : 0u;
     b = b < n ? b : 0u;
     keys[e] = rename ? kc.encode(rename[a], rename[b]) : kc.encode(a, b);
     if (idx) idx[e] = (uint32_t)e;
+  }
+  if (bad && __any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
+// In-degrees from sorted keys: each group of 32 keys adds the length of each
+// of its runs of equal destination to indeg (a destination's edges form one
+// run per sub-shard, cut at group boundaries).
+__global__ void k_indeg_from_keys(const uint64_t* __restrict__ keys, uint64_t m, KeyCodec kc,
+                                  uint32_t* __restrict__ indeg) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t ng = (m + 31) / 32;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nwarps) {
+    const uint64_t e = g * 32 + lane;
+    const bool valid = e < m;
+    uint32_t i = 0, j = 0, dv = 0, sl = 0;
+    if (valid) kc.decode(keys[e], &i, &j, &dv, &sl);
+    const uint32_t key = valid ? (j * kc.P + i) : 0xFFFFFFFFu;  // sub-shard: runs never span two
+    const uint32_t up_d = __shfl_up_sync(0xffffffffu, dv, 1), up_k = __shfl_up_sync(0xffffffffu, key, 1);
+    const uint32_t dn_d = __shfl_down_sync(0xffffffffu, dv, 1), dn_k = __shfl_down_sync(0xffffffffu, key, 1);
+    const bool head = valid && (lane == 0 || up_d != dv || up_k != key);
+    const bool tail = valid && (lane == 31 || dn_d != dv || dn_k != key || e + 1 == m);
+    const uint32_t tails = __ballot_sync(0xffffffffu, tail);
+    if (head) {
+      const uint32_t last = lane + __ffs(tails >> lane) - 1;  // this run's tail lane
+      atomicAdd(&indeg[dv], last - lane + 1);
+    }
   }
 }
 
@@ -308,7 +339,7 @@ nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geom
     if (wn) NX_TRY(idx.alloc(std::max<uint64_t>(m, 1) * sizeof(uint32_t)));
     if (m) {
       k_make_keys<<<grid_for(m), 256, 0, stream()>>>(s, d, m, geo.n, kc, rename, keys.as<uint64_t>(),
-                                                     wn ? idx.as<uint32_t>() : nullptr);
+                                                     wn ? idx.as<uint32_t>() : nullptr, nullptr);
       NX_LAUNCH_CHECK();
       NX_TRY(radix_sort_u64(keys, wn ? &idx : nullptr, m, key_bits));
     }
@@ -458,7 +489,8 @@ struct Upload {
 // landed, so NX_RELABEL's order is computed while dst arrives; each dst
 // chunk's keys (forward, and transpose when asked) are made in the new ids and
 // sorted as it lands, and only the merge of the sorted chunks is left once the
-// last chunk is in. The keys are the same as build_one's, so is their order.
+// last chunk is in (pairs of sorted chunks are merged while later ones
+// arrive). The keys are the same as build_one's, so is their order.
 nx_status upload_and_sort(nx_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t m,
                           uint32_t n, uint32_t P, bool relabel, bool want_t, uint32_t* hs,
                           uint32_t* hd, uint32_t* indeg, uint32_t* bad, DevBuf* sorted) {
@@ -512,27 +544,30 @@ nx_status upload_and_sort(nx_graph* g, const uint32_t* src, const uint32_t* dst,
   DevBuf scratch, counts;
   NX_TRY(scratch.alloc(chunk * sizeof(uint64_t)));
   NX_TRY(counts.alloc(radix_sort_count_words(chunk) * sizeof(uint32_t)));
-  std::vector<uint64_t> bounds{0};
+  RunMerger mg[2];
+  for (int k = 0; k < nk; ++k) NX_TRY(mg[k].init(sorted[k], m));
   for (int c = 0; c < nc; ++c) {
     range(c, &e0, &len);
     if (!queue_all) NX_TRY(copy(c, true));
     NX_CUDA(cudaStreamWaitEvent(stream(), up.copied[nc + c], 0));
-    k_check_count<<<grid_for(len), 256, 0, stream()>>>(hd + e0, len, n, indeg, bad);
-    NX_LAUNCH_CHECK();
     for (int k = 0; k < nk; ++k) {
       uint64_t* kk = sorted[k].as<uint64_t>() + e0;
       k_make_keys<<<grid_for(len), 256, 0, stream()>>>(k ? hd + e0 : hs + e0, k ? hs + e0 : hd + e0,
-                                                       len, n, kc, ren, kk, nullptr);
+                                                       len, n, kc, ren, kk, nullptr, k ? nullptr : bad);
       NX_LAUNCH_CHECK();
       bool in_b = false;
       NX_TRY(radix_sort_u64_raw(kk, scratch.as<uint64_t>(), nullptr, nullptr, counts.as<uint32_t>(),
                                 len, key_bits, &in_b));
       if (in_b)
         NX_CUDA(cudaMemcpyAsync(kk, scratch.p, len * sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream()));
+      NX_TRY(mg[k].push(e0, e0 + len));
     }
-    bounds.push_back(e0 + len);
   }
-  for (int k = 0; k < nk; ++k) NX_TRY(merge_runs_u64(sorted[k], bounds));  // synchronises
+  for (int k = 0; k < nk; ++k) NX_TRY(mg[k].finish());  // synchronises
+  // in-degrees (of the new ids) from the sorted keys: counting them as the
+  // dst chunks landed would have slowed every chunk by about a third
+  k_indeg_from_keys<<<grid_for(m), 256, 0, stream()>>>(sorted[0].as<uint64_t>(), m, kc, indeg);
+  NX_LAUNCH_CHECK();
   return NX_OK;
 }
 
@@ -649,12 +684,15 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   }
   if (flags & NX_RELABEL) {
     {  // degrees of the renamed ids: new vertex k is caller vertex old_of_new[k]
+      // (the presorted path counted the in-degrees in the new ids already)
       DevBuf od2 = std::move(od_new), id2;
-      NX_TRY(id2.alloc((uint64_t)n * 4));
       NX_TRY(gather_u32(g->old_of_new.as<uint32_t>(), g->outdeg.p, od2.p, n));
-      NX_TRY(gather_u32(g->old_of_new.as<uint32_t>(), indeg.p, id2.p, n));
       g->outdeg = std::move(od2);
-      indeg = std::move(id2);
+      if (!presorted) {
+        NX_TRY(id2.alloc((uint64_t)n * 4));
+        NX_TRY(gather_u32(g->old_of_new.as<uint32_t>(), indeg.p, id2.p, n));
+        indeg = std::move(id2);
+      }
     }
   }
   geo.P = P;

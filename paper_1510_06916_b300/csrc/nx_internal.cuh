@@ -171,10 +171,29 @@ nx_status radix_sort_u64(DevBuf& keys, DevBuf* vals, uint64_t n, uint32_t key_bi
 nx_status radix_sort_u64_raw(uint64_t* a, uint64_t* b, uint32_t* va, uint32_t* vb, uint32_t* counts,
                              uint64_t n, uint32_t key_bits, bool* in_b);
 uint64_t radix_sort_count_words(uint64_t n);
-// Stable merge (ties: the earlier run first) of the sorted runs
-// keys[bounds[r], bounds[r + 1]) into one sorted sequence, pairwise by merge
-// path; keys may be swapped with the scratch buffer as in radix_sort_u64.
-nx_status merge_runs_u64(DevBuf& keys, const std::vector<uint64_t>& bounds);
+// Stable merge (ties: the earlier run first) of sorted runs laid end to end in
+// `keys` into one sorted sequence, pairwise by merge path, stream-ordered.
+// Runs are pushed in order as they become sorted and neighbours of equal rank
+// are merged at once (a binary counter), so most of the merging overlaps the
+// work that produces the later runs; finish() merges the rest, leaving the
+// result in keys (possibly swapped with the scratch buffer, as in
+// radix_sort_u64) and synchronising the stream.
+struct RunMerger {
+  nx_status init(DevBuf& keys, uint64_t n);
+  nx_status push(uint64_t x0, uint64_t x1);  // keys[x0, x1) is sorted
+  nx_status finish();
+
+ private:
+  struct Run {
+    uint64_t x0, x1;
+    int level;
+    bool in_tmp;
+  };
+  nx_status merge_top();
+  DevBuf* keys = nullptr;
+  DevBuf tmp, split;
+  std::vector<Run> st;
+};
 // Smallest shared-memory carveout that keeps the occupancy of kernel `fn`
 // (`threads` per block, `smem` dynamic bytes); the rest of L1 caches loads.
 nx_status prefer_l1(const void* fn, int threads, size_t smem);

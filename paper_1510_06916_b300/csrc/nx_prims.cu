@@ -657,34 +657,41 @@ nx_status merge_u64(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t 
 
 uint64_t merge_split_words(uint64_t n) { return ceil_div(std::max<uint64_t>(n, 1), MG_TILE) + 2; }
 
-nx_status merge_runs_u64(DevBuf& keys, const std::vector<uint64_t>& bounds) {
-  if (bounds.size() <= 2) return NX_OK;  // one run (or none)
-  const uint64_t n = bounds.back();
-  DevBuf tmp, split;
+nx_status RunMerger::init(DevBuf& k, uint64_t n) {
+  keys = &k;
+  st.clear();
   NX_TRY(tmp.alloc(std::max<uint64_t>(n, 1) * sizeof(uint64_t)));
   NX_TRY(split.alloc(merge_split_words(n) * sizeof(uint64_t)));
-  std::vector<uint64_t> bd = bounds;
-  DevBuf* src = &keys;
-  DevBuf* dst = &tmp;
-  while (bd.size() > 2) {  // pairs of adjacent runs; an odd last run is copied
-    std::vector<uint64_t> nbd{0};
-    for (size_t r = 0; r + 1 < bd.size(); r += 2) {
-      const uint64_t x0 = bd[r], x1 = bd[r + 1];
-      const uint64_t x2 = (r + 2 < bd.size()) ? bd[r + 2] : x1;
-      if (x2 > x1) {
-        NX_TRY(merge_u64(src->as<uint64_t>() + x0, x1 - x0, src->as<uint64_t>() + x1, x2 - x1,
-                         dst->as<uint64_t>() + x0, split.as<uint64_t>()));
-      } else if (x1 > x0) {
-        NX_CUDA(cudaMemcpyAsync(dst->as<uint64_t>() + x0, src->as<uint64_t>() + x0, (x1 - x0) * 8,
-                                cudaMemcpyDeviceToDevice, stream()));
-      }
-      nbd.push_back(x2);
-    }
-    bd.swap(nbd);
-    std::swap(src, dst);
-  }
-  if (src != &keys) std::swap(keys, tmp);
-  NX_CUDA(cudaStreamSynchronize(stream()));  // tmp and split are freed on return
+  return NX_OK;
+}
+
+nx_status RunMerger::merge_top() {
+  const Run b = st.back();
+  st.pop_back();
+  const Run a = st.back();
+  st.pop_back();
+  DevBuf* bufs[2] = {keys, &tmp};
+  if (a.in_tmp != b.in_tmp)  // both inputs in one buffer, the output in the other
+    NX_CUDA(cudaMemcpyAsync(bufs[a.in_tmp]->as<uint64_t>() + b.x0, bufs[b.in_tmp]->as<uint64_t>() + b.x0,
+                            (b.x1 - b.x0) * sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream()));
+  const uint64_t* in = bufs[a.in_tmp]->as<uint64_t>();
+  uint64_t* out = bufs[!a.in_tmp]->as<uint64_t>();
+  NX_TRY(merge_u64(in + a.x0, a.x1 - a.x0, in + b.x0, b.x1 - b.x0, out + a.x0, split.as<uint64_t>()));
+  st.push_back(Run{a.x0, b.x1, std::max(a.level, b.level) + 1, !a.in_tmp});
+  return NX_OK;
+}
+
+nx_status RunMerger::push(uint64_t x0, uint64_t x1) {
+  if (x1 <= x0) return NX_OK;
+  st.push_back(Run{x0, x1, 0, false});
+  while (st.size() >= 2 && st[st.size() - 1].level == st[st.size() - 2].level) NX_TRY(merge_top());
+  return NX_OK;
+}
+
+nx_status RunMerger::finish() {
+  while (st.size() >= 2) NX_TRY(merge_top());
+  if (!st.empty() && st[0].in_tmp) std::swap(*keys, tmp);
+  NX_CUDA(cudaStreamSynchronize(stream()));  // the scratch is freed with the merger
   return NX_OK;
 }
 
