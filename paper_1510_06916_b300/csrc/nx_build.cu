@@ -28,16 +28,17 @@ namespace {
 // per vertex of shared memory.
 constexpr uint32_t kTileMaxCap = 2048;
 
-// Degree histogram of ids a[0..m) into h[0..n); ids >= n are counted nowhere
-// and raise *bad (the build reads it before anything indexes by an id).
+// Degree histogram of ids a[0..m) into h[0..n) (h nullable: the check only);
+// ids >= n are counted nowhere and raise *bad (the build reads it before
+// anything indexes by an id).
 __global__ void k_check_count(const uint32_t* __restrict__ a, uint64_t m, uint32_t n,
                               uint32_t* __restrict__ h, uint32_t* __restrict__ bad) {
   uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   bool any = false;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
     const uint32_t v = a[e];
-    if (v < n) atomicAdd(&h[v], 1u);
-    else any = true;
+    if (v >= n) any = true;
+    else if (h) atomicAdd(&h[v], 1u);
   }
   if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
 }
@@ -317,32 +318,44 @@ unsigned grid_for(uint64_t work, unsigned threads = 256) {
   return (unsigned)std::min<uint64_t>(b, cap);
 }
 
+// DSSS keys of (s, d) over the geometry's P, L, lb, sorted; with want_idx,
+// idx[k] is the input position of the k-th key. rename (nullable): applied to
+// s and d while the keys are made.
+nx_status sort_keys(const uint32_t* s, const uint32_t* d, uint64_t m, const Geometry& geo,
+                    const uint32_t* rename, bool want_idx, DevBuf& keys, DevBuf& idx) {
+  const KeyCodec kc{geo.P, geo.L, geo.lb};
+  const uint32_t key_bits = bits_for((uint64_t)geo.P * geo.P) + 2 * geo.lb;
+  if (key_bits > 64) return invalid("DSSS key does not fit 64 bits (n too large for P)");
+  NX_TRY(keys.alloc(std::max<uint64_t>(m, 1) * sizeof(uint64_t)));
+  if (want_idx) NX_TRY(idx.alloc(std::max<uint64_t>(m, 1) * sizeof(uint32_t)));
+  if (m) {
+    k_make_keys<<<grid_for(m), 256, 0, stream()>>>(s, d, m, geo.n, kc, rename, keys.as<uint64_t>(),
+                                                   want_idx ? idx.as<uint32_t>() : nullptr, nullptr);
+    NX_LAUNCH_CHECK();
+    NX_TRY(radix_sort_u64(keys, want_idx ? &idx : nullptr, m, key_bits));
+  }
+  return NX_OK;
+}
+
 // Builds one DSSS from (s, d) over the geometry; wn (nullable) are the
 // normalised weights in input order.
 // rename (nullable): applied to s and d while the keys are made.
-// sorted (nullable): the keys of (s, d), already sorted (taken over; no
-// weights).
+// sorted / sorted_idx (nullable): the keys of (s, d) already sorted, and with
+// weights their input positions (both taken over).
 nx_status build_one(const uint32_t* s, const uint32_t* d, uint64_t m, const Geometry& geo,
                     const uint64_t* vt, const float* wn, Dsss& out,
-                    const uint32_t* rename = nullptr, DevBuf* sorted = nullptr) {
+                    const uint32_t* rename = nullptr, DevBuf* sorted = nullptr,
+                    DevBuf* sorted_idx = nullptr) {
   out.m = m;
   const uint64_t npieces = (uint64_t)geo.P * geo.ntiles;
   KeyCodec kc{geo.P, geo.L, geo.lb};
-  const uint32_t key_bits = bits_for((uint64_t)geo.P * geo.P) + 2 * geo.lb;
-  if (key_bits > 64) return invalid("DSSS key does not fit 64 bits (n too large for P)");
   DevBuf keys, idx;
   if (sorted && sorted->p) {
-    if (wn) return invalid("build_one: presorted keys carry no weights");
+    if (wn && !(sorted_idx && sorted_idx->p)) return invalid("build_one: presorted keys without positions");
     keys = std::move(*sorted);
+    if (wn) idx = std::move(*sorted_idx);
   } else {
-    NX_TRY(keys.alloc(std::max<uint64_t>(m, 1) * sizeof(uint64_t)));
-    if (wn) NX_TRY(idx.alloc(std::max<uint64_t>(m, 1) * sizeof(uint32_t)));
-    if (m) {
-      k_make_keys<<<grid_for(m), 256, 0, stream()>>>(s, d, m, geo.n, kc, rename, keys.as<uint64_t>(),
-                                                     wn ? idx.as<uint32_t>() : nullptr, nullptr);
-      NX_LAUNCH_CHECK();
-      NX_TRY(radix_sort_u64(keys, wn ? &idx : nullptr, m, key_bits));
-    }
+    NX_TRY(sort_keys(s, d, m, geo, rename, wn != nullptr, keys, idx));
   }
   const uint64_t mpad = round_up(m, kEdgeAlign) + kEdgeAlign;
   NX_TRY(out.ew.alloc(mpad * sizeof(uint32_t)));
@@ -493,7 +506,7 @@ struct Upload {
 // arrive). The keys are the same as build_one's, so is their order.
 nx_status upload_and_sort(nx_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t m,
                           uint32_t n, uint32_t P, bool relabel, bool want_t, uint32_t* hs,
-                          uint32_t* hd, uint32_t* indeg, uint32_t* bad, DevBuf* sorted) {
+                          uint32_t* hd, uint32_t* bad, DevBuf* sorted) {
   const uint32_t L = (uint32_t)ceil_div(n, P), lb = bits_for(L);
   const KeyCodec kc{P, L, lb};
   const uint32_t key_bits = bits_for((uint64_t)P * P) + 2 * lb;
@@ -564,10 +577,6 @@ nx_status upload_and_sort(nx_graph* g, const uint32_t* src, const uint32_t* dst,
     }
   }
   for (int k = 0; k < nk; ++k) NX_TRY(mg[k].finish());  // synchronises
-  // in-degrees (of the new ids) from the sorted keys: counting them as the
-  // dst chunks landed would have slowed every chunk by about a third
-  k_indeg_from_keys<<<grid_for(m), 256, 0, stream()>>>(sorted[0].as<uint64_t>(), m, kc, indeg);
-  NX_LAUNCH_CHECK();
   return NX_OK;
 }
 
@@ -601,11 +610,12 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   NX_CUDA(cudaMemsetAsync(indeg.p, 0, (uint64_t)n * 4, stream()));
   NX_CUDA(cudaMemsetAsync(bad.p, 0, 4, stream()));
   // per range of edges: ids < n, and the degree histograms
+  // per range of edges: ids < n and the out-degrees (the in-degrees are
+  // counted from the sorted forward keys, in the ids the DSSS uses)
   auto scan_edges = [&](const uint32_t* s0, const uint32_t* d0, uint64_t len) -> nx_status {
     k_check_count<<<grid_for(len), 256, 0, stream()>>>(s0, len, n, g->outdeg.as<uint32_t>(),
                                                        bad.as<uint32_t>());
-    k_check_count<<<grid_for(len), 256, 0, stream()>>>(d0, len, n, indeg.as<uint32_t>(),
-                                                       bad.as<uint32_t>());
+    k_check_count<<<grid_for(len), 256, 0, stream()>>>(d0, len, n, nullptr, bad.as<uint32_t>());
     NX_LAUNCH_CHECK();
     return NX_OK;
   };
@@ -625,7 +635,7 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
     if (want_w) wp = dw.as<float>();
     if (presorted) {
       NX_TRY(upload_and_sort(g, src, dst, m, n, P, (flags & NX_RELABEL) != 0, want_t, ds.as<uint32_t>(),
-                             dd.as<uint32_t>(), indeg.as<uint32_t>(), bad.as<uint32_t>(), sorted));
+                             dd.as<uint32_t>(), bad.as<uint32_t>(), sorted));
     } else if (m) {
       constexpr int kChunks = 8;
       Upload up;
@@ -683,16 +693,10 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
     d = dout;
   }
   if (flags & NX_RELABEL) {
-    {  // degrees of the renamed ids: new vertex k is caller vertex old_of_new[k]
-      // (the presorted path counted the in-degrees in the new ids already)
-      DevBuf od2 = std::move(od_new), id2;
+    {  // out-degrees of the renamed ids: new vertex k is caller vertex old_of_new[k]
+      DevBuf od2 = std::move(od_new);
       NX_TRY(gather_u32(g->old_of_new.as<uint32_t>(), g->outdeg.p, od2.p, n));
       g->outdeg = std::move(od2);
-      if (!presorted) {
-        NX_TRY(id2.alloc((uint64_t)n * 4));
-        NX_TRY(gather_u32(g->old_of_new.as<uint32_t>(), indeg.p, id2.p, n));
-        indeg = std::move(id2);
-      }
     }
   }
   geo.P = P;
@@ -701,6 +705,18 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   const uint32_t cap_log2 = (flags >> 8) & 0xFu, edges_log2 = (flags >> 12) & 0x1Fu;
   const uint64_t cap = cap_log2 ? (1ull << cap_log2) : kTileMaxCap;
   geo.tile_max = (uint32_t)std::min<uint64_t>(cap, 1ull << (32 - geo.lb));
+  // the forward keys, sorted (host edges: already, as they arrived), give the
+  // in-degrees the tiles are cut by
+  DevBuf sorted_idx;
+  if (!presorted)
+    NX_TRY(sort_keys(s, d, m, geo, rename_in_keys ? g->new_of_old.as<uint32_t>() : nullptr, want_w,
+                     sorted[0], sorted_idx));
+  if (m) {
+    const KeyCodec kc{geo.P, geo.L, geo.lb};
+    k_indeg_from_keys<<<grid_for(m), 256, 0, stream()>>>(sorted[0].as<uint64_t>(), m, kc,
+                                                         indeg.as<uint32_t>());
+    NX_LAUNCH_CHECK();
+  }
   DevBuf vt;
   NX_TRY(build_geometry(g, indeg.as<uint32_t>(), want_t ? g->outdeg.as<uint32_t>() : nullptr,
                         want_t ? 2 * m : m, edges_log2, vt));
@@ -724,7 +740,7 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
     g->has_w = true;
   }
   NX_TRY(build_one(s, d, m, geo, vt.as<uint64_t>(), want_w ? wn.as<float>() : nullptr, g->fwd,
-                   rename_in_keys ? g->new_of_old.as<uint32_t>() : nullptr, &sorted[0]));
+                   rename_in_keys ? g->new_of_old.as<uint32_t>() : nullptr, &sorted[0], &sorted_idx));
   if (flags & NX_ONCHIP_HUBS) NX_TRY(build_onchip(g, s, d, m));
   if (want_t) {
     NX_TRY(build_one(d, s, m, geo, vt.as<uint64_t>(), want_w ? wn.as<float>() : nullptr,
