@@ -1005,7 +1005,9 @@ def test_relabel_rejected_where_unsupported():
         plain.relabel_map()
 
 
-@pytest.mark.parametrize("m", [8200, 100_000])  # 5 (odd) and 8 sorted chunks to merge
+# 3, 7, 5 and 8 sorted chunks to merge: the first two leave runs of unequal
+# rank in different buffers at the end (the copy before the merge)
+@pytest.mark.parametrize("m", [3000, 7000, 8200, 100_000])
 @pytest.mark.parametrize("kind", ["pageable", "pinned", "device"])
 def test_host_upload_sorts_while_edges_arrive(kind, m):
     # Host edges without weights are sorted chunk by chunk as they land and the
