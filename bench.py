@@ -386,6 +386,34 @@ def measure_strategies(nx, inputs, torch, scale=22, seed=2, P=16):
     return out
 
 
+def host_link_gbs(torch, nbytes=1 << 30, reps=5):
+    """Measured host->device bandwidth of one pinned 1 GB copy (median of 5): the
+    roofline of the bytes a budgeted run streams over the host link."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    d.copy_(h, non_blocking=True)
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        d.copy_(h, non_blocking=True)
+        e1.record(s)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    del h, d
+    return nbytes / (sorted(ts)[reps // 2] / 1e3) / 1e9
+
+
+def link_roofline(st, link_gbs):
+    """Host-link bytes of a run over its time, against the measured link bandwidth."""
+    b = st["h2d_bytes"] + st["d2h_bytes"]
+    if not st["h2d_bytes"] or not st["ms"]:  # nothing streamed (activity flags only)
+        return None
+    gbs = b / (st["ms"] / 1e3) / 1e9
+    return {"link_gbs": gbs, "link_frac": gbs / link_gbs}
+
+
 def measure_budget_sweep(nx, inputs, torch, scale=22, seed=2, P=16, iters=10):
     """Exp 4: PageRank x10 on the scale-22 graph as the device budget shrinks.
 
@@ -405,8 +433,9 @@ def measure_budget_sweep(nx, inputs, torch, scale=22, seed=2, P=16, iters=10):
     points += [(f"{f:g}F", int(f * full)) for f in (0.75, 0.5, 0.25)]
     points += [("2nBa", vert + 1)]
     points += [(f"Q={q}", q * vert // P + 1) for q in (P * 3 // 4, P // 2, P // 4, 1)]
+    link = host_link_gbs(torch)
     out = {"workload": f"R-MAT scale {scale} ef 16 seed {seed}, P={P}, PageRank x{iters}",
-           "F_bytes": full, "points": []}
+           "F_bytes": full, "host_link_gbs": link, "points": []}
     for label, budget in points:
         g.run("pr", iters, "auto", budget=budget)
         st = g.run("pr", iters, "auto", budget=budget)
@@ -419,6 +448,7 @@ def measure_budget_sweep(nx, inputs, torch, scale=22, seed=2, P=16, iters=10):
             "budget": label, "bytes": budget, "strategy": strat.upper(),
             "Q": st["Q"], "streamed_cols": st["streamed_cols"], "ms_per_iter": st["ms"] / iters,
             "link_bytes_per_iter": (st["h2d_bytes"] + st["d2h_bytes"]) / iters,
+            "link": link_roofline(st, link),
             "model_bytes_per_iter": rd + wr, "model_link_bytes_per_iter": model_link, "model_Q": Q})
     g.free()
     torch.cuda.empty_cache()
@@ -487,12 +517,16 @@ def measure_rmat26_programs(nx, inputs, torch, budget=6 * 10**9):
     g = nx.Graph(src, dst, n, w["P"], transpose=True, relabel=True)
     del src, dst
     torch.cuda.empty_cache()
-    out = {"workload": workload_name(w, "rmat26") + ", with transpose", "budget_bytes": budget}
+    link = host_link_gbs(torch)
+    out = {"workload": workload_name(w, "rmat26") + ", with transpose", "budget_bytes": budget,
+           "host_link_gbs": link}
 
     def rec(st):
         return {"ms": st["ms"], "sweeps": st["iters_done"], "edges_swept": st["edges_swept"],
+                "intervals_skipped": st["intervals_skipped"],
                 "gteps_swept": st["edges_swept"] / (st["ms"] / 1e3) / 1e9 if st["ms"] else None,
-                "host_to_device_bytes": st["h2d_bytes"], "streamed_cols": st["streamed_cols"]}
+                "host_to_device_bytes": st["h2d_bytes"], "streamed_cols": st["streamed_cols"],
+                "link": link_roofline(st, link)}
 
     for prog, it in (("bfs", 1000), ("wcc", 1000)):
         g.run(prog, it, "spu")
@@ -505,6 +539,7 @@ def measure_rmat26_programs(nx, inputs, torch, budget=6 * 10**9):
     torch.cuda.empty_cache()
     for k in ("spu_bfs", "spu_wcc", "mpu6gb_pr", "mpu6gb_bfs", "mpu6gb_wcc"):
         out[k + "_ms"] = out[k]["ms"]
+    out["mpu6gb_wcc_link_frac"] = (out["mpu6gb_wcc"]["link"] or {}).get("link_frac")
     return out
 
 
@@ -676,7 +711,8 @@ def compact(extras):
         "adjoint": ("adjoint_gteps", "forward_gteps", "adjoint_over_forward"),
         "multi_graph": ("gteps", "multi_ms", "separate_runs_kernel_ms"),
         "autotune": ("best_P", "best_tile_cap", "best_tile_edges", "scale26"),
-        "rmat26_programs": ("spu_bfs_ms", "spu_wcc_ms", "mpu6gb_pr_ms", "mpu6gb_bfs_ms", "mpu6gb_wcc_ms"),
+        "rmat26_programs": ("spu_bfs_ms", "spu_wcc_ms", "mpu6gb_pr_ms", "mpu6gb_bfs_ms", "mpu6gb_wcc_ms",
+                            "mpu6gb_wcc_link_frac", "host_link_gbs"),
         "strategies": ("spu_pr_ms", "dpu_pr_ms", "mpu_pr_ms", "dpu_over_spu_pr",
                        "src_coarse_over_spu_pr", "src_fine_over_spu_pr"),
         "relabel": ("relabel_over_ids",),

@@ -132,7 +132,9 @@ typedef struct {
   uint64_t h2d_bytes;     /* host->device bytes of the loop (streaming)         */
   uint64_t d2h_bytes;     /* device->host bytes of the loop                     */
   uint32_t launches;      /* kernels launched by the loop                       */
-  uint32_t pad_;
+  uint32_t intervals_skipped; /* BFS / WCC under SPU, DPU, MPU: source intervals
+                             skipped as inactive, summed over the sweeps (each
+                             skips its sub-shards SS_i*, Algorithm 1); else 0  */
 } nx_run_stats;
 
 typedef struct {

@@ -1234,7 +1234,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   NX_TRY(ev.create());
   Scal sc = scal_of(g);
   uint64_t swept = 0;
-  uint32_t done = 0;
+  uint32_t done = 0, skipped = 0;
   // activity: [0] = active-interval count, [1 + i] = flag of interval i (pinned)
   if (g->hact.bytes < ((size_t)P + 1) * 4) NX_TRY(g->hact.alloc(((size_t)P + 1) * 4));
   uint32_t* hact = g->hact.as<uint32_t>();
@@ -1249,8 +1249,10 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   }
   NX_CUDA(cudaEventRecord(ev.e0, stream()));
   for (uint32_t it = 0; it < iters; ++it) {
-    for (uint32_t i = 0; i < P; ++i)
+    for (uint32_t i = 0; i < P; ++i) {
       if (act_h[i]) swept += row_edges[i];
+      else ++skipped;
+    }
     if (strat == NX_SPU && !streaming && nbands == 1) {
       NX_TRY(spu_iteration(g, prog, a, n_a));
       ++c.launches;
@@ -1296,6 +1298,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     st->streamed_cols = streaming ? P - c.Jc : 0;
     st->ms = ms;
     st->edges_swept = swept;
+    st->intervals_skipped = skipped;
     st->bytes_model = bytes_per_sweep(g, prog, 0) * done + 4 * swept + (prog == NX_WPR ? 4 * swept : 0);
     if (strat == NX_DPU && !staged) st->bytes_model += (uint64_t)done * 3 * 4 * g->fwd.D;
     st->h2d_bytes = c.h2d;

@@ -46,10 +46,10 @@ class NxRunStats(ctypes.Structure):
                 ("ms", ctypes.c_float), ("edges_swept", ctypes.c_uint64),
                 ("bytes_model", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64),
                 ("d2h_bytes", ctypes.c_uint64), ("launches", ctypes.c_uint32),
-                ("pad_", ctypes.c_uint32)]
+                ("intervals_skipped", ctypes.c_uint32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class NxShape(ctypes.Structure):

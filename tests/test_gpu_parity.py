@@ -87,6 +87,27 @@ def test_bfs_max_depth_is_algorithm4_output():
     g.free()
 
 
+@pytest.mark.parametrize("strategy", ["spu", "dpu", "mpu"])
+def test_inactive_intervals_are_skipped_and_counted(strategy):
+    # Edges only inside interval 0 of P = 4: a BFS from vertex 0 never
+    # activates intervals 1-3, so every sweep skips them (Algorithm 1) and
+    # reads interval 0's edges alone.
+    n, P = 4096, 4
+    L = n // P
+    rng = np.random.default_rng(5)
+    s = rng.integers(0, L, 20000).astype(np.uint32)
+    d = rng.integers(0, L, 20000).astype(np.uint32)
+    g = nx.Graph(s, d, n, P, transpose=True)
+    budget = 2 * n * 4 * 2 // P + 1 if strategy == "mpu" else 0  # Q = 2
+    st = g.run("bfs", 1000, strategy, budget=budget, root=0)
+    assert (g.values(dtype=np.uint32) == oracle.bfs(n, s, d, 0)).all()
+    assert st["intervals_skipped"] == 3 * st["iters_done"]
+    assert st["edges_swept"] == len(s) * st["iters_done"]
+    st = g.run("pr", 5, strategy, budget=budget)
+    assert st["intervals_skipped"] == 0 and st["edges_swept"] == 5 * len(s)
+    g.free()
+
+
 # ------------------------------------------------- on-chip double-phase update
 
 def _onchip_hub_count(s, d):
