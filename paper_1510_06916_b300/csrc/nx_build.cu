@@ -483,6 +483,9 @@ struct Upload {
   cudaEvent_t ready = nullptr;
   std::vector<cudaEvent_t> copied;
   ~Upload() {
+    // copies still in flight (an early error return) must land before the
+    // buffers they write are freed on the main stream
+    if (side) cudaStreamSynchronize(side);
     for (cudaEvent_t e : copied)
       if (e) cudaEventDestroy(e);
     if (ready) cudaEventDestroy(ready);
