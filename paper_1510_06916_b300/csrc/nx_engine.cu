@@ -579,6 +579,7 @@ struct Streamer {
   cudaStream_t side = nullptr;
   cudaEvent_t copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
   ~Streamer() {
+    if (side) cudaStreamSynchronize(side);  // no copy outlives the run (early error returns)
     for (int k = 0; k < 2; ++k) {
       if (copied[k]) cudaEventDestroy(copied[k]);
       if (used[k]) cudaEventDestroy(used[k]);
@@ -715,6 +716,7 @@ struct Staged {
   cudaEvent_t row_in[2] = {}, row_used[2] = {}, col_in[2] = {}, col_done[2] = {}, col_out[2] = {};
   uint32_t nrow = 0, ncol = 0;  // buffers handed out so far (parity picks the buffer)
   ~Staged() {
+    if (side) cudaStreamSynchronize(side);  // no copy outlives the run (early error returns)
     for (cudaEvent_t* e : {row_in, row_used, col_in, col_done, col_out})
       for (int k = 0; k < 2; ++k)
         if (e[k]) cudaEventDestroy(e[k]);
