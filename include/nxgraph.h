@@ -179,7 +179,12 @@ void nx_last_error(char* buf, size_t len);
  *   m, n, P  : edges, vertices (1 <= n <= 2^30), intervals (1 <= P <= min(n, 1024))
  *   w        : edge weights [m] (> 0) when NX_WITH_WEIGHTS, else ignored
  *   out      : receives the new graph (caller frees with nx_graph_free)
- * Input arrays are copied; the caller keeps ownership.
+ * Input arrays are copied; the caller keeps ownership. Host edges without
+ * weights are sorted chunk by chunk while they cross the host link (all source
+ * chunks first, then the destination chunks) and the sorted chunks merged;
+ * from page-locked (pinned) host memory every copy is queued at once, from
+ * pageable memory each chunk is staged by the calling thread in turn. The
+ * result does not depend on the path taken.
  * NX_RELABEL renames the vertices before sharding: internal id k is the
  * caller vertex with the k-th largest out-degree (ties by caller id), so
  * heavily read source values cluster. No vertex is dropped and n is kept.
