@@ -133,3 +133,31 @@ def test_scc_is_a_program_of_the_abi():
     assert nx.PROGRAMS["scc"] == nx.SCC == 5
     text = open(HDR).read()
     assert "NX_SCC = 5" in text
+
+
+@pytest.mark.parametrize("ctype,cname", [
+    ("NxParams", "nx_params"), ("NxRunStats", "nx_run_stats"), ("NxGraphInfo", "nx_graph_info"),
+    ("NxShape", "nx_shape"), ("NxBatchShape", "nx_batch_shape")])
+def test_binding_structs_match_the_header_layout(ctype, cname, tmp_path):
+    # sizeof and offsetof of every field, from a C program built against the
+    # public header, equal the ctypes structures the binding passes by pointer
+    import ctypes
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    st = getattr(nx, ctype)
+    fields = [f for f, _ in st._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text(
+        "#include <stdio.h>\n#include <stddef.h>\n#include \"nxgraph.h\"\nint main(void) {\n"
+        f"  printf(\"%zu\\n\", sizeof({cname}));\n"
+        + "".join(f"  printf(\"%zu\\n\", offsetof({cname}, {f}));\n" for f in fields)
+        + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HDR), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(st)
+    assert out[1:] == [getattr(st, f).offset for f in fields]
