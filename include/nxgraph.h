@@ -170,6 +170,15 @@ nx_status nx_trim_memory(void);
 /* Copies the last error message of this thread into buf (always terminated). */
 void nx_last_error(char* buf, size_t len);
 
+/* Test hook for the error paths: the library's device allocation made `after`
+ * allocations from now (0: the next one) fails as if the device were out of
+ * memory, so the call that made it returns NX_ERR_OOM (nx_last_error says the
+ * failure was injected). A negative `after` disarms the hook; it disarms
+ * itself once it fires. The countdown is process-wide and counts the
+ * library's own device allocations only. A graph whose call failed stays
+ * valid: a later call may use or free it. Always NX_OK. */
+nx_status nx_debug_fail_alloc(int64_t after);
+
 /*
  * Builds the DSSS of Section II-A / III-A on the device: equal intervals of
  * L = ceil(n/P) vertices, P*P sub-shards sorted by (destination, source), the

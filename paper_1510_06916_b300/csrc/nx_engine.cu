@@ -1113,9 +1113,9 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   const int key = (((int)strat * 16 + (int)c.ds.size()) * 4096 + (int)(staged ? Q + 1 : 0) +
                    (streaming ? (int)(c.Jc + 2048) : 0)) * 2048 + (int)(nbands > 1 ? band : 0);
   auto& slot_plan = g->plans[key];
-  if (!slot_plan) {
-    slot_plan.reset(new nx_graph::Plan());
-    nx_graph::Plan& pl = *slot_plan;
+  if (!slot_plan) {  // built aside and cached only once complete (a failed call caches nothing)
+    std::unique_ptr<nx_graph::Plan> fresh(new nx_graph::Plan());
+    nx_graph::Plan& pl = *fresh;
     const uint64_t total = g->m * c.ds.size();
     const uint64_t blk = target_block_edges(total);
     PlanOut plan;
@@ -1164,6 +1164,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
     pl.na = n_a;
     pl.nb = n_b;
     pl.off = launch_off;
+    slot_plan = std::move(fresh);
   }
   nx_graph::Plan& pl = *slot_plan;
   NX_TRY(ensure_split(g, pl.slots));
@@ -1322,13 +1323,14 @@ nx_status probe_impl(nx_graph* g, uint32_t sweeps, float* ms_per_sweep) {
   // one launch over all sources, as the SPU run's default
   const int key = (((int)NX_SPU * 16 + 1) * 4096) * 2048;
   auto& slot = g->plans[key];
-  if (!slot) {
-    slot.reset(new nx_graph::Plan());
+  if (!slot) {  // cached only once complete
+    std::unique_ptr<nx_graph::Plan> fresh(new nx_graph::Plan());
     PlanOut plan;
     std::vector<const Dsss*> ds{&g->fwd};
     plan_tiles(g, ds, 0, P, 0, P, true, target_block_edges(g->m), plan);
-    NX_TRY(upload_items(g, plan, *slot));
-    slot->na = (uint32_t)slot->h_items.size();
+    NX_TRY(upload_items(g, plan, *fresh));
+    fresh->na = (uint32_t)fresh->h_items.size();
+    slot = std::move(fresh);
   }
   NX_TRY(ensure_split(g, slot->slots));
   nx_params p{};
@@ -1404,13 +1406,14 @@ constexpr int kTrPlanKey = -7;  // plan over the transpose DSSS (adjoint, SCC)
 
 nx_status tr_plan(nx_graph* g, nx_graph::Plan** out) {
   auto& slot = g->plans[kTrPlanKey];
-  if (!slot) {
-    slot.reset(new nx_graph::Plan());
+  if (!slot) {  // cached only once complete
+    std::unique_ptr<nx_graph::Plan> fresh(new nx_graph::Plan());
     PlanOut plan;
     std::vector<const Dsss*> ds{&g->tr};
     plan_tiles(g, ds, 0, g->geo.P, 0, g->geo.P, true, target_block_edges(g->m), plan);
-    NX_TRY(upload_items(g, plan, *slot));
-    slot->na = (uint32_t)slot->h_items.size();
+    NX_TRY(upload_items(g, plan, *fresh));
+    fresh->na = (uint32_t)fresh->h_items.size();
+    slot = std::move(fresh);
   }
   NX_TRY(ensure_split(g, slot->slots));
   *out = slot.get();
@@ -1427,13 +1430,14 @@ nx_status scc_impl(nx_graph* g, uint32_t max_sweeps, nx_run_stats* st) {
   // plans: tiles over the forward DSSS and over the transpose
   const int fkey = ((int)NX_SPU * 16 + 1) * 4096 * 2048;
   auto& fslot = g->plans[fkey];
-  if (!fslot) {
-    fslot.reset(new nx_graph::Plan());
+  if (!fslot) {  // cached only once complete
+    std::unique_ptr<nx_graph::Plan> fresh(new nx_graph::Plan());
     PlanOut plan;
     std::vector<const Dsss*> ds{&g->fwd};
     plan_tiles(g, ds, 0, P, 0, P, true, target_block_edges(g->m), plan);
-    NX_TRY(upload_items(g, plan, *fslot));
-    fslot->na = (uint32_t)fslot->h_items.size();
+    NX_TRY(upload_items(g, plan, *fresh));
+    fresh->na = (uint32_t)fresh->h_items.size();
+    fslot = std::move(fresh);
   }
   NX_TRY(ensure_split(g, fslot->slots));
   nx_graph::Plan* tpl = nullptr;
@@ -1745,12 +1749,13 @@ nx_status multi_impl(nx_graph** gs, uint32_t count, nx_program prog, float alpha
     if (prog == NX_WCC) ds.push_back(&g->tr);
     const int key = ((int)NX_SPU * 16 + (int)ds.size()) * 4096;
     auto& slot = g->plans[key];
-    if (!slot) {
-      slot.reset(new nx_graph::Plan());
+    if (!slot) {  // cached only once complete
+      std::unique_ptr<nx_graph::Plan> fresh(new nx_graph::Plan());
       PlanOut plan;
       plan_tiles(g, ds, 0, g->geo.P, 0, g->geo.P, true, target_block_edges(g->m * ds.size()), plan);
-      NX_TRY(upload_items(g, plan, *slot));
-      slot->na = (uint32_t)slot->h_items.size();
+      NX_TRY(upload_items(g, plan, *fresh));
+      fresh->na = (uint32_t)fresh->h_items.size();
+      slot = std::move(fresh);
     }
     NX_TRY(ensure_split(g, slot->slots));
     SweepArgs a = base_args(g, prog, p, nullptr);

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "nx_internal.cuh"
@@ -92,9 +93,17 @@ void DevBuf::release() {
   p = nullptr;
   bytes = 0;
 }
+// nx_debug_fail_alloc: allocations left before the injected failure (-1: off)
+static std::atomic<long long> g_fail_after{-1};
+
 nx_status DevBuf::alloc(size_t n) {
   release();
   if (n == 0) return NX_OK;
+  if (g_fail_after.load() >= 0 && g_fail_after.fetch_sub(1) == 0) {
+    g_fail_after.store(-1);
+    set_error("device allocation failed: injected by nx_debug_fail_alloc");
+    return NX_ERR_OOM;
+  }
   cudaMemPool_t pool = nullptr;
   cudaError_t e = pool_of_current_device(&pool);
   pooled = (e == cudaSuccess);
@@ -696,6 +705,11 @@ nx_status RunMerger::finish() {
 }
 
 }  // namespace nx
+
+extern "C" nx_status nx_debug_fail_alloc(int64_t after) {
+  nx::g_fail_after.store(after < 0 ? -1 : (long long)after);
+  return NX_OK;
+}
 
 extern "C" nx_status nx_set_stream(void* s) {
   nx::g_stream = (cudaStream_t)s;

@@ -26,7 +26,7 @@ STRATEGIES = {"spu": SPU, "dpu": DPU, "mpu": MPU, "auto": AUTO,
               "src_coarse": SRC_COARSE, "src_fine": SRC_FINE, "dpu_onchip": DPU_ONCHIP}
 
 EXPORTS = [
-    "nx_set_stream", "nx_trim_memory", "nx_last_error", "nx_build_dsss", "nx_graph_get_info", "nx_run",
+    "nx_set_stream", "nx_trim_memory", "nx_debug_fail_alloc", "nx_last_error", "nx_build_dsss", "nx_graph_get_info", "nx_run",
     "nx_get_values", "nx_set_values", "nx_run_ppr_batch", "nx_adjoint_wpr", "nx_run_multi",
     "nx_graph_free", "nx_io_model", "nx_dsss_export", "nx_pagerank_step_noalloc",
     "nx_autotune", "nx_get_relabel", "nx_bfs_max_depth", "nx_set_barrier_limit",
@@ -90,6 +90,7 @@ def lib():
         d = ctypes.c_double
         L.nx_set_stream.argtypes = [vp]
         L.nx_trim_memory.argtypes = []
+        L.nx_debug_fail_alloc.argtypes = [ctypes.c_int64]
         L.nx_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         L.nx_last_error.restype = None
         L.nx_build_dsss.argtypes = [vp, vp, u64, u32, u32, u32, vp, ctypes.POINTER(vp)]
@@ -173,6 +174,12 @@ def set_stream(stream) -> None:
 def trim_memory() -> None:
     """Returns the library's cached, unused device memory to the driver."""
     check(lib().nx_trim_memory())
+
+
+def debug_fail_alloc(after: int) -> None:
+    """Test hook: the library's device allocation `after` allocations from now
+    fails as out of memory (NX_ERR_OOM); a negative value disarms it."""
+    check(lib().nx_debug_fail_alloc(int(after)))
 
 
 def set_barrier_limit(cycles: int) -> None:

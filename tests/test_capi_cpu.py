@@ -161,3 +161,9 @@ def test_binding_structs_match_the_header_layout(ctype, cname, tmp_path):
                                           check=True).stdout.split()]
     assert out[0] == ctypes.sizeof(st)
     assert out[1:] == [getattr(st, f).offset for f in fields]
+
+
+def test_fault_injection_hook_arms_and_disarms_without_a_device():
+    nx.debug_fail_alloc(3)
+    nx.debug_fail_alloc(-1)
+    nx.debug_fail_alloc(-7)  # any negative value disarms

@@ -1083,3 +1083,53 @@ def test_host_upload_sorts_while_edges_arrive(kind, m):
     with pytest.raises(nx.NxError) as e:
         nx.Graph(a, b, n, 5, transpose=True, relabel=True)
     assert e.value.code == nx.NX_ERR_INVALID_ARG
+
+
+def test_injected_allocation_failures_leave_the_library_usable():
+    # Host-side fault injection: every device allocation of a build and of its
+    # runs fails in turn (SPU, SPU with streamed shards, MPU with staged
+    # intervals, DPU). The failing call returns NX_ERR_OOM and says so; the
+    # graph, when it exists, stays usable (the same runs repeated match the
+    # oracle), and so does the library.
+    import torch
+
+    n = 1 << 12
+    s, d, _ = rmat(12, 16, 21)
+    m = len(s)
+    ref = oracle.pagerank(n, s, d, 0.85, 5)
+    wcc = oracle.wcc(n, s, d)
+    hs = torch.from_numpy(s.view(np.int32)).pin_memory()
+    hd = torch.from_numpy(d.view(np.int32)).pin_memory()
+    runs = [("pr", 5, "spu", 0), ("pr", 5, "spu", 2 * n * 4 + 4 * m // 3),
+            ("wcc", 100, "mpu", n * 4 + 1), ("pr", 5, "dpu", 0)]  # MPU: Q = 2 of P = 4
+    k, failures, in_runs = 0, 0, 0
+    while True:
+        nx.debug_fail_alloc(k)
+        g = None
+        try:
+            g = nx.Graph(hs, hd, n, 4, transpose=True, relabel=True)
+            for prog, it, strat, budget in runs:
+                g.run(prog, it, strat, budget=budget)
+            nx.debug_fail_alloc(-1)
+            g.free()
+            break
+        except nx.NxError as e:
+            nx.debug_fail_alloc(-1)
+            assert e.code == nx.NX_ERR_OOM and "injected" in str(e), (k, e)
+            failures += 1
+            if g is not None:
+                in_runs += 1
+                for prog, it, strat, budget in runs:
+                    g.run(prog, it, strat, budget=budget)
+                    if prog == "pr":
+                        assert_pr_close(g.values(), ref, f"{strat} after failure {k}")
+                    else:
+                        assert (g.values(dtype=np.uint32) == wcc).all(), k
+                g.free()
+        k += 1
+        assert k < 2000
+    assert failures >= 20 and in_runs >= 10, (failures, in_runs)
+    g = nx.Graph(s, d, n, 4, transpose=True)
+    g.run("pr", 5)
+    assert_pr_close(g.values(), ref, "a fresh build after the failures")
+    g.free()
