@@ -525,6 +525,7 @@ extern "C" nx_status nx_run_ppr_batch(nx_graph* g, const float* teleport, uint32
   if (B == 0 || B > 64) return nx::invalid("nx_run_ppr_batch: B must be in [1, 64]");
   if (!(alpha >= 0.f && alpha < 1.f)) return nx::invalid("nx_run_ppr_batch: alpha must be in [0, 1)");
   if (g->geo.P > 1024) return nx::invalid("nx_run_ppr_batch: P too large");
+  nx::TraceRange trace("nx_run_ppr_batch");
   NX_TRY(nx::ensure_resident(g));
   return nx::ppr_batch_impl(g, teleport, B, iters, alpha, ranks, ptrs_are_device, stats);
 }

@@ -637,6 +637,7 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
     d = dd.as<uint32_t>();
     if (want_w) wp = dw.as<float>();
     if (presorted) {
+      TraceRange tr("upload and sort");
       NX_TRY(upload_and_sort(g, src, dst, m, n, P, (flags & NX_RELABEL) != 0, want_t, ds.as<uint32_t>(),
                              dd.as<uint32_t>(), bad.as<uint32_t>(), sorted));
     } else if (m) {
@@ -711,6 +712,7 @@ nx_status build_impl(const uint32_t* src, const uint32_t* dst, uint64_t m, uint3
   // the forward keys, sorted (host edges: already, as they arrived), give the
   // in-degrees the tiles are cut by
   DevBuf sorted_idx;
+  TraceRange tr_rest("keys, geometry, words");
   if (!presorted)
     NX_TRY(sort_keys(s, d, m, geo, rename_in_keys ? g->new_of_old.as<uint32_t>() : nullptr, want_w,
                      sorted[0], sorted_idx));
@@ -815,6 +817,7 @@ extern "C" nx_status nx_build_dsss(const uint32_t* src, const uint32_t* dst, uin
   }
   if ((flags & NX_WITH_WEIGHTS) && m && !w)
     return nx::invalid("nx_build_dsss: NX_WITH_WEIGHTS needs w");
+  nx::TraceRange trace("nx_build_dsss");
   nx_graph* g = new (std::nothrow) nx_graph();
   if (!g) return nx::invalid("nx_build_dsss: out of host memory");
   nx_status st = nx::build_impl(src, dst, m, n, P, flags, w, g);

@@ -1114,6 +1114,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
                    (streaming ? (int)(c.Jc + 2048) : 0)) * 2048 + (int)(nbands > 1 ? band : 0);
   auto& slot_plan = g->plans[key];
   if (!slot_plan) {  // built aside and cached only once complete (a failed call caches nothing)
+    TraceRange trace_plan("plan");
     std::unique_ptr<nx_graph::Plan> fresh(new nx_graph::Plan());
     nx_graph::Plan& pl = *fresh;
     const uint64_t total = g->m * c.ds.size();
@@ -1236,6 +1237,7 @@ nx_status run_impl(nx_graph* g, nx_program prog, const nx_params& p, uint32_t it
   EventPair ev;
   NX_TRY(ev.create());
   Scal sc = scal_of(g);
+  TraceRange trace_loop("iterations");
   uint64_t swept = 0;
   uint32_t done = 0, skipped = 0;
   // activity: [0] = active-interval count, [1 + i] = flag of interval i (pinned)
@@ -1945,6 +1947,7 @@ extern "C" nx_status nx_run(nx_graph* g, nx_program program, const nx_params* pa
                             nx_run_stats* stats) {
   if (!g) return nx::invalid("nx_run: graph is NULL");
   if ((int)program < 0 || (int)program > 5) return nx::invalid("nx_run: unknown program");
+  nx::TraceRange trace("nx_run");
   if ((int)strategy < 0 || (int)strategy > 6) return nx::invalid("nx_run: unknown strategy");
   if (program == NX_SCC) {
     if (!g->has_tr) return nx::invalid("nx_run: SCC needs the transpose DSSS (NX_WITH_TRANSPOSE)");
@@ -1973,6 +1976,7 @@ extern "C" nx_status nx_adjoint_wpr(nx_graph* g, const float* grad_r, uint32_t a
   if (g->last_prog != NX_WPR)
     return nx::invalid("nx_adjoint_wpr: run NX_WPR first (its ranks are the forward state)");
   if (adj_terms == 0) return nx::invalid("nx_adjoint_wpr: adj_terms must be >= 1");
+  nx::TraceRange trace("nx_adjoint_wpr");
   NX_TRY(nx::ensure_resident(g));
   return nx::adjoint_impl(g, grad_r, adj_terms, grad_w, grad_t, ptrs_are_device, stats);
 }
@@ -1993,6 +1997,7 @@ extern "C" nx_status nx_run_multi(nx_graph** graphs, uint32_t count, nx_program 
     if (program == NX_WPR && !g->has_w) return nx::invalid("nx_run_multi: WPR needs weights");
     if (g->relabeled) return nx::invalid("nx_run_multi: a graph was built with NX_RELABEL");
   }
+  nx::TraceRange trace("nx_run_multi");
   return nx::multi_impl(graphs, count, program, alpha, iters, stats);
 }
 

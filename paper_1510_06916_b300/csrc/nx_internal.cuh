@@ -9,8 +9,19 @@
 #include <vector>
 
 #include "../../include/nxgraph.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace nx {
+
+// A named range on the NVTX timeline for the library's phases (builds, runs,
+// their plan and iteration loops), for Nsight tools; with no tool attached a
+// push and a pop cost a few nanoseconds.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
