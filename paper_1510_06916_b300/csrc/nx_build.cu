@@ -15,6 +15,13 @@
 //     format": destination and source high bits are implied by the position.
 //   * Hub index (Table I, H_ij): one entry per distinct destination of each
 //     sub-shard, in order, with its destination offset inside its tile.
+//
+// Steps: ids checked and out-degrees counted as the edges arrive; with
+// NX_RELABEL the degree order of the vertices; keys (j*P + i, dst - jL,
+// src - iL) radix-sorted (host edges: chunk by chunk as the chunks land, the
+// sorted chunks merged by merge path); in-degrees counted from the sorted
+// forward keys and the tiles cut by them; one pass writes the edge words, run
+// heads and piece starts; the hub index follows from the run heads.
 #include <algorithm>
 #include <cstdio>
 
