@@ -128,3 +128,20 @@ def test_compact_extras_keep_scalars_and_errors():
     assert out["rmat22"] == {"gteps": 1.0, "roofline_frac": 0.2}
     assert len(out["scc"]["error"]) == 120
     assert out["unknown"] == {} and "bad" not in out
+
+
+def test_link_roofline_only_for_runs_that_stream():
+    resident = {"h2d_bytes": 0, "d2h_bytes": 4096, "ms": 10.0}  # activity flags only
+    assert bench.link_roofline(resident, 50.0) is None
+    streamed = {"h2d_bytes": 500_000_000, "d2h_bytes": 0, "ms": 20.0}
+    r = bench.link_roofline(streamed, 50.0)
+    assert abs(r["link_gbs"] - 25.0) < 1e-9 and abs(r["link_frac"] - 0.5) < 1e-12
+
+
+def test_compact_keeps_the_named_scalars_and_errors():
+    extras = {"rmat26_programs": {"spu_bfs_ms": 1.0, "mpu6gb_wcc_link_frac": 0.9, "spu_bfs": {"ms": 1.0}},
+              "scc": {"error": "x" * 500}, "unknown": {"a": 1}, "not_a_dict": 3}
+    out = bench.compact(extras)
+    assert out["rmat26_programs"] == {"spu_bfs_ms": 1.0, "mpu6gb_wcc_link_frac": 0.9}
+    assert out["scc"] == {"error": "x" * 120}
+    assert out["unknown"] == {} and "not_a_dict" not in out
