@@ -249,12 +249,14 @@ nx_status nx_dsss_export(const nx_graph* g, int32_t transpose, uint32_t* src, ui
  *  - B_M >= 2 n B_a (SPU, and MPU / AUTO with Q = P): shards [0, Jc) and the
  *    head of shard Jc that fit stay on the device; the rest of the edge words
  *    live only in pinned host memory and stream through two staging buffers
- *    (bands of sub-shards of at most 64 MB, unless one sub-shard is larger)
- *    on a side stream every iteration. DSSS the program does not read, the
- *    hub index and (except for NX_WPR) the weights move to pinned host memory
- *    too. The device then holds the budget plus: out-degrees and PageRank
- *    contributions (12 n bytes), piece offsets (16 bytes per piece per DSSS),
- *    tile tables, one column of accumulators and the staging buffers. The
+ *    on a side stream every iteration, in bands of at most 64 MB (consecutive
+ *    sub-shards of a shard, or ranges of the tiles of one larger sub-shard; a
+ *    band exceeds 64 MB only when a single tile does). DSSS the program does
+ *    not read, the hub index and (except for NX_WPR) the weights move to
+ *    pinned host memory too. The device then holds the budget plus:
+ *    out-degrees and PageRank contributions (12 n bytes), the id maps of
+ *    NX_RELABEL (8 n), piece offsets (16 bytes per piece per DSSS), tile
+ *    tables, one column of accumulators and the staging buffers. The
  *    layout persists after the run (nx_graph_get_info: device_bytes,
  *    host_bytes); a later call that needs more on the device (a run without a
  *    budget, nx_run_ppr_batch, nx_adjoint_wpr, nx_run_multi, nx_dsss_export)
