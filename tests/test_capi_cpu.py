@@ -167,3 +167,9 @@ def test_fault_injection_hook_arms_and_disarms_without_a_device():
     nx.debug_fail_alloc(3)
     nx.debug_fail_alloc(-1)
     nx.debug_fail_alloc(-7)  # any negative value disarms
+
+
+def test_binding_declares_argument_types_for_every_export():
+    # without argtypes ctypes would pass 64-bit sizes and pointers as C ints
+    lib = nx.lib()
+    assert [n for n in nx.EXPORTS if getattr(lib, n).argtypes is None] == []
